@@ -1,0 +1,133 @@
+"""Workload descriptions: the paper's two flows at the benchmark sizes.
+
+A workload is a plain dict of parameters.  Keys:
+
+  dim, nx, ny, nz     lattice (2-D: nz = 1; D2Q9 in 2-D, D3Q19 in 3-D)
+  walls               halfway bounce-back walls in y (rows 0 and ny-1 solid)
+  tau                 BGK relaxation time
+  forcing             'edm' (exact difference method) or 'guo'
+  body_force          constant force density (Fx, Fy, Fz)
+  kolmo_amp, kolmo_k  Kolmogorov force density amp*sin(2*pi*k*y/ny) along x
+  kolmo_drag          linear drag rate alpha: force density -alpha * rho v
+  substrate           'none' | 'smag' | 'wale', with c_smag / c_wale
+  qois                list of (kind, filter, scale): kind 'E' or 'Z',
+                      filter 'G' (Gaussian), 'L' (Laplacian) or 'B' (3x3 binomial)
+  n_mp                number of mean-profile QoIs (channel only)
+  to_mode             'off' | 'gamma' | 'lrs' | 'track'
+  gamma_std           std of the per-step random gamma ('gamma' mode)
+  h                   LRS history length
+  seed                run seed (Philox key and input generators)
+  init                ('noise', amp) or ('channel', u_c, noise_frac)
+  storage             'fp32' | 'fp16' | 'bf16' (GPU population storage)
+  steps               steps of the full run
+"""
+
+import copy
+import math
+
+from .units import channel_lattice, kolmogorov_lattice
+
+SCALE_QOIS_3D = [("E", "G", 3), ("Z", "G", 3), ("E", "L", 3), ("Z", "L", 3), ("E", "L", 1), ("Z", "L", 1)]
+
+
+def _base():
+    return dict(dim=2, nx=8, ny=8, nz=1, walls=False, tau=0.6, forcing="edm", body_force=(0.0, 0.0, 0.0),
+                kolmo_amp=0.0, kolmo_k=0, kolmo_drag=0.0, substrate="none", c_smag=0.1, c_wale=0.5,
+                qois=[], n_mp=0, to_mode="off", gamma_std=0.0, h=0, seed=1234, init=("noise", 1e-3),
+                storage="fp32", steps=10)
+
+
+def _c1():
+    w = _base()
+    w.update(name="kolmogorov2d_64_fp64_gamma", dim=2, nx=64, ny=64, tau=0.52, forcing="guo",
+             kolmo_amp=1e-5, kolmo_k=4, qois=[("E", "B", 1), ("Z", "B", 1)], to_mode="gamma",
+             gamma_std=1e-2, seed=20260901, init=("noise", 1e-3), steps=2000)
+    return w
+
+
+def _c2():
+    p = kolmogorov_lattice(256)
+    w = _base()
+    w.update(name="kolmogorov2d_256_smag_tolrs", dim=2, nx=256, ny=256, tau=p["tau"], forcing="guo",
+             kolmo_amp=p["kolmo_amp"], kolmo_k=4, kolmo_drag=p["kolmo_drag"], substrate="smag", c_smag=0.1,
+             qois=[("E", "G", 3), ("Z", "G", 3), ("E", "L", 1), ("Z", "L", 1)], to_mode="lrs", h=400,
+             seed=20260902, init=("noise", 1e-3), steps=20000)
+    return w
+
+
+def _c3():
+    p = channel_lattice(40)
+    w = _base()
+    w.update(name="channel3d_96x40x48_wale_tolrs", dim=3, nx=96, ny=40, nz=48, walls=True, tau=p["tau"],
+             forcing="edm", body_force=(p["body_force"], 0.0, 0.0), substrate="wale", c_wale=2.20,
+             qois=list(SCALE_QOIS_3D), n_mp=6, to_mode="lrs", h=500, seed=20260903,
+             init=("channel", 0.1, 0.05), steps=50000)
+    return w
+
+
+def _c4():
+    p = channel_lattice(200)
+    w = _base()
+    w.update(name="channel3d_480x200x240_bgk", dim=3, nx=480, ny=200, nz=240, walls=True, tau=p["tau"],
+             forcing="edm", body_force=(p["body_force"], 0.0, 0.0), seed=20260904,
+             init=("channel", 0.1, 0.05), steps=2000)
+    return w
+
+
+def _c4_to():
+    """The full TO-LRS channel step (C3 physics) on the 480x200x240 grid."""
+    p = channel_lattice(200)
+    w = _c3()
+    w.update(name="channel3d_480x200x240_wale_tolrs", nx=480, ny=200, nz=240, tau=p["tau"],
+             body_force=(p["body_force"], 0.0, 0.0), seed=20260905, steps=2000)
+    return w
+
+
+WORKLOADS = {
+    "C1": _c1,
+    "C2": _c2,
+    "C3": _c3,
+    "C4": _c4,
+    "C4_TO": _c4_to,
+}
+
+
+def workload(name, **overrides):
+    """A fresh copy of a named workload with keyword overrides applied."""
+    w = copy.deepcopy(WORKLOADS[name]())
+    w.update(overrides)
+    return w
+
+
+def serving_mix(n_members, seed, rate_per_s):
+    """Poisson request stream of mixed 2-D/3-D ensemble members.
+
+    Sizes are uniform over {128, 256, 384, 512}^2 (Kolmogorov, Smagorinsky +
+    TO-LRS with 4 QoIs) and {48x20x24, 72x30x36, 96x40x48} (channel, WALE +
+    TO-LRS with 12 QoIs); horizons are log-uniform in [1e3, 1e4] steps.
+    """
+    import numpy as np
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    sizes2 = [128, 256, 384, 512]
+    sizes3 = [(48, 20, 24), (72, 30, 36), (96, 40, 48)]
+    for m in range(n_members):
+        t += rng.exponential(1.0 / rate_per_s)
+        if rng.uniform() < 0.5:
+            n = int(sizes2[rng.integers(len(sizes2))])
+            p = kolmogorov_lattice(n)
+            w = _c2()
+            w.update(nx=n, ny=n, tau=p["tau"], kolmo_amp=p["kolmo_amp"], kolmo_drag=p["kolmo_drag"])
+        else:
+            nx, ny, nz = sizes3[rng.integers(len(sizes3))]
+            p = channel_lattice(ny)
+            w = _c3()
+            w.update(nx=nx, ny=ny, nz=nz, tau=p["tau"], body_force=(p["body_force"], 0.0, 0.0))
+        w["seed"] = int(seed * 1000 + m)
+        w["steps"] = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e4)))))
+        w["arrival_s"] = t
+        w["name"] = f"member{m}"
+        out.append(w)
+    return out

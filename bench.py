@@ -1,0 +1,332 @@
+"""Benchmark of the fused D3Q19 lattice-Boltzmann + Tau-orthogonal LES step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C4_TO] [--impl ours|reference]
+
+One step is one pass of the whole hot path: pull-stream + WALE + BGK + body
+force, vorticity, the three compact filters applied twice to (v, omega), the
+enstrophy sensitivities, the QoI/Gram reduction, the LRS prediction and FP64
+pattern solve, and the SGS corrector.  The default workload is the 12-QoI
+channel LES (WALE C_w = 2.20, TO-LRS h = 500) on the 480x200x240 D3Q19 grid
+(23.04 M nodes, 3.5 GB per population copy: inputs far larger than the 126 MB
+L2, so no flush is needed between steps).  Inputs are synthetic and seeded
+(laminar profile + 5 % noise, synthetic LRS coefficients).
+
+Printed: one JSON line (rank 0).  `value` is million lattice updates per
+second (MLUPS, all nodes counted, as the paper counts them), summed over ranks.
+Multi-GPU runs are independent replicas (one ensemble member per GPU, no
+collective on the data path).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "D3Q19 MLUPS (HBM GB/s vs 8 TB/s nominal)"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _lrs_for(wl):
+    nq = len(wl["qois"]) + wl["n_mp"]
+    c, mu, sig = synthetic.synthetic_lrs(nq, wl["h"], wl["seed"])
+    return c, mu, sig
+
+
+def _algorithmic_bytes(wl, n):
+    """Per-class minimal DRAM bytes per launch (roofline)."""
+    q = 19 if wl["dim"] == 3 else 9
+    b = {"fp32": 4, "fp16": 2, "bf16": 2}[wl["storage"]]
+    d = wl["dim"]
+    ncomp = 6 if d == 3 else 3
+    to = wl["to_mode"] != "off"
+    return {
+        "collide": n * (2 * q * b + ((1 + d) * 4 if to else 0) + (3 * 4 if wl["substrate"] == "wale" else 0)),
+        "moments": n * (q * b + 3 * 4),
+        "filter": n * 2 * ncomp * 4,
+        "apply": n * (2 * q * b + (1 + d) * 4),
+    }
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2609_32892_b300 import LbmSim, binding as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synthetic.workload(args.workload, storage=args.storage)
+    n_nodes = wl["nx"] * wl["ny"] * wl["nz"]
+    nq = len(wl["qois"]) + wl["n_mp"] if wl["to_mode"] != "off" else 0
+    stream = torch.cuda.Stream(device=dev)
+    sim = LbmSim(wl, member=rank, device=dev, stream=stream)
+    u0 = synthetic.initial_velocity(wl)
+    sim.init(u0)
+    lrs = None
+    if wl["to_mode"] == "lrs":
+        c, mu, sig = _lrs_for(wl)
+        # reference scales from an observe-only warm-up of this run
+        sim.set_lrs(c, mu, sig, np.ones(nq))
+        sim.step(2)
+        rows = sim.qoi()
+        sref = np.sqrt((rows[:, 1:1 + nq] ** 2).mean(axis=0))
+        sref = np.where(sref > 0, sref, 1.0)
+        lrs = (c, mu, sig, sref)
+        sim.init(u0)
+        sim.set_lrs(*lrs)
+    launches = B.lbm_launches_per_step(sim.ctx)
+
+    # warm-up (also captures the CUDA graph)
+    sim.step(args.warmup)
+    sim.sync()
+    sim.qoi()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    B.lbm_sync(sim.ctx)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = ms / args.steps
+    mlups = world * n_nodes * args.steps / (ms * 1e-3) / 1e6
+
+    # per-kernel-class timing: eager launches bracketed by CUDA events on the stream
+    B.lbm_profile(sim.ctx, 1)
+    sim.step(args.profile_steps)
+    sim.sync()
+    prof = B.lbm_profile_read(sim.ctx)
+    B.lbm_profile(sim.ctx, 0)
+    algo = _algorithmic_bytes(wl, n_nodes)
+    peak, peak_kind = _peaks()
+    dominant = max(prof, key=lambda k: prof[k][0])
+    sections = {}
+    for k, (tms, cnt) in prof.items():
+        if cnt:
+            ent = {"ms_per_launch": tms / cnt, "launches_per_step": cnt / args.profile_steps,
+                   "ms_per_step": tms / args.profile_steps}
+            if k in algo:
+                ent["gbs"] = algo[k] / (tms / cnt * 1e-3) / 1e9
+            sections[k] = ent
+    roof = None
+    if dominant in algo:
+        avg_ms = prof[dominant][0] / prof[dominant][1]
+        ach = algo[dominant] / (avg_ms * 1e-3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_kind": peak_kind, "traffic": None,
+                "bytes_per_launch": algo[dominant], "avg_launch_ms": avg_ms}
+    coll = prof["collide"]
+    coll_gbs = algo["collide"] / (coll[0] / coll[1] * 1e-3) / 1e9 if coll[1] else None
+    step_gbs = n_nodes * (2 * (19 if wl["dim"] == 3 else 9) * (4 if wl["storage"] == "fp32" else 2)
+                          + (2 * (1 + wl["dim"]) * 4 if nq else 0)) / (ms_per_step * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: upload the initial field
+    # and the LRS coefficients, step, drain the QoI block, read the status
+    t0 = time.perf_counter()
+    sim.init(u0)
+    if lrs is not None:
+        sim.set_lrs(*lrs)
+    sim.step(args.steps)
+    rows = sim.qoi()
+    B.lbm_sync(sim.ctx)
+    t_e2e = time.perf_counter() - t0
+    h2d = u0.size * 8 + (sum(a.size * 8 for a in lrs) if lrs is not None else 0)
+    d2h = rows.size * 8 + 64
+    e2e = {"value": round(world * n_nodes * args.steps / t_e2e / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+           "note": "lbm_init_macros + lbm_set_lrs from host arrays, K steps, lbm_qoi drain, lbm_sync"}
+
+    extra = {}
+    if args.bgk and rank == 0:
+        for st in ("fp32", "fp16", "bf16"):
+            w4 = synthetic.workload("C4", storage=st)
+            s4 = LbmSim(w4, device=dev, stream=stream)
+            s4.init(u0)
+            s4.step(4)
+            s4.sync()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s4.step(20)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            t4 = a.elapsed_time(b) / 20
+            byts = n_nodes * 2 * 19 * (4 if st == "fp32" else 2)
+            extra[st] = {"ms_per_step": round(t4, 4), "mlups": round(n_nodes / (t4 * 1e-3) / 1e6, 1),
+                         "gbs": round(byts / (t4 * 1e-3) / 1e9, 1), "frac_of_measured": round(byts / (t4 * 1e-3) / 1e9 / peak, 4),
+                         "frac_of_8tbs": round(byts / (t4 * 1e-3) / 1e9 / 8000.0, 4)}
+            s4.close()
+    sim.close()
+    return dict(ms_per_step=ms_per_step, mlups=mlups, launches=launches, clocks=clk, sections=sections,
+                roofline=roof, e2e=e2e, bgk=extra, collide_gbs=coll_gbs, step_gbs=step_gbs, wl=wl,
+                n_nodes=n_nodes)
+
+
+def cpu_oracle_sample(wl, seconds=15.0):
+    """The oracle (as it stands) stepping a bounded sample of the workload:
+    the same physics and QoI set on a 48x40x24 sub-grid, timed for ~`seconds`."""
+    from oracle.sim import Simulation
+
+    sw = dict(wl, nx=48, ny=40, nz=24)
+    if sw["to_mode"] == "lrs":
+        sw["h"] = min(sw["h"], 500)
+    nq = len(sw["qois"]) + sw["n_mp"] if sw["to_mode"] != "off" else 0
+    lrs = None
+    if sw["to_mode"] == "lrs":
+        c, mu, sig = _lrs_for(sw)
+        lrs = (c, mu, sig, np.ones(nq))
+    sim = Simulation(sw, synthetic.initial_velocity(sw), lrs=lrs)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step()
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    nodes = sw["nx"] * sw["ny"] * sw["nz"]
+    return {"value": round(nodes * n / dt / 1e6, 6), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full steps of the same workload physics on a 48x40x24 sub-grid ({nodes} nodes), "
+                      f"FP64 numpy, single thread, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--workload", default="C4_TO")
+    ap.add_argument("--storage", default="fp32")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--no-bgk", dest="bgk", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    wl = synthetic.workload(args.workload, storage=args.storage)
+    config = {"workload": wl["name"], "grid": [wl["nx"], wl["ny"], wl["nz"]], "lattice": "D3Q19" if wl["dim"] == 3 else "D2Q9",
+              "substrate": wl["substrate"], "to_mode": wl["to_mode"],
+              "n_qoi": (len(wl["qois"]) + wl["n_mp"]) if wl["to_mode"] != "off" else 0, "h": wl["h"],
+              "storage": wl["storage"], "l2_policy": "inputs larger than L2 (3.5 GB per population copy)",
+              "parallelism": f"replicas{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        if world > 1:
+            pass
+        samp = cpu_oracle_sample(wl, args.cpu_seconds)
+        line = {"impl": "reference", "metric": METRIC, "value": samp["value"], "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "config": config,
+                "cpu_baseline": samp, "e2e": {"value": samp["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                                              "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+
+        torch.distributed.init_process_group("nccl" if os.environ.get("LBM_DIST_BACKEND") != "gloo" else "gloo")
+    r = run_ours(args, world, rank, local)
+    if rank == 0:
+        cpu = cpu_oracle_sample(wl, args.cpu_seconds) if world == 1 else None
+        line = {"metric": METRIC, "value": round(r["mlups"], 1), "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms_per_step"], 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.storage == "fp32" else f"f32 compute, {args.storage} storage",
+                "data": "synthetic (seeded laminar channel + 5% noise, synthetic LRS coefficients)",
+                "config": config, "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
+                "gpu_launches": int(r["launches"] * args.steps), "clocks": r["clocks"],
+                "step_hbm_gbs": round(r["step_gbs"], 1), "collide_gbs": r["collide_gbs"],
+                "sections": r["sections"], "bgk_480x200x240": r["bgk"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * lbm.h -- C ABI of the B300 library for the fused lattice-Boltzmann LES step
+ * with the Tau-orthogonal (TO) subgrid-scale forcing of "Reduced Subgrid-Scale
+ * Terms for Turbulence Simulations with the Lattice Boltzmann Method".
+ *
+ * One time step (Sec. 3, Eqs. LES-1..3 with the predictor-corrector of Sec. 4):
+ *   stream (pull, periodic x/z, halfway bounce-back walls in y)
+ *   -> moments -> effective relaxation time (Smagorinsky or WALE, Sec. 5)
+ *   -> BGK relaxation (Eq. LES-1) + body force (exact-difference method, Eq.
+ *      collide-and-stream; or Guo's scheme) giving the predictor f^{p*}
+ *   -> QoIs, sensitivities and Gram matrix on v^{p*} (Sec. 4.1-4.2, App. A)
+ *   -> dQ from the coefficient source (Eq. LRS, Eq. dQ-from-ref, or random gamma)
+ *   -> pattern solve and dv_SGS = sum gamma_i O_i (Eqs. TO-ansatz, O-from-V,
+ *      tau-from-dQ) applied as an equilibrium difference (Eq. LES-2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an lbm_status; nothing aborts, prints or traps.
+ *   After a non-OK status, lbm_last_error() gives a one-line reason.
+ * - Memory ownership: the CALLER owns all device memory and streams.  The
+ *   library asks for a byte count (lbm_required_bytes), the caller allocates
+ *   one device buffer of at least that size (256-byte aligned) and passes it
+ *   to lbm_create together with a CUDA stream; every device array lives in
+ *   that buffer and the library never frees it.  lbm_destroy frees only the
+ *   library's host-side state (and its CUDA graph / events).
+ * - Host pointers passed in are read during the call only; the library keeps
+ *   no caller pointer except the device buffer and the stream.
+ * - Grid layout: node index n = (z*ny + y)*nx + x, x fastest.  2-D runs use
+ *   nz = 1.  A velocity field is [3][nz][ny][nx] (component-major); the z
+ *   component of 2-D runs is zero.  Populations are [Q][nz][ny][nx] with the
+ *   population order below.
+ * - With walls (wall flag 1) rows y = 0 and y = ny-1 are solid; the walls
+ *   sit half a cell inside them.  Solid rows are never collided; their
+ *   density reads back as 1 and their velocity as 0.
+ *
+ * Population order (Q = 9 in 2-D, Q = 19 in 3-D):
+ *   D2Q9 : rest, +x, +y, -x, -y, (+x+y), (-x+y), (-x-y), (+x-y)
+ *   D3Q19: rest, +x, -x, +y, -y, +z, -z, (+x+y), (-x-y), (+x-y), (-x+y),
+ *          (+x+z), (-x-z), (+x-z), (-x+z), (+y+z), (-y-z), (+y-z), (-y+z)
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,            /* invalid argument or configuration            */
+    LBM_ERR_BUDGET = 2,         /* buffer too small / batch memory budget full  */
+    LBM_ERR_CUDA = 3,           /* a CUDA runtime call failed                   */
+    LBM_ERR_UNSTABLE = 4,       /* non-finite state, rho <= 0 or |v| > c_s      */
+    LBM_ERR_SINGULAR_GRAM = 5,  /* reported through QoI flags, not as a status  */
+    LBM_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                */
+    LBM_ERR_STATE = 7           /* call not valid in the current state          */
+} lbm_status;
+
+enum { LBM_FORCING_EDM = 0, LBM_FORCING_GUO = 1 };
+enum { LBM_SUBSTRATE_NONE = 0, LBM_SUBSTRATE_SMAG = 1, LBM_SUBSTRATE_WALE = 2 };
+/* Populations are always stored shifted, as g_i = f_i - w_i. */
+enum { LBM_STORAGE_FP32 = 0, LBM_STORAGE_FP16 = 1, LBM_STORAGE_BF16 = 2 };
+enum { LBM_QOI_ENERGY = 0, LBM_QOI_ENSTROPHY = 1 };
+enum { LBM_FILTER_GAUSS = 0, LBM_FILTER_LAPLACE = 1, LBM_FILTER_BINOMIAL = 2 };
+enum {
+    LBM_TO_OFF = 0,      /* substrate-only LES, no QoIs                              */
+    LBM_TO_OBSERVE = 1,  /* QoIs and Gram on the predictor, no forcing (dQ = 0)      */
+    LBM_TO_GAMMA = 2,    /* gamma_i = gamma_std * z_i, z Philox normals per step     */
+    LBM_TO_LRS = 3,      /* online TO-LRS: dQ = LRS(q_h) - q^{n*} (Eq. LRS)         */
+    LBM_TO_TRACK = 4     /* dQ = Q_ref(t^n) - q^{n*} (Eq. dQ-from-ref)              */
+};
+
+#define LBM_MAX_QOI 16   /* scale-aware QoIs + mean-profile bands */
+
+/* QoI flags in the per-step QoI block */
+#define LBM_FLAG_SINGULAR 1u  /* Gram pivot <= 1e-14 max diag: SGS skipped */
+#define LBM_FLAG_UNSTABLE 2u  /* instability seen during this step        */
+
+typedef struct {
+    int32_t kind;    /* LBM_QOI_ENERGY or LBM_QOI_ENSTROPHY               */
+    int32_t filter;  /* LBM_FILTER_*                                        */
+    int32_t scale;   /* s of G_s / L_s (odd, >= 1); ignored for binomial    */
+    int32_t pad;
+} lbm_qoi_spec;
+
+typedef struct {
+    int32_t dim;        /* 2 (D2Q9) or 3 (D3Q19)                                  */
+    int32_t nx, ny, nz; /* lattice size; nz = 1 in 2-D                             */
+    int32_t walls;      /* 1: halfway bounce-back walls in y, 0: periodic in y     */
+    int32_t forcing;    /* LBM_FORCING_*                                           */
+    int32_t substrate;  /* LBM_SUBSTRATE_*                                         */
+    int32_t storage;    /* LBM_STORAGE_*                                           */
+    double tau;         /* molecular relaxation time (nu = (tau - 1/2)/3)          */
+    double body_force[3];  /* constant force density                           */
+    double kolmo_amp;   /* force density kolmo_amp*sin(2 pi kolmo_k y/ny) along x  */
+    double kolmo_drag;  /* linear drag: force density -kolmo_drag * rho u          */
+    int32_t kolmo_k;
+    int32_t to_mode;    /* LBM_TO_*                                                */
+    double c_smag;      /* Smagorinsky constant                                    */
+    double c_wale;      /* WALE constant                                           */
+    int32_t n_qoi;      /* number of scale-aware QoIs in qoi[]                     */
+    int32_t n_mp;       /* number of mean-profile bands (walls only)               */
+    lbm_qoi_spec qoi[LBM_MAX_QOI];
+    int32_t h;          /* LRS history length (LBM_TO_LRS)                         */
+    int32_t qoi_ring;   /* device QoI ring capacity in rows (0: 4096)              */
+    double gamma_std;   /* LBM_TO_GAMMA: std of the per-step gamma                 */
+    uint64_t seed;      /* Philox key word 0                                       */
+    uint64_t member;    /* Philox key word 1 (ensemble member id)                  */
+    int64_t track_len;  /* LBM_TO_TRACK: number of reference rows the buffer holds */
+} lbm_config;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Length of one QoI block row: [step, q*[N], dQ[N], gamma[N], flags], N =
+ * n_qoi + n_mp.  Values are doubles. */
+int lbm_qoi_row_len(const lbm_config* cfg, int64_t* len);
+
+/* Bytes of device memory lbm_create needs for this configuration.
+ * ERR_ARG if the configuration is invalid (the text says why). */
+int lbm_required_bytes(const lbm_config* cfg, size_t* bytes);
+
+/* Build a simulation inside the caller's device buffer.
+ *   dev_buf      device pointer, 256-byte aligned, at least lbm_required_bytes
+ *   bytes        its size (ERR_BUDGET if too small)
+ *   cuda_stream  cudaStream_t on which all work is queued (NULL = legacy default)
+ *   out          receives the handle
+ * The state starts at rest (f = w); call lbm_init_macros or
+ * lbm_set_populations next.  Device errors: ERR_CUDA. */
+int lbm_create(const lbm_config* cfg, void* dev_buf, size_t bytes, void* cuda_stream, lbm_ctx** out);
+
+/* Free host-side state.  Does not touch dev_buf.  Waits for queued work. */
+int lbm_destroy(lbm_ctx* ctx);
+
+/* Text of the last error on this context (NUL-terminated, truncated to len). */
+int lbm_last_error(const lbm_ctx* ctx, char* buf, size_t len);
+
+/* Set the state to f = f^eq(rho, u) from host FP64 arrays rho[nz][ny][nx]
+ * (NULL: rho = 1) and u[3][nz][ny][nx].  Resets the step counter, the QoI
+ * ring, the mean profile and the LRS histories.  Synchronous. */
+int lbm_init_macros(lbm_ctx* ctx, const double* rho, const double* u);
+
+/* Coefficient source of the TO forcing (Sec. 4.3-4.4).  Host FP64 inputs:
+ *   C          [(2h+1)*N + 1][N] row-major LRS matrix; rows ordered as the
+ *              input vector [q^{n-1..n-h}, q^{n*}, q^{n-1*..n-h*}, 1] (Eq. LRS)
+ *   mu, Sigma  residual mean [N] and covariance [N][N] (scaled units);
+ *              Sigma must be symmetric positive definite (ERR_ARG otherwise)
+ *   sigma_ref  [N] per-QoI reference scales (> 0)
+ *   q_hist, qs_hist  optional [h][N] initial histories, row k = q^{n-1-k}
+ *              (NULL: zeros)
+ * Only valid for LBM_TO_LRS.  Synchronous. */
+int lbm_set_lrs(lbm_ctx* ctx, const double* C, const double* mu, const double* Sigma,
+                const double* sigma_ref, const double* q_hist, const double* qs_hist);
+
+/* Reference QoI series for LBM_TO_TRACK: qref[len][N], row n used at step n
+ * (len <= cfg.track_len; steps past the end reuse the last row). */
+int lbm_set_track_reference(lbm_ctx* ctx, const double* qref, int64_t len);
+
+/* Queue nsteps time steps on the stream (asynchronous).  Returns the status
+ * of previously completed work only; instabilities surface at lbm_sync. */
+int lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* Wait for queued work; ERR_UNSTABLE if any step saw an unstable state. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Drain QoI block rows written since the last drain into out[capacity][row_len]
+ * (host).  Synchronises the stream.  If more rows were produced than the ring
+ * holds, the oldest are lost and *n_lost says how many. */
+int lbm_qoi(lbm_ctx* ctx, double* out, int64_t capacity, int64_t* n_written, int64_t* n_lost);
+
+/* Density rho[nz][ny][nx] and velocity u[3][nz][ny][nx] = sum c f / rho of
+ * the current post-collision state, as host FP64.  Synchronous. */
+int lbm_get_macros(lbm_ctx* ctx, double* rho, double* u);
+
+/* Full populations f (not shifted) as host FP64 [Q][nz][ny][nx]. */
+int lbm_get_populations(lbm_ctx* ctx, double* f);
+int lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* Running sum over steps of the plane-mean streamwise velocity of the
+ * corrected post-collision state, prof[ny], and the number of steps summed
+ * (accumulated only while the TO phase runs). */
+int lbm_get_profile(lbm_ctx* ctx, double* prof, int64_t* nsteps);
+
+/* Steps completed (device counter; synchronises). */
+int lbm_get_step(lbm_ctx* ctx, int64_t* step);
+
+/* Checkpoint: the whole device state (populations, counters, LRS histories,
+ * QoI ring, profile) as an opaque host blob of lbm_state_bytes bytes.
+ * lbm_load requires a context created with the same configuration. */
+int lbm_state_bytes(lbm_ctx* ctx, size_t* bytes);
+int lbm_save(lbm_ctx* ctx, void* host_buf, size_t bytes);
+int lbm_load(lbm_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Execution controls.
+ *   lbm_set_graphs(ctx, 1): lbm_step replays a captured CUDA graph of two
+ *     steps (default on); 0 launches every kernel eagerly.
+ *   lbm_profile(ctx, 1): eager launches bracketed by CUDA events on the
+ *     context's stream, accumulated per kernel class; lbm_profile_read
+ *     returns the totals.  Class ids are the LBM_K_* values. */
+enum {
+    LBM_K_MOMENTS = 0, LBM_K_COLLIDE = 1, LBM_K_CURL = 2, LBM_K_FILTER = 3, LBM_K_SENS = 4,
+    LBM_K_REDUCE = 5, LBM_K_LRS = 6, LBM_K_SOLVE = 7, LBM_K_APPLY = 8, LBM_K_COUNT = 9
+};
+int lbm_set_graphs(lbm_ctx* ctx, int enable);
+int lbm_profile(lbm_ctx* ctx, int enable);
+int lbm_profile_read(lbm_ctx* ctx, double* ms, int64_t* launches, int count);
+
+/* Kernel launches one lbm_step(ctx, 1) queues (for launch accounting). */
+int lbm_launches_per_step(lbm_ctx* ctx, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

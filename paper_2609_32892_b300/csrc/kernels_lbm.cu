@@ -1,0 +1,497 @@
+// Stream-collide, SGS apply and state conversion kernels (D2Q9 / D3Q19).
+//
+// Populations are stored shifted, g_i = f_i - w_i, in FP32, FP16 or BF16, as
+// [Q][nz][ny][nx] arrays; all arithmetic is FP32.  Writing the equilibrium and
+// the forcing terms as deviations (delta rho = sum g, rho u = sum c g, since
+// sum w = 1 and sum w c = 0) keeps the small velocity-carrying part of each
+// population at full relative precision.
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------- lattice --
+// Velocity sets in the library's population order (see lbm.h); constexpr so
+// that fully unrolled loops fold every c_i and w_i into immediates.
+template <int DIM> struct Lat;
+
+template <> struct Lat<2> {
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int cx(int i) {
+        constexpr int t[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        constexpr int t[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) {
+        constexpr int t[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+        return t[i];
+    }
+    __host__ __device__ static constexpr float w(int i) {
+        return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+    }
+};
+
+template <> struct Lat<3> {
+    static constexpr int Q = 19;
+    __host__ __device__ static constexpr int cx(int i) {
+        constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cz(int i) {
+        constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        constexpr int t[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+        return t[i];
+    }
+    __host__ __device__ static constexpr float w(int i) {
+        return i == 0 ? 1.0f / 3.0f : (i < 7 ? 1.0f / 18.0f : 1.0f / 36.0f);
+    }
+};
+
+// ---------------------------------------------------------------- storage --
+template <typename T> __device__ __forceinline__ float ldg_(const T* p);
+template <> __device__ __forceinline__ float ldg_<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldg_<__half>(const __half* p) { return __half2float(__ldg(p)); }
+template <> __device__ __forceinline__ float ldg_<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+}
+template <typename T> __device__ __forceinline__ float ld_(const T* p);
+template <> __device__ __forceinline__ float ld_<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ld_<__half>(const __half* p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float ld_<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
+}
+template <typename T> __device__ __forceinline__ void st_(T* p, float v);
+template <> __device__ __forceinline__ void st_<float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void st_<__half>(__half* p, float v) { *p = __float2half_rn(v); }
+template <> __device__ __forceinline__ void st_<__nv_bfloat16>(__nv_bfloat16* p, float v) {
+    *p = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// -------------------------------------------------------------- pull + moments
+// Pull-stream the populations arriving at node (x, y, z) (Eq. LES-3 of the
+// previous step): g_i(x) = g^p_i(x - c_i), or, if x - c_i is a solid row,
+// halfway bounce-back g_i(x) = g^p_{opp(i)}(x).
+template <int DIM, typename T>
+__device__ __forceinline__ void pull(const Params& p, const T* __restrict__ src, int x, int y, int z, int n,
+                                     float* g) {
+    using LT = Lat<DIM>;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int N = (int)p.n;
+    const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
+    const int ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
+    const int zm = DIM == 3 ? wrap(z - 1, nz) : 0, zp = DIM == 3 ? wrap(z + 1, nz) : 0;
+    const bool wall_lo = p.walls && (y == 1);        // source row y-1 solid
+    const bool wall_hi = p.walls && (y == ny - 2);   // source row y+1 solid
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+        const bool bb = (cy == 1 && wall_lo) || (cy == -1 && wall_hi);
+        if (bb) {
+            g[i] = ldg_<T>(src + (size_t)LT::opp(i) * N + n);
+        } else {
+            const int xs = cx == 0 ? x : (cx > 0 ? xm : xp);
+            const int ys = cy == 0 ? y : (cy > 0 ? ym : yp);
+            const int zs = cz == 0 ? z : (cz > 0 ? zm : zp);
+            g[i] = ldg_<T>(src + (size_t)i * N + ((size_t)zs * ny + ys) * nx + xs);
+        }
+    }
+}
+
+struct Macro {
+    float drho, rho, jx, jy, jz;   // deviation density, density, momentum sum c g
+    float fx, fy, fz;              // force density
+    float ux, uy, uz;              // equilibrium velocity (EDM: j/rho, Guo: (j + F/2)/rho)
+};
+
+template <int DIM>
+__device__ __forceinline__ Macro macros_of(const Params& p, const float* g, const float* kolmo, int y) {
+    using LT = Lat<DIM>;
+    Macro m;
+    float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        dr += g[i];
+        if (LT::cx(i)) jx += LT::cx(i) * g[i];
+        if (LT::cy(i)) jy += LT::cy(i) * g[i];
+        if (DIM == 3 && LT::cz(i)) jz += LT::cz(i) * g[i];
+    }
+    m.drho = dr;
+    m.rho = 1.0f + dr;
+    m.jx = jx; m.jy = jy; m.jz = jz;
+    // F = F_body + A sin(2 pi k y / ny) e_x - alpha rho u
+    m.fx = p.body[0] + kolmo[y] - p.kolmo_drag * jx;
+    m.fy = p.body[1] - p.kolmo_drag * jy;
+    m.fz = DIM == 3 ? p.body[2] - p.kolmo_drag * jz : 0.f;
+    const float inv = 1.0f / m.rho;
+    if (p.forcing == LBM_FORCING_GUO) {
+        m.ux = (jx + 0.5f * m.fx) * inv;
+        m.uy = (jy + 0.5f * m.fy) * inv;
+        m.uz = (jz + 0.5f * m.fz) * inv;
+    } else {
+        m.ux = jx * inv;
+        m.uy = jy * inv;
+        m.uz = jz * inv;
+    }
+    return m;
+}
+
+// ------------------------------------------------------------------ kernels --
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) moments_kernel(Params p, const T* __restrict__ src, float* __restrict__ vn,
+                                                      const float* __restrict__ kolmo) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const int N = (int)p.n;
+    const int x = n % p.nx;
+    const int t = n / p.nx;
+    const int y = t % p.ny;
+    const int z = t / p.ny;
+    if (p.walls && (y == 0 || y == p.ny - 1)) {
+        vn[n] = 0.f; vn[N + n] = 0.f; vn[2 * N + n] = 0.f;
+        return;
+    }
+    float g[Lat<DIM>::Q];
+    pull<DIM, T>(p, src, x, y, z, n, g);
+    const Macro m = macros_of<DIM>(p, g, kolmo, y);
+    vn[n] = m.ux;
+    vn[N + n] = m.uy;
+    vn[2 * N + n] = m.uz;
+}
+
+// WALE eddy viscosity from the post-stream velocity field (Sec. 5.2): g_ij =
+// d_j v_i by central differences (zero velocity on solid rows), then
+// nu_t = C_w^2 (Sd:Sd)^{3/2} / ((S:S)^{5/2} + (Sd:Sd)^{5/4}), 0 if that
+// denominator is below 1e-30.
+template <int DIM>
+__device__ __forceinline__ float wale_nut(const Params& p, const float* __restrict__ vn, int x, int y, int z) {
+    const int N = (int)p.n, nx = p.nx, ny = p.ny, nz = p.nz;
+    float gm[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) gm[a][b] = 0.f;
+    const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
+    const int ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
+    const size_t row = ((size_t)z * ny + y) * nx;
+#pragma unroll
+    for (int i = 0; i < (DIM == 3 ? 3 : 2); ++i) {
+        const float* v = vn + (size_t)i * N;
+        gm[i][0] = 0.5f * (v[row + xp] - v[row + xm]);
+        gm[i][1] = 0.5f * (v[((size_t)z * ny + yp) * nx + x] - v[((size_t)z * ny + ym) * nx + x]);
+        if (DIM == 3) {
+            const int zm = wrap(z - 1, nz), zp = wrap(z + 1, nz);
+            gm[i][2] = 0.5f * (v[((size_t)zp * ny + y) * nx + x] - v[((size_t)zm * ny + y) * nx + x]);
+        }
+    }
+    float g2[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) g2[a][b] = gm[a][0] * gm[0][b] + gm[a][1] * gm[1][b] + gm[a][2] * gm[2][b];
+    const float tr = g2[0][0] + g2[1][1] + g2[2][2];
+    float ss = 0.f, sdsd = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float s = 0.5f * (gm[a][b] + gm[b][a]);
+            float sd = 0.5f * (g2[a][b] + g2[b][a]);
+            if (a == b) sd -= tr * (1.0f / 3.0f);
+            ss += s * s;
+            sdsd += sd * sd;
+        }
+    const float den = ss * ss * sqrtf(ss) + sdsd * sqrtf(sqrtf(sdsd));
+    if (!(den >= 1e-30f)) return 0.f;
+    return p.c_wale2 * sdsd * sqrtf(sdsd) / den;
+}
+
+// One fused predictor step per node: pull, moments, substrate tau_eff, BGK
+// (Eq. LES-1) and the body force (EDM: Eq. collide-and-stream; or Guo),
+// written to dst.  With fields != 0 the density and the predictor velocity
+// v^{p*} = (rho u + F)/rho are stored for the TO phase.
+template <int DIM, typename T, int SUB>
+__global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
+                                                      float* __restrict__ rho_out, float* __restrict__ vps,
+                                                      const float* __restrict__ vn, const float* __restrict__ kolmo,
+                                                      DevState* st, int fields) {
+    using LT = Lat<DIM>;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const int N = (int)p.n;
+    const int x = n % p.nx;
+    const int t = n / p.nx;
+    const int y = t % p.ny;
+    const int z = t / p.ny;
+    if (p.walls && (y == 0 || y == p.ny - 1)) {
+        if (fields) {
+            rho_out[n] = 1.f;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) vps[(size_t)a * N + n] = 0.f;
+        }
+        return;
+    }
+    float g[LT::Q];
+    pull<DIM, T>(p, src, x, y, z, n, g);
+    const Macro m = macros_of<DIM>(p, g, kolmo, y);
+    const float ux = m.ux, uy = m.uy, uz = m.uz;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    if (!(m.rho > 0.f) || !(uu <= (1.0f / 3.0f))) atomicOr(&st->status, 1u);
+
+    // equilibrium deviations g^eq_i = w_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 uu))
+    float geq[LT::Q];
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const float cu = LT::cx(i) * ux + LT::cy(i) * uy + LT::cz(i) * uz;
+        geq[i] = LT::w(i) * (m.drho + m.rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+    }
+    float tau = p.tau;
+    if (SUB == LBM_SUBSTRATE_SMAG) {
+        // Pi^neq_ab = sum_i c_ia c_ib (f_i - f^eq_i); tau_eff closed form (Sec. 5.1)
+        float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+        for (int i = 0; i < LT::Q; ++i) {
+            const float d = g[i] - geq[i];
+            const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+            if (cx) pxx += d;
+            if (cy) pyy += d;
+            if (cz) pzz += d;
+            if (cx * cy) pxy += (cx * cy) * d;
+            if (cx * cz) pxz += (cx * cz) * d;
+            if (cy * cz) pyz += (cy * cz) * d;
+        }
+        const float pn = sqrtf(2.0f * (pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz)));
+        tau = 0.5f * (p.tau + sqrtf(p.tau * p.tau + 18.0f * p.c_smag2 * pn / m.rho));
+    } else if (SUB == LBM_SUBSTRATE_WALE) {
+        tau = p.tau + 3.0f * wale_nut<DIM>(p, vn, x, y, z);
+    }
+    const float om = 1.0f / tau;
+
+    const float fx = m.fx, fy = m.fy, fz = m.fz;
+    if (p.forcing == LBM_FORCING_GUO) {
+        const float pre = 1.0f - 0.5f * om;
+#pragma unroll
+        for (int i = 0; i < LT::Q; ++i) {
+            const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+            const float cu = cx * ux + cy * uy + cz * uz;
+            const float cf = cx * fx + cy * fy + cz * fz;
+            const float s = LT::w(i) * pre * (3.0f * (cf - (ux * fx + uy * fy + uz * fz)) + 9.0f * cu * cf);
+            g[i] = g[i] + (geq[i] - g[i]) * om + s;
+        }
+    } else {
+        const float inv = 1.0f / m.rho;
+        const float dx = fx * inv, dy = fy * inv, dz = fz * inv;
+        const float du = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
+#pragma unroll
+        for (int i = 0; i < LT::Q; ++i) {
+            const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+            const float cu = cx * ux + cy * uy + cz * uz;
+            const float cd = cx * dx + cy * dy + cz * dz;
+            const float s = LT::w(i) * m.rho * (3.0f * cd + 4.5f * cd * (2.0f * cu + cd) - 1.5f * du);
+            g[i] = g[i] + (geq[i] - g[i]) * om + s;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) st_<T>(dst + (size_t)i * N + n, g[i]);
+    if (fields) {
+        const float inv = 1.0f / m.rho;
+        rho_out[n] = m.rho;
+        vps[n] = (m.jx + fx) * inv;
+        vps[(size_t)N + n] = (m.jy + fy) * inv;
+        if (DIM == 3) vps[(size_t)2 * N + n] = (m.jz + fz) * inv;
+    }
+}
+
+// Eq. LES-2 corrector: g^p = g^{p*} + f^eq(rho, v* + dv) - f^eq(rho, v*), with
+// dv = sum_k beta_k V_k + sum_j beta_mp_j w_j(y) e_x (the orthogonal patterns
+// folded into one combination of the sensitivities, beta = G^-1 dQ).
+struct VPtrs {
+    const float* v[kMaxQoi];
+};
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) apply_kernel(Params p, T* __restrict__ f, const float* __restrict__ rho,
+                                                    const float* __restrict__ vps, VPtrs vk,
+                                                    const double* __restrict__ beta,
+                                                    const double* __restrict__ w_mp) {
+    using LT = Lat<DIM>;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const int N = (int)p.n;
+    const int y = (n / p.nx) % p.ny;
+    if (p.walls && (y == 0 || y == p.ny - 1)) return;
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    for (int k = 0; k < p.n_s; ++k) {
+        const float b = (float)beta[k];
+        const float* v = vk.v[k];
+        dx += b * v[n];
+        dy += b * v[(size_t)N + n];
+        if (DIM == 3) dz += b * v[(size_t)2 * N + n];
+    }
+    for (int j = 0; j < p.n_mp; ++j) dx += (float)(beta[p.n_s + j] * w_mp[(size_t)j * p.ny + y]);
+    if (dx == 0.f && dy == 0.f && dz == 0.f) return;
+    const float r = rho[n];
+    const float ux = vps[n], uy = vps[(size_t)N + n], uz = DIM == 3 ? vps[(size_t)2 * N + n] : 0.f;
+    const float du = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+        const float cu = cx * ux + cy * uy + cz * uz;
+        const float cd = cx * dx + cy * dy + cz * dz;
+        T* q = f + (size_t)i * N + n;
+        st_<T>(q, ld_<T>(q) + LT::w(i) * r * (3.0f * cd + 4.5f * cd * (2.0f * cu + cd) - 1.5f * du));
+    }
+}
+
+// f = f^eq(rho, u) on fluid nodes, 0 (= rest) on solid rows; inputs are the
+// density deviation and the velocity as FP32 device arrays.
+template <int DIM, typename T>
+__global__ void init_feq_kernel(Params p, T* __restrict__ f, const float* __restrict__ drho_in,
+                                const float* __restrict__ u) {
+    using LT = Lat<DIM>;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const int N = (int)p.n;
+    const int y = (n / p.nx) % p.ny;
+    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+    const float dr = solid ? 0.f : drho_in[n];
+    const float r = 1.0f + dr;
+    const float ux = solid ? 0.f : u[n], uy = solid ? 0.f : u[(size_t)N + n];
+    const float uz = (solid || DIM == 2) ? 0.f : u[(size_t)2 * N + n];
+    const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const float cu = LT::cx(i) * ux + LT::cy(i) * uy + LT::cz(i) * uz;
+        st_<T>(f + (size_t)i * N + n, solid ? 0.f : LT::w(i) * (dr + r * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu)));
+    }
+}
+
+// density deviation and velocity sum c f / rho of a stored state
+template <int DIM, typename T>
+__global__ void macros_kernel(Params p, const T* __restrict__ f, float* __restrict__ drho, float* __restrict__ u) {
+    using LT = Lat<DIM>;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const int N = (int)p.n;
+    const int y = (n / p.nx) % p.ny;
+    if (p.walls && (y == 0 || y == p.ny - 1)) {
+        drho[n] = 0.f;
+        u[n] = 0.f; u[(size_t)N + n] = 0.f; u[(size_t)2 * N + n] = 0.f;
+        return;
+    }
+    float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const float gi = ld_<T>(f + (size_t)i * N + n);
+        dr += gi;
+        jx += LT::cx(i) * gi;
+        jy += LT::cy(i) * gi;
+        jz += LT::cz(i) * gi;
+    }
+    const float inv = 1.0f / (1.0f + dr);
+    drho[n] = dr;
+    u[n] = jx * inv;
+    u[(size_t)N + n] = jy * inv;
+    u[(size_t)2 * N + n] = jz * inv;
+}
+
+// ---------------------------------------------------------------- launchers --
+static inline unsigned grid_of(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+#define LBM_DISPATCH_STORAGE(p, FN, ...)                                                    \
+    do {                                                                                    \
+        if ((p).storage == LBM_STORAGE_FP16) FN<__half>(__VA_ARGS__);                       \
+        else if ((p).storage == LBM_STORAGE_BF16) FN<__nv_bfloat16>(__VA_ARGS__);           \
+        else FN<float>(__VA_ARGS__);                                                        \
+    } while (0)
+
+template <typename T>
+static void do_init(const Params& p, const Layout& L, const float* drho, const float* u, int which, cudaStream_t s) {
+    if (p.dim == 2)
+        init_feq_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[which], drho, u);
+    else
+        init_feq_kernel<3, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[which], drho, u);
+}
+cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* drho, const float* u, int which,
+                            cudaStream_t s) {
+    LBM_DISPATCH_STORAGE(p, do_init, p, L, drho, u, which, s);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static void do_moments(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    if (p.dim == 2)
+        moments_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
+    else
+        moments_kernel<3, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
+}
+cudaError_t launch_moments(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    LBM_DISPATCH_STORAGE(p, do_moments, p, L, src, s);
+    return cudaGetLastError();
+}
+
+template <int DIM, typename T>
+static void do_collide_d(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    const int fields = p.to_mode != LBM_TO_OFF;
+    const T* a = (const T*)L.f[src];
+    T* b = (T*)L.f[1 - src];
+    const unsigned gr = grid_of(p.n, 256);
+    if (p.substrate == LBM_SUBSTRATE_SMAG)
+        collide_kernel<DIM, T, LBM_SUBSTRATE_SMAG><<<gr, 256, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
+    else if (p.substrate == LBM_SUBSTRATE_WALE)
+        collide_kernel<DIM, T, LBM_SUBSTRATE_WALE><<<gr, 256, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
+    else
+        collide_kernel<DIM, T, LBM_SUBSTRATE_NONE><<<gr, 256, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
+}
+template <typename T>
+static void do_collide(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    if (p.dim == 2) do_collide_d<2, T>(p, L, src, s);
+    else do_collide_d<3, T>(p, L, src, s);
+}
+cudaError_t launch_collide(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    LBM_DISPATCH_STORAGE(p, do_collide, p, L, src, s);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static void do_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) {
+    VPtrs vk;
+    for (int k = 0; k < kMaxQoi; ++k) vk.v[k] = nullptr;
+    for (int k = 0; k < p.n_s; ++k) {
+        const int slot = p.qoi_filter_slot[k];
+        vk.v[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
+    }
+    if (p.dim == 2)
+        apply_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
+    else
+        apply_kernel<3, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
+}
+cudaError_t launch_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) {
+    LBM_DISPATCH_STORAGE(p, do_apply, p, L, dst, s);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static void do_macros(const Params& p, const Layout& L, int which, float* drho, float* u, cudaStream_t s) {
+    if (p.dim == 2)
+        macros_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (const T*)L.f[which], drho, u);
+    else
+        macros_kernel<3, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (const T*)L.f[which], drho, u);
+}
+cudaError_t launch_macros(const Params& p, const Layout& L, int which, float* drho, float* u, cudaStream_t s) {
+    LBM_DISPATCH_STORAGE(p, do_macros, p, L, which, drho, u, s);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,479 @@
+// Tau-orthogonal phase kernels (Sec. 4, App. A): vorticity, separable filter
+// passes, enstrophy sensitivities, the QoI / Gram block reduction, the LRS
+// history matvec and the single-block FP64 coefficient solve.
+//
+// Fields are FP32 structure-of-arrays [comp][nz][ny][nx].  Every field is
+// zero on solid rows, which is exactly the zero extension the filters and the
+// central differences use beyond the walls (Sec. 4.1).
+#include "lbm_common.cuh"
+#include "rng.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__device__ __forceinline__ int modp(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// ------------------------------------------------------------ vorticity --
+// omega = curl v* by central differences: 3-D (d_y v_z - d_z v_y, d_z v_x -
+// d_x v_z, d_x v_y - d_y v_x); 2-D the scalar d_x v_y - d_y v_x.  Written
+// after the d velocity components of the stacked field x6.
+__global__ void __launch_bounds__(256) curl_kernel(Params p, float* __restrict__ x6) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const int N = (int)p.n, nx = p.nx, ny = p.ny, nz = p.nz;
+    const int x = n % nx;
+    const int t = n / nx;
+    const int y = t % ny;
+    const int z = t / ny;
+    const int d = p.dim;
+    if (p.walls && (y == 0 || y == ny - 1)) {
+        for (int c = d; c < p.ncomp; ++c) x6[(size_t)c * N + n] = 0.f;
+        return;
+    }
+    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
+    const int ym = wrapi(y - 1, ny), yp = wrapi(y + 1, ny);
+    const size_t r0 = ((size_t)z * ny + y) * nx;
+    const size_t iym = ((size_t)z * ny + ym) * nx + x, iyp = ((size_t)z * ny + yp) * nx + x;
+    const float* vx = x6;
+    const float* vy = x6 + N;
+    if (d == 2) {
+        const float dxvy = 0.5f * (vy[r0 + xp] - vy[r0 + xm]);
+        const float dyvx = 0.5f * (vx[iyp] - vx[iym]);
+        x6[(size_t)2 * N + n] = dxvy - dyvx;
+        return;
+    }
+    const float* vz = x6 + 2 * (size_t)N;
+    const int zm = wrapi(z - 1, nz), zp = wrapi(z + 1, nz);
+    const size_t izm = ((size_t)zm * ny + y) * nx + x, izp = ((size_t)zp * ny + y) * nx + x;
+    const float dyvz = 0.5f * (vz[iyp] - vz[iym]), dzvy = 0.5f * (vy[izp] - vy[izm]);
+    const float dzvx = 0.5f * (vx[izp] - vx[izm]), dxvz = 0.5f * (vz[r0 + xp] - vz[r0 + xm]);
+    const float dxvy = 0.5f * (vy[r0 + xp] - vy[r0 + xm]), dyvx = 0.5f * (vx[iyp] - vx[iym]);
+    x6[(size_t)3 * N + n] = dyvz - dzvy;
+    x6[(size_t)4 * N + n] = dzvx - dxvz;
+    x6[(size_t)5 * N + n] = dxvy - dyvx;
+}
+
+// --------------------------------------------------------- filter pass --
+// out(x) = [out(x) +] scale * sum_r t(r) in(x - r e_axis) for every component:
+// one 1-D factor of a separable filter.  Periodic along x and z (and y without
+// walls, any radius); along y with walls, rows outside the array contribute
+// nothing and solid rows hold zero, and the output is zero on solid rows.
+__global__ void __launch_bounds__(256) pass_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                   int ncomp, int axis, Taps tp, float scale, int accumulate) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const size_t N = (size_t)p.n;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int x = n % nx;
+    const int t = n / nx;
+    const int y = t % ny;
+    const int z = t / ny;
+    if (p.walls && (y == 0 || y == ny - 1)) {
+        for (int c = 0; c < ncomp; ++c) out[c * N + n] = 0.f;
+        return;
+    }
+    const int R = tp.radius;
+    for (int c = 0; c < ncomp; ++c) {
+        const float* a = in + c * N;
+        float s = 0.f;
+        if (axis == 0) {
+            const size_t row = ((size_t)z * ny + y) * nx;
+            for (int r = -R; r <= R; ++r) s += tp.t[r + R] * a[row + modp(x - r, nx)];
+        } else if (axis == 1) {
+            if (p.walls) {
+                for (int r = -R; r <= R; ++r) {
+                    const int ys = y - r;
+                    if (ys >= 0 && ys < ny) s += tp.t[r + R] * a[((size_t)z * ny + ys) * nx + x];
+                }
+            } else {
+                for (int r = -R; r <= R; ++r) s += tp.t[r + R] * a[((size_t)z * ny + modp(y - r, ny)) * nx + x];
+            }
+        } else {
+            for (int r = -R; r <= R; ++r) s += tp.t[r + R] * a[((size_t)modp(z - r, nz) * ny + y) * nx + x];
+        }
+        float* o = out + c * N + n;
+        *o = accumulate ? (*o + scale * s) : scale * s;
+    }
+}
+
+// ---------------------------------------------- enstrophy sensitivities --
+// V_Z = curl*(W), W = R R omega (App. A): 2-D (d_y W, -d_x W); 3-D curl W.
+__global__ void __launch_bounds__(256) sens_curl_kernel(Params p, const float* __restrict__ w, float* __restrict__ out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const int N = (int)p.n, nx = p.nx, ny = p.ny, nz = p.nz;
+    const int x = n % nx;
+    const int t = n / nx;
+    const int y = t % ny;
+    const int z = t / ny;
+    const int d = p.dim;
+    if (p.walls && (y == 0 || y == ny - 1)) {
+        for (int c = 0; c < d; ++c) out[(size_t)c * N + n] = 0.f;
+        return;
+    }
+    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
+    const int ym = wrapi(y - 1, ny), yp = wrapi(y + 1, ny);
+    const size_t r0 = ((size_t)z * ny + y) * nx;
+    const size_t iym = ((size_t)z * ny + ym) * nx + x, iyp = ((size_t)z * ny + yp) * nx + x;
+    if (d == 2) {
+        out[n] = 0.5f * (w[iyp] - w[iym]);
+        out[(size_t)N + n] = -0.5f * (w[r0 + xp] - w[r0 + xm]);
+        return;
+    }
+    const float* wx = w;
+    const float* wy = w + N;
+    const float* wz = w + 2 * (size_t)N;
+    const int zm = wrapi(z - 1, nz), zp = wrapi(z + 1, nz);
+    const size_t izm = ((size_t)zm * ny + y) * nx + x, izp = ((size_t)zp * ny + y) * nx + x;
+    out[n] = 0.5f * (wz[iyp] - wz[iym]) - 0.5f * (wy[izp] - wy[izm]);
+    out[(size_t)N + n] = 0.5f * (wx[izp] - wx[izm]) - 0.5f * (wz[r0 + xp] - wz[r0 + xm]);
+    out[(size_t)2 * N + n] = 0.5f * (wy[r0 + xp] - wy[r0 + xm]) - 0.5f * (wx[iyp] - wx[iym]);
+}
+
+// ------------------------------------------------------ block reduction --
+// Per block (one y row, a chunk of z planes): <v*, V_k> and <V_i, V_j> (i <= j)
+// over its fluid nodes, and the row sums of v*_x and V_k,x (the mean-profile
+// couplings).  FP32 per thread over a few nodes, FP64 across threads/blocks.
+struct RedPtrs {
+    const float* v[kMaxQoi];
+};
+
+template <int NS>
+__global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __restrict__ vps, RedPtrs vk,
+                                                     double* __restrict__ part, double* __restrict__ plane_part) {
+    constexpr int NG = NS * (NS + 1) / 2;
+    constexpr int NV = NS + NG + 1 + NS;  // <v,V_k>, Gram, row sums (v_x, V_k,x)
+    const int y = blockIdx.x;
+    const int zc = blockIdx.y;
+    const int zper = (p.nz + p.nzc - 1) / p.nzc;
+    const int z0 = zc * zper;
+    const int z1 = min(p.nz, z0 + zper);
+    const size_t N = (size_t)p.n;
+    const int d = p.dim;
+    float acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+    const int cnt = solid ? 0 : (z1 - z0) * p.nx;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int z = z0 + e / p.nx;
+        const int x = e % p.nx;
+        const size_t n = ((size_t)z * p.ny + y) * p.nx + x;
+        float u[3], w[NS][3];
+        u[0] = vps[n]; u[1] = vps[N + n]; u[2] = d == 3 ? vps[2 * N + n] : 0.f;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            w[k][0] = vk.v[k][n];
+            w[k][1] = vk.v[k][N + n];
+            w[k][2] = d == 3 ? vk.v[k][2 * N + n] : 0.f;
+        }
+        int idx = 0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc[idx++] += u[0] * w[k][0] + u[1] * w[k][1] + u[2] * w[k][2];
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+#pragma unroll
+            for (int j = i; j < NS; ++j) acc[idx++] += w[i][0] * w[j][0] + w[i][1] * w[j][1] + w[i][2] * w[j][2];
+        acc[idx++] += u[0];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc[idx++] += w[k][0];
+    }
+    __shared__ double sh[4][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double a = (double)acc[v];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[wid][v] = a;
+    }
+    __syncthreads();
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+        const double s = (sh[0][v] + sh[1][v]) + (sh[2][v] + sh[3][v]);
+        if (v < NS + NG) part[(size_t)blk * (NS + NG) + v] = s;
+        else plane_part[((size_t)zc * p.ny + y) * (1 + NS) + (v - NS - NG)] = s;
+    }
+}
+
+// ------------------------------------------------ LRS history matvec --
+// Partial sums over the rows of C whose inputs are already known before the
+// current QoIs: the histories q^{n-1..n-h}, q^{n-1*..n-h*} (scaled by
+// sigma_ref) and the bias 1 (Eq. LRS).  The q^{n*} block is added in the solve.
+__global__ void __launch_bounds__(256) lrs_hist_kernel(Params p, Layout L) {
+    const int nq = p.n_q, h = p.h;
+    const long long rows = (long long)(2 * h + 1) * nq + 1;
+    const long long r0 = (long long)blockIdx.x * p.lrs_rows_per_blk;
+    const long long r1 = min(rows, r0 + p.lrs_rows_per_blk);
+    const long long pos = L.st->hist_pos;
+    double acc[kMaxQoi];
+    for (int k = 0; k < nq; ++k) acc[k] = 0.0;
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double xr;
+        if (r < (long long)h * nq) {
+            const int kk = (int)(r / nq) + 1, i = (int)(r % nq);
+            const long long slot = ((pos - kk) % h + h) % h;
+            xr = L.qh[slot * nq + i] / L.lrs_sigma[i];
+        } else if (r < (long long)(h + 1) * nq) {
+            continue;
+        } else if (r < rows - 1) {
+            const long long rr = r - (long long)(h + 1) * nq;
+            const int kk = (int)(rr / nq) + 1, i = (int)(rr % nq);
+            const long long slot = ((pos - kk) % h + h) % h;
+            xr = L.qsh[slot * nq + i] / L.lrs_sigma[i];
+        } else {
+            xr = 1.0;
+        }
+        const double* c = L.lrs_C + r * nq;
+        for (int k = 0; k < nq; ++k) acc[k] = fma(xr, c[k], acc[k]);
+    }
+    __shared__ double sh[8][kMaxQoi];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < nq; ++k) {
+        double a = acc[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[wid][k] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][threadIdx.x];
+        L.lrs_part[(size_t)blockIdx.x * nq + threadIdx.x] = s;
+    }
+}
+
+// ------------------------------------------------------------- solve --
+// One block: sum the partials, assemble q^{n*} and the Gram matrix, draw the
+// normals, evaluate the coefficient source, Cholesky-factor G (FP64), and
+// produce beta = G^-1 dQ (dv_SGS = sum_k beta_k V_k equals sum_i gamma_i O_i
+// with c_ij and gamma_i of Sec. 4.2-4.3), gamma_i = dQ_i (G^-1)_ii.  Then
+// write the QoI block row, push the LRS histories, add the mean profile and
+// advance the step counter.
+__global__ void __launch_bounds__(256) solve_kernel(Params p, Layout L) {
+    const int ns = p.n_s, nmp = p.n_mp, nq = p.n_q;
+    const int ng = ns * (ns + 1) / 2;
+    const int npart = ns + ng;
+    __shared__ double red[kMaxQoi + kMaxQoi * (kMaxQoi + 1) / 2];
+    __shared__ double G[kMaxQoi][kMaxQoi];
+    __shared__ double Lc[kMaxQoi][kMaxQoi];
+    __shared__ double Li[kMaxQoi][kMaxQoi];
+    __shared__ double q[kMaxQoi], dq[kMaxQoi], gam[kMaxQoi], beta[kMaxQoi], z[kMaxQoi], tmp[kMaxQoi];
+    __shared__ double wP[kMaxQoi][kMaxQoi + 1];  // sum_y w_j(y) P_k(y), k = 0 (v_x), 1..ns (V_k,x)
+    __shared__ int singular;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const long long step = L.st->step;
+
+    // 1. block partials -> totals (fixed order: strided lanes, then tree)
+    for (int v = wid; v < npart; v += nw) {
+        double a = 0.0;
+        for (int b = lane; b < p.nblk_red; b += 32) a += L.part[(size_t)b * npart + v];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[v] = a;
+    }
+    // 2. plane sums P_k(y) over the z chunks
+    const int np1 = 1 + ns;
+    for (int e = tid; e < p.ny * np1; e += blockDim.x) {
+        const int y = e / np1, k = e % np1;
+        double a = 0.0;
+        for (int zc = 0; zc < p.nzc; ++zc) a += L.plane_part[((size_t)zc * p.ny + y) * np1 + k];
+        L.plane_sum[e] = a;
+    }
+    __syncthreads();
+    // 3. mean-profile couplings sum_y w_j(y) P_k(y)
+    for (int e = tid; e < nmp * np1; e += blockDim.x) {
+        const int j = e / np1, k = e % np1;
+        double a = 0.0;
+        for (int y = 0; y < p.ny; ++y) a += L.w_mp[(size_t)j * p.ny + y] * L.plane_sum[(size_t)y * np1 + k];
+        wP[j][k] = a;
+    }
+    // LRS: sum the history partials
+    if (p.to_mode == LBM_TO_LRS && tid < nq) {
+        double a = 0.0;
+        for (int b = 0; b < p.nblk_lrs; ++b) a += L.lrs_part[(size_t)b * nq + tid];
+        tmp[tid] = a;
+    }
+    __syncthreads();
+    // 4. q^{n*} and G
+    if (tid < nq) {
+        const int i = tid;
+        q[i] = i < ns ? 0.5 * red[i] : wP[i - ns][0];
+        for (int j = 0; j < nq; ++j) {
+            double gij;
+            if (i < ns && j < ns) {
+                const int a = min(i, j), b = max(i, j);
+                gij = red[ns + a * ns - a * (a - 1) / 2 + (b - a)];
+            } else if (i >= ns && j >= ns) {
+                gij = L.g_mpmp[(size_t)(i - ns) * nmp + (j - ns)];
+            } else if (i >= ns) {
+                gij = wP[i - ns][1 + j];
+            } else {
+                gij = wP[j - ns][1 + i];
+            }
+            G[i][j] = gij;
+        }
+        z[i] = 0.0;
+        if (p.to_mode == LBM_TO_LRS) z[i] = philox_normal(p.seed, p.member, step, kStreamLrs, i);
+        if (p.to_mode == LBM_TO_GAMMA) z[i] = philox_normal(p.seed, p.member, step, kStreamGamma, i);
+    }
+    __syncthreads();
+    // 5. Cholesky of G with the pivot test (warp 0)
+    if (wid == 0) {
+        double dmax = 0.0;
+        for (int i = 0; i < nq; ++i) dmax = fmax(dmax, G[i][i]);
+        int sing = !(dmax > 0.0);
+        for (int k = 0; k < nq && !sing; ++k) {
+            double dk = G[k][k];
+            for (int m = 0; m < k; ++m) dk -= Lc[k][m] * Lc[k][m];
+            if (!(dk > 1e-14 * dmax)) { sing = 1; break; }
+            const double lkk = sqrt(dk);
+            const int i = k + 1 + lane;
+            if (i < nq) {
+                double a = G[i][k];
+                for (int m = 0; m < k; ++m) a -= Lc[i][m] * Lc[k][m];
+                Lc[i][k] = a / lkk;
+            }
+            if (lane == 0) Lc[k][k] = lkk;
+            __syncwarp();
+        }
+        if (lane == 0) singular = sing;
+        __syncwarp();
+        // inverse of the factor, column `lane`: L X = e_lane
+        if (!sing && lane < nq) {
+            const int c = lane;
+            for (int r = 0; r < nq; ++r) {
+                double a = (r == c) ? 1.0 : 0.0;
+                for (int m = c; m < r; ++m) a -= Lc[r][m] * Li[m][c];
+                Li[r][c] = r < c ? 0.0 : a / Lc[r][r];
+            }
+        }
+    }
+    __syncthreads();
+    // 6. coefficient source -> dQ, gamma, beta
+    if (tid < nq) {
+        const int i = tid;
+        double ginv_ii = 0.0;
+        if (!singular)
+            for (int r = i; r < nq; ++r) ginv_ii += Li[r][i] * Li[r][i];
+        double d = 0.0, g = 0.0;
+        if (p.to_mode == LBM_TO_LRS) {
+            double qh = tmp[i] + L.lrs_mu[i];
+            for (int j = 0; j < nq; ++j)
+                qh += (q[j] / L.lrs_sigma[j]) * L.lrs_C[((size_t)p.h * nq + j) * nq + i] + L.lrs_L[(size_t)i * nq + j] * z[j];
+            const double qn = L.lrs_sigma[i] * qh;
+            d = qn - q[i];
+            tmp[i] = qn;  // corrected QoI for the history
+            g = singular ? 0.0 : d * ginv_ii;
+        } else if (p.to_mode == LBM_TO_GAMMA) {
+            if (!singular) {
+                g = p.gamma_std * z[i];
+                d = g / ginv_ii;
+            }
+        } else if (p.to_mode == LBM_TO_TRACK) {
+            long long row = step < p.track_len ? step : p.track_len - 1;
+            d = L.track[(size_t)row * nq + i] - q[i];
+            g = singular ? 0.0 : d * ginv_ii;
+        }
+        dq[i] = d;
+        gam[i] = g;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // beta = G^-1 dQ = L^-T L^-1 dQ
+        const bool skip = singular || p.to_mode == LBM_TO_OBSERVE;
+        double yv[kMaxQoi];
+        for (int r = 0; r < nq; ++r) {
+            double a = 0.0;
+            if (!skip)
+                for (int m = 0; m <= r; ++m) a += Li[r][m] * dq[m];
+            yv[r] = a;
+        }
+        for (int c = 0; c < nq; ++c) {
+            double a = 0.0;
+            if (!skip)
+                for (int r = c; r < nq; ++r) a += Li[r][c] * yv[r];
+            beta[c] = a;
+            L.beta[c] = a;
+        }
+        // QoI block row
+        const long long rc = L.st->ring_count;
+        double* row = L.ring + (size_t)(rc % p.ring_cap) * p.row_len;
+        row[0] = (double)step;
+        for (int i = 0; i < nq; ++i) {
+            row[1 + i] = q[i];
+            row[1 + nq + i] = dq[i];
+            row[1 + 2 * nq + i] = gam[i];
+        }
+        unsigned fl = singular ? LBM_FLAG_SINGULAR : 0u;
+        if (L.st->status & 1u) fl |= LBM_FLAG_UNSTABLE;
+        row[1 + 3 * nq] = (double)fl;
+        L.st->ring_count = rc + 1;
+        if (p.to_mode == LBM_TO_LRS && p.h > 0) {
+            const long long slot = L.st->hist_pos % p.h;
+            for (int i = 0; i < nq; ++i) {
+                L.qh[slot * nq + i] = tmp[i];
+                L.qsh[slot * nq + i] = q[i];
+            }
+            L.st->hist_pos += 1;
+        }
+    }
+    __syncthreads();
+    // 7. mean profile of the corrected velocity: P_v + sum_k beta_k P_k + nx nz sum_j beta_mp_j w_j
+    const double area = (double)p.nx * (double)p.nz;
+    for (int y = tid; y < p.ny; y += blockDim.x) {
+        double a = L.plane_sum[(size_t)y * np1];
+        for (int k = 0; k < ns; ++k) a += beta[k] * L.plane_sum[(size_t)y * np1 + 1 + k];
+        for (int j = 0; j < nmp; ++j) a += area * beta[ns + j] * L.w_mp[(size_t)j * p.ny + y];
+        L.profile[y] += a / area;
+    }
+    if (tid == 0) {
+        L.st->prof_steps += 1;
+        L.st->step = step + 1;
+    }
+}
+
+// ------------------------------------------------------------ launchers --
+static inline unsigned gridn(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t launch_to_curl(const Params& p, const Layout& L, cudaStream_t s) {
+    curl_kernel<<<gridn(p.n, 256), 256, 0, s>>>(p, L.x6);
+    return cudaGetLastError();
+}
+cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t, float scale,
+                        int accumulate, cudaStream_t s) {
+    pass_kernel<<<gridn(p.n, 256), 256, 0, s>>>(p, in, out, ncomp, axis, t, scale, accumulate);
+    return cudaGetLastError();
+}
+cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s) {
+    sens_curl_kernel<<<gridn(p.n, 256), 256, 0, s>>>(p, w, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* vk, cudaStream_t s) {
+    RedPtrs r;
+    for (int k = 0; k < kMaxQoi; ++k) r.v[k] = k < p.n_s ? vk[k] : nullptr;
+    dim3 grid(p.ny, p.nzc);
+    switch (p.n_s) {
+        case 1: reduce_kernel<1><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        case 2: reduce_kernel<2><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        case 3: reduce_kernel<3><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        case 4: reduce_kernel<4><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        case 5: reduce_kernel<5><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        case 6: reduce_kernel<6><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        case 7: reduce_kernel<7><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        case 8: reduce_kernel<8><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+cudaError_t launch_lrs_hist(const Params& p, const Layout& L, cudaStream_t s) {
+    lrs_hist_kernel<<<p.nblk_lrs, 256, 0, s>>>(p, L);
+    return cudaGetLastError();
+}
+cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s) {
+    solve_kernel<<<1, 256, 0, s>>>(p, L);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

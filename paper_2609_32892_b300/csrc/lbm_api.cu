@@ -1,0 +1,923 @@
+// C ABI of the library (include/lbm.h): configuration checks, placement of
+// every device array inside the caller's buffer, the per-step launch
+// sequence, CUDA-graph replay and host<->device marshalling.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "lbm_common.cuh"
+
+using namespace lbm;
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+struct Filter {
+    int kind;   // LBM_FILTER_*
+    int scale;
+    bool need_z;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_config cfg;
+    Params p;
+    Layout L;
+    cudaStream_t stream;       // caller's stream
+    cudaStream_t cap_stream;   // private stream used only to capture the step graph
+    std::vector<Filter> filters;
+    std::vector<Taps> taps1d;  // scratch for building passes
+    int cur;                   // which population buffer holds the current state
+    int use_graphs;
+    int profiling;
+    cudaGraphExec_t graph;     // two steps: src 0 -> 1, then 1 -> 0
+    long long host_read;       // QoI rows already drained
+    long long launches_per_step;
+    float* aux;                // [4][N] scratch for macros / init
+    size_t elem;               // bytes per stored population
+    char err[256];
+    // profiling
+    cudaEvent_t ev[2 * 96];
+    int ev_used;
+    int ev_class[96];
+    double prof_ms[LBM_K_COUNT];
+    long long prof_n[LBM_K_COUNT];
+    int lrs_set;
+};
+
+static int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+    char buf[256];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    snprintf(g_err, sizeof g_err, "%s", buf);
+    if (c) snprintf(c->err, sizeof c->err, "%s", buf);
+    return code;
+}
+
+#define CK(c, call)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail((c), LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------ validation --
+static int qoi_count(const lbm_config* c) { return c->to_mode == LBM_TO_OFF ? 0 : c->n_qoi + c->n_mp; }
+
+static int validate(const lbm_config* c) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "config is NULL");
+    if (c->dim != 2 && c->dim != 3) return fail(nullptr, LBM_ERR_ARG, "dim must be 2 or 3");
+    if (c->nx < 3 || c->ny < 3 || c->nz < 1) return fail(nullptr, LBM_ERR_ARG, "grid too small (nx, ny >= 3)");
+    if (c->dim == 2 && c->nz != 1) return fail(nullptr, LBM_ERR_ARG, "2-D runs need nz = 1");
+    if (c->dim == 3 && c->nz < 3) return fail(nullptr, LBM_ERR_ARG, "3-D runs need nz >= 3");
+    if (c->walls && c->ny < 4) return fail(nullptr, LBM_ERR_ARG, "walls need ny >= 4");
+    if (!(c->tau > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau must exceed 1/2");
+    if (c->forcing != LBM_FORCING_EDM && c->forcing != LBM_FORCING_GUO) return fail(nullptr, LBM_ERR_ARG, "bad forcing");
+    if (c->substrate < 0 || c->substrate > 2) return fail(nullptr, LBM_ERR_ARG, "bad substrate");
+    if (c->storage < 0 || c->storage > 2) return fail(nullptr, LBM_ERR_ARG, "bad storage");
+    if (c->to_mode < 0 || c->to_mode > 4) return fail(nullptr, LBM_ERR_ARG, "bad to_mode");
+    const long long n = (long long)c->nx * c->ny * c->nz;
+    const int q = c->dim == 2 ? 9 : 19;
+    if (n * q >= (1LL << 31) || n * 6 >= (1LL << 31)) return fail(nullptr, LBM_ERR_ARG, "grid too large (Q*N >= 2^31)");
+    if (c->to_mode != LBM_TO_OFF) {
+        if (c->n_qoi < 0 || c->n_mp < 0 || c->n_qoi + c->n_mp < 1 || c->n_qoi + c->n_mp > LBM_MAX_QOI)
+            return fail(nullptr, LBM_ERR_ARG, "need 1..%d QoIs", LBM_MAX_QOI);
+        if (c->n_qoi > 8) return fail(nullptr, LBM_ERR_ARG, "at most 8 scale-aware QoIs");
+        if (c->n_qoi < 1) return fail(nullptr, LBM_ERR_ARG, "need at least one scale-aware QoI");
+        if (c->n_mp > 0 && !c->walls) return fail(nullptr, LBM_ERR_ARG, "mean-profile QoIs need walls");
+        if (c->n_mp == 1) return fail(nullptr, LBM_ERR_ARG, "mean-profile bands need n_mp >= 2");
+        for (int i = 0; i < c->n_qoi; ++i) {
+            const lbm_qoi_spec& s = c->qoi[i];
+            if (s.kind != LBM_QOI_ENERGY && s.kind != LBM_QOI_ENSTROPHY) return fail(nullptr, LBM_ERR_ARG, "bad QoI kind");
+            if (s.filter < 0 || s.filter > 2) return fail(nullptr, LBM_ERR_ARG, "bad QoI filter");
+            if (s.filter != LBM_FILTER_BINOMIAL && (s.scale < 1 || s.scale % 2 == 0))
+                return fail(nullptr, LBM_ERR_ARG, "filter scale must be odd and >= 1");
+            const int alpha = c->dim == 2 ? 4 : 2;
+            if (s.filter == LBM_FILTER_GAUSS && 2 * alpha * s.scale + 1 > kMaxTaps)
+                return fail(nullptr, LBM_ERR_ARG, "Gaussian scale too large");
+            if (s.filter == LBM_FILTER_LAPLACE && 5 * s.scale > kMaxTaps)
+                return fail(nullptr, LBM_ERR_ARG, "Laplacian scale too large");
+        }
+        if (c->to_mode == LBM_TO_LRS && c->h < 1) return fail(nullptr, LBM_ERR_ARG, "LRS needs h >= 1");
+        if (c->to_mode == LBM_TO_TRACK && c->track_len < 1) return fail(nullptr, LBM_ERR_ARG, "tracking needs track_len >= 1");
+    }
+    return LBM_OK;
+}
+
+static std::vector<Filter> distinct_filters(const lbm_config* c, int* slot) {
+    std::vector<Filter> out;
+    if (c->to_mode == LBM_TO_OFF) return out;
+    for (int i = 0; i < c->n_qoi; ++i) {
+        const int kind = c->qoi[i].filter;
+        const int s = kind == LBM_FILTER_BINOMIAL ? 1 : c->qoi[i].scale;
+        int found = -1;
+        for (size_t j = 0; j < out.size(); ++j)
+            if (out[j].kind == kind && out[j].scale == s) found = (int)j;
+        if (found < 0) {
+            out.push_back({kind, s, false});
+            found = (int)out.size() - 1;
+        }
+        if (c->qoi[i].kind == LBM_QOI_ENSTROPHY) out[found].need_z = true;
+        slot[i] = found;
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------- layout --
+struct Carver {
+    size_t off = 0;
+    char* base = nullptr;
+    template <typename T> T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* r = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return r;
+    }
+};
+
+static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* filt) {
+    memset(p, 0, sizeof *p);
+    p->dim = c->dim;
+    p->q = c->dim == 2 ? 9 : 19;
+    p->nx = c->nx; p->ny = c->ny; p->nz = c->nz;
+    p->walls = c->walls ? 1 : 0;
+    p->forcing = c->forcing;
+    p->substrate = c->substrate;
+    p->storage = c->storage;
+    p->to_mode = c->to_mode;
+    p->n = (long long)c->nx * c->ny * c->nz;
+    p->tau = (float)c->tau;
+    for (int a = 0; a < 3; ++a) p->body[a] = (float)c->body_force[a];
+    if (c->dim == 2) p->body[2] = 0.f;
+    p->kolmo_drag = (float)c->kolmo_drag;
+    p->c_smag2 = (float)(c->c_smag * c->c_smag);
+    p->c_wale2 = (float)(c->c_wale * c->c_wale);
+    const bool to = c->to_mode != LBM_TO_OFF;
+    p->n_s = to ? c->n_qoi : 0;
+    p->n_mp = to ? c->n_mp : 0;
+    p->n_q = p->n_s + p->n_mp;
+    int slot[kMaxQoi] = {0};
+    *filt = distinct_filters(c, slot);
+    for (int i = 0; i < p->n_s; ++i) {
+        p->qoi_kind[i] = c->qoi[i].kind;
+        p->qoi_filter_slot[i] = slot[i];
+    }
+    p->n_filters = (int)filt->size();
+    p->ncomp = c->dim == 2 ? 3 : 6;
+    p->h = c->to_mode == LBM_TO_LRS ? c->h : 0;
+    p->ring_cap = c->qoi_ring > 0 ? c->qoi_ring : 4096;
+    p->row_len = 2 + 3 * p->n_q;
+    p->track_len = c->to_mode == LBM_TO_TRACK ? c->track_len : 0;
+    p->gamma_std = c->gamma_std;
+    p->seed = c->seed;
+    p->member = c->member;
+    // reduction geometry: one block per (row y, chunk of z planes), ~1200 blocks
+    int target = (1184 + c->ny - 1) / c->ny;
+    if (target < 1) target = 1;
+    if (target > c->nz) target = c->nz;
+    const int zper = (c->nz + target - 1) / target;
+    p->nzc = (c->nz + zper - 1) / zper;
+    p->nblk_red = c->ny * p->nzc;
+    p->npart = p->n_s + p->n_s * (p->n_s + 1) / 2;
+    if (p->h > 0) {
+        const long long rows = (long long)(2 * p->h + 1) * p->n_q + 1;
+        p->lrs_rows_per_blk = 1024;
+        p->nblk_lrs = (int)((rows + 1023) / 1024);
+    }
+}
+
+static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filter>& filt, char* base, Layout* L,
+                    float** aux) {
+    Carver cv;
+    cv.base = base;
+    Layout l;
+    memset(&l, 0, sizeof l);
+    const size_t N = (size_t)p.n;
+    const size_t elem = c->storage == LBM_STORAGE_FP32 ? 4 : 2;
+    l.f[0] = cv.take<char>(elem * p.q * N);
+    l.f[1] = cv.take<char>(elem * p.q * N);
+    *aux = cv.take<float>(4 * N);
+    l.kolmo = cv.take<float>(p.ny);
+    if (c->substrate == LBM_SUBSTRATE_WALE) l.vn = cv.take<float>(3 * N);
+    if (p.to_mode != LBM_TO_OFF) {
+        l.rho = cv.take<float>(N);
+        l.x6 = cv.take<float>(p.ncomp * N);
+        l.vps = l.x6;
+        l.t1 = cv.take<float>(p.ncomp * N);
+        l.t2 = cv.take<float>(p.ncomp * N);
+        l.acc = cv.take<float>(p.ncomp * N);
+        for (size_t f = 0; f < filt.size(); ++f) {
+            l.rr[f] = cv.take<float>(p.ncomp * N);
+            l.vz[f] = filt[f].need_z ? cv.take<float>(p.dim * N) : nullptr;
+        }
+        l.part = cv.take<double>((size_t)p.nblk_red * (p.npart > 0 ? p.npart : 1));
+        l.plane_part = cv.take<double>((size_t)p.nzc * p.ny * (1 + p.n_s));
+        l.plane_sum = cv.take<double>((size_t)p.ny * (1 + p.n_s));
+        if (p.h > 0) {
+            const size_t rows = (size_t)(2 * p.h + 1) * p.n_q + 1;
+            l.lrs_part = cv.take<double>((size_t)p.nblk_lrs * p.n_q);
+            l.lrs_C = cv.take<double>(rows * p.n_q);
+            l.lrs_mu = cv.take<double>(p.n_q);
+            l.lrs_L = cv.take<double>((size_t)p.n_q * p.n_q);
+            l.lrs_sigma = cv.take<double>(p.n_q);
+            l.qh = cv.take<double>((size_t)p.h * p.n_q);
+            l.qsh = cv.take<double>((size_t)p.h * p.n_q);
+        }
+        if (p.track_len > 0) l.track = cv.take<double>((size_t)p.track_len * p.n_q);
+        l.w_mp = cv.take<double>((size_t)(p.n_mp > 0 ? p.n_mp : 1) * p.ny);
+        l.g_mpmp = cv.take<double>((size_t)(p.n_mp > 0 ? p.n_mp * p.n_mp : 1));
+        l.beta = cv.take<double>(kMaxQoi);
+        l.ring = cv.take<double>((size_t)p.ring_cap * p.row_len);
+        l.profile = cv.take<double>(p.ny);
+    }
+    l.st = cv.take<DevState>(1);
+    if (L) *L = l;
+    return (cv.off + 255) & ~(size_t)255;
+}
+
+// -------------------------------------------------------- filter passes --
+// 1-D factors of the compact filters (Sec. 4.1).
+//   G_s: exp(-r^2/(2 s^2)) normalised on |r| <= alpha s (alpha = 4 in 2-D,
+//        2 in 3-D); the d-D kernel of Eq. gaussian is the product of these.
+//   L_s: sum over axes a of [l dilated by s along a] x [box_s on the other
+//        axes], l = [1,-4,6,-4,1], scaled by 1/(8 d s^d) so sum |L_s| = 2
+//        (Eq. laplace, Kronecker dilation with the all-ones block).
+//   B3 : [1, 2, 1] / 4 on every axis.
+static Taps gauss_taps(int s, int dim) {
+    Taps t;
+    memset(&t, 0, sizeof t);
+    const int alpha = dim == 2 ? 4 : 2;
+    t.radius = alpha * s;
+    double sum = 0.0, v[kMaxTaps];
+    for (int r = -t.radius; r <= t.radius; ++r) {
+        v[r + t.radius] = exp(-(double)(r * r) / (2.0 * s * s));
+        sum += v[r + t.radius];
+    }
+    for (int i = 0; i <= 2 * t.radius; ++i) t.t[i] = (float)(v[i] / sum);
+    return t;
+}
+static Taps ell_taps(int s) {
+    static const double ell[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
+    Taps t;
+    memset(&t, 0, sizeof t);
+    t.radius = (5 * s - 1) / 2;
+    for (int m = 0; m < 5 * s; ++m) t.t[m] = (float)ell[m / s];
+    return t;
+}
+static Taps box_taps(int s) {
+    Taps t;
+    memset(&t, 0, sizeof t);
+    t.radius = (s - 1) / 2;
+    for (int m = 0; m < s; ++m) t.t[m] = 1.0f;
+    return t;
+}
+static Taps binom_taps() {
+    Taps t;
+    memset(&t, 0, sizeof t);
+    t.radius = 1;
+    t.t[0] = 0.25f; t.t[1] = 0.5f; t.t[2] = 0.25f;
+    return t;
+}
+
+// ---------------------------------------------------------- step sequence --
+struct Launcher {
+    lbm_ctx* c;
+    cudaStream_t s;
+    bool count_only;
+    long long n;
+    cudaError_t err = cudaSuccess;
+    bool timed;
+    void before(int cls) {
+        ++n;
+        if (timed && c->ev_used < 96) {
+            c->ev_class[c->ev_used] = cls;
+            cudaEventRecord(c->ev[2 * c->ev_used], s);
+        }
+    }
+    void after(cudaError_t e) {
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+        if (timed && c->ev_used < 96) {
+            cudaEventRecord(c->ev[2 * c->ev_used + 1], s);
+            ++c->ev_used;
+        }
+    }
+};
+
+#define LAUNCH(lc, cls, expr)              \
+    do {                                   \
+        (lc).before(cls);                  \
+        if (!(lc).count_only) (lc).after(expr); \
+    } while (0)
+
+static void enqueue_filter(Launcher& lc, const Filter& f, const float* in, float* out) {
+    lbm_ctx* c = lc.c;
+    const Params& p = c->p;
+    const int nc = p.ncomp;
+    const int d = p.dim;
+    float* t1 = c->L.t1;
+    float* t2 = c->L.t2;
+    if (f.kind == LBM_FILTER_GAUSS || f.kind == LBM_FILTER_BINOMIAL) {
+        const Taps t = f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps();
+        if (d == 2) {
+            LAUNCH(lc, LBM_K_FILTER, launch_pass(p, in, t1, nc, 0, t, 1.f, 0, lc.s));
+            LAUNCH(lc, LBM_K_FILTER, launch_pass(p, t1, out, nc, 1, t, 1.f, 0, lc.s));
+        } else {
+            LAUNCH(lc, LBM_K_FILTER, launch_pass(p, in, t1, nc, 0, t, 1.f, 0, lc.s));
+            LAUNCH(lc, LBM_K_FILTER, launch_pass(p, t1, t2, nc, 1, t, 1.f, 0, lc.s));
+            LAUNCH(lc, LBM_K_FILTER, launch_pass(p, t2, out, nc, 2, t, 1.f, 0, lc.s));
+        }
+        return;
+    }
+    // Laplacian high-pass: sum of d separable terms
+    const int s = f.scale;
+    double sd = 1.0;
+    for (int a = 0; a < d; ++a) sd *= s;
+    const float scale = (float)(1.0 / (8.0 * d * sd));
+    const Taps el = ell_taps(s);
+    const Taps bx = box_taps(s);
+    for (int a = 0; a < d; ++a) {
+        const int acc = a > 0;
+        if (s == 1) {
+            LAUNCH(lc, LBM_K_FILTER, launch_pass(p, in, out, nc, a, el, scale, acc, lc.s));
+            continue;
+        }
+        int others[2], no = 0;
+        for (int b = 0; b < d; ++b)
+            if (b != a) others[no++] = b;
+        const float* src = in;
+        float* bufs[2] = {t1, t2};
+        for (int k = 0; k < no; ++k) {
+            LAUNCH(lc, LBM_K_FILTER, launch_pass(p, src, bufs[k], nc, others[k], bx, 1.f, 0, lc.s));
+            src = bufs[k];
+        }
+        LAUNCH(lc, LBM_K_FILTER, launch_pass(p, src, out, nc, a, el, scale, acc, lc.s));
+    }
+}
+
+static void enqueue_step(Launcher& lc, int src) {
+    lbm_ctx* c = lc.c;
+    const Params& p = c->p;
+    const Layout& L = c->L;
+    if (p.substrate == LBM_SUBSTRATE_WALE) LAUNCH(lc, LBM_K_MOMENTS, launch_moments(p, L, src, lc.s));
+    LAUNCH(lc, LBM_K_COLLIDE, launch_collide(p, L, src, lc.s));
+    if (p.to_mode == LBM_TO_OFF) return;
+    if (p.to_mode == LBM_TO_LRS) LAUNCH(lc, LBM_K_LRS, launch_lrs_hist(p, L, lc.s));
+    LAUNCH(lc, LBM_K_CURL, launch_to_curl(p, L, lc.s));
+    for (size_t f = 0; f < c->filters.size(); ++f) {
+        enqueue_filter(lc, c->filters[f], L.x6, L.acc);
+        enqueue_filter(lc, c->filters[f], L.acc, L.rr[f]);
+        if (c->filters[f].need_z)
+            LAUNCH(lc, LBM_K_SENS, launch_sens_curl(p, L.rr[f] + (size_t)p.dim * p.n, L.vz[f], lc.s));
+    }
+    const float* vk[kMaxQoi];
+    for (int k = 0; k < p.n_s; ++k) {
+        const int slot = p.qoi_filter_slot[k];
+        vk[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
+    }
+    LAUNCH(lc, LBM_K_REDUCE, launch_reduce(p, L, vk, lc.s));
+    LAUNCH(lc, LBM_K_SOLVE, launch_solve(p, L, lc.s));
+    if (p.to_mode != LBM_TO_OBSERVE) LAUNCH(lc, LBM_K_APPLY, launch_apply(p, L, 1 - src, lc.s));
+}
+
+static void count_launches(lbm_ctx* c) {
+    Launcher lc{c, c->stream, true, 0};
+    lc.timed = false;
+    enqueue_step(lc, 0);
+    c->launches_per_step = lc.n;
+}
+
+static int build_graph(lbm_ctx* c) {
+    if (c->graph) return LBM_OK;
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    Launcher lc{c, c->cap_stream, false, 0};
+    lc.timed = false;
+    enqueue_step(lc, 0);
+    enqueue_step(lc, 1);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (lc.err != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(c, LBM_ERR_CUDA, "graph capture failed: %s",
+                    cudaGetErrorString(lc.err != cudaSuccess ? lc.err : e));
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return fail(c, LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+static int eager_step(lbm_ctx* c) {
+    Launcher lc{c, c->stream, false, 0};
+    lc.timed = c->profiling != 0;
+    c->ev_used = 0;
+    enqueue_step(lc, c->cur);
+    if (lc.err != cudaSuccess) return fail(c, LBM_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(lc.err));
+    c->cur = 1 - c->cur;
+    if (lc.timed) {
+        CK(c, cudaEventSynchronize(c->ev[2 * (c->ev_used - 1) + 1]));
+        for (int i = 0; i < c->ev_used; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]);
+            c->prof_ms[c->ev_class[i]] += ms;
+            c->prof_n[c->ev_class[i]] += 1;
+        }
+    }
+    return LBM_OK;
+}
+
+// ------------------------------------------------------ host-side tables --
+// Mean-profile band weights (Eq. 3d-mp-band-weights) on fluid rows 1..ny-2:
+// d_w = min(y - 1/2, 2H - (y - 1/2)), H = (ny - 2)/2; centres log-spaced from
+// 0.5 to H; sigma = spacing of ln(centre); each band sums to 1 over fluid rows.
+static void band_weights(int ny, int nb, std::vector<double>* w) {
+    w->assign((size_t)nb * ny, 0.0);
+    const double h = 0.5 * (ny - 2);
+    const double l0 = log(0.5), l1 = log(h);
+    const double sig = (l1 - l0) / (nb - 1);
+    for (int j = 0; j < nb; ++j) {
+        const double lc = l0 + (l1 - l0) * j / (nb - 1);
+        double sum = 0.0;
+        for (int y = 1; y <= ny - 2; ++y) {
+            const double yw = y - 0.5;
+            const double dw = yw < 2.0 * h - yw ? yw : 2.0 * h - yw;
+            const double e = (log(dw) - lc) / sig;
+            (*w)[(size_t)j * ny + y] = exp(-0.5 * e * e);
+            sum += (*w)[(size_t)j * ny + y];
+        }
+        for (int y = 1; y <= ny - 2; ++y) (*w)[(size_t)j * ny + y] /= sum;
+    }
+}
+
+template <typename T> static float to_f(T v);
+template <> float to_f<float>(float v) { return v; }
+template <> float to_f<__half>(__half v) { return __half2float(v); }
+template <> float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+static const double kW2[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+static double lat_w(int dim, int i) {
+    if (dim == 2) return kW2[i];
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+static int sync_check(lbm_ctx* c) {
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+template <typename T>
+static void widen(const std::vector<char>& raw, int dim, int q, size_t N, double* f) {
+    const T* g = (const T*)raw.data();
+    for (int i = 0; i < q; ++i)
+        for (size_t n = 0; n < N; ++n) f[(size_t)i * N + n] = lat_w(dim, i) + (double)to_f<T>(g[(size_t)i * N + n]);
+}
+
+// checkpoint blob: magic, sizes, DevState, populations, histories, ring, profile, cursor
+struct BlobHead {
+    uint64_t magic, fbytes, hbytes, rbytes, pbytes;
+    int64_t host_read;
+};
+static const uint64_t kMagic = 0x4c424d544f303031ULL;
+
+static void blob_sizes(lbm_ctx* c, BlobHead* h) {
+    const Params& p = c->p;
+    h->magic = kMagic;
+    h->fbytes = c->elem * p.q * (size_t)p.n;
+    h->hbytes = p.h > 0 ? sizeof(double) * (size_t)p.h * p.n_q : 0;
+    h->rbytes = c->L.ring ? sizeof(double) * (size_t)p.ring_cap * p.row_len : 0;
+    h->pbytes = c->L.profile ? sizeof(double) * (size_t)p.ny : 0;
+    h->host_read = c->host_read;
+}
+
+// ================================================================== C ABI ==
+extern "C" {
+
+int lbm_qoi_row_len(const lbm_config* cfg, int64_t* len) {
+    if (!cfg || !len) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    *len = 2 + 3 * qoi_count(cfg);
+    return LBM_OK;
+}
+
+int lbm_required_bytes(const lbm_config* cfg, size_t* bytes) {
+    int rc = validate(cfg);
+    if (rc) return rc;
+    if (!bytes) return fail(nullptr, LBM_ERR_ARG, "bytes is NULL");
+    Params p;
+    std::vector<Filter> f;
+    make_params(cfg, &p, &f);
+    float* aux;
+    *bytes = carve(cfg, p, f, nullptr, nullptr, &aux);
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_config* cfg, void* dev_buf, size_t bytes, void* cuda_stream, lbm_ctx** out) {
+    int rc = validate(cfg);
+    if (rc) return rc;
+    if (!out || !dev_buf) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    if (((uintptr_t)dev_buf & 255) != 0) return fail(nullptr, LBM_ERR_ARG, "dev_buf must be 256-byte aligned");
+    lbm_ctx* c = new lbm_ctx();
+    memset(c->err, 0, sizeof c->err);
+    c->cfg = *cfg;
+    make_params(cfg, &c->p, &c->filters);
+    const size_t need = carve(cfg, c->p, c->filters, (char*)dev_buf, &c->L, &c->aux);
+    if (bytes < need) {
+        delete c;
+        return fail(nullptr, LBM_ERR_BUDGET, "buffer holds %zu bytes, %zu needed", bytes, need);
+    }
+    c->stream = (cudaStream_t)cuda_stream;
+    c->elem = cfg->storage == LBM_STORAGE_FP32 ? 4 : 2;
+    c->use_graphs = 1;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, LBM_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < 2 * 96; ++i) cudaEventCreate(&c->ev[i]);
+    // zero everything (rest state: shifted populations g = 0), then tables
+    e = cudaMemsetAsync(dev_buf, 0, need, c->stream);
+    std::vector<float> kol(cfg->ny);
+    for (int y = 0; y < cfg->ny; ++y)
+        kol[y] = (float)(cfg->kolmo_amp * sin(2.0 * M_PI * cfg->kolmo_k * (double)y / cfg->ny));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->L.kolmo, kol.data(), sizeof(float) * cfg->ny, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->p.n_mp > 0) {
+        std::vector<double> w;
+        band_weights(cfg->ny, c->p.n_mp, &w);
+        std::vector<double> g((size_t)c->p.n_mp * c->p.n_mp);
+        const double area = (double)cfg->nx * cfg->nz;
+        for (int i = 0; i < c->p.n_mp; ++i)
+            for (int j = 0; j < c->p.n_mp; ++j) {
+                double a = 0.0;
+                for (int y = 0; y < cfg->ny; ++y) a += w[(size_t)i * cfg->ny + y] * w[(size_t)j * cfg->ny + y];
+                g[(size_t)i * c->p.n_mp + j] = area * a;
+            }
+        e = cudaMemcpyAsync(c->L.w_mp, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->L.g_mpmp, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ERR_CUDA, "create: %s", cudaGetErrorString(e));
+    }
+    count_launches(c);
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_OK;
+    cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (int i = 0; i < 2 * 96; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return LBM_OK;
+}
+
+int lbm_last_error(const lbm_ctx* c, char* buf, size_t len) {
+    if (!buf || len == 0) return LBM_ERR_ARG;
+    snprintf(buf, len, "%s", c ? c->err : g_err);
+    return LBM_OK;
+}
+
+static int reset_counters(lbm_ctx* c) {
+    const Params& p = c->p;
+    DevState st;
+    memset(&st, 0, sizeof st);
+    if (p.h > 0) {
+        // keep the LRS history position
+        CK(c, cudaMemcpyAsync(&st, c->L.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        const long long hp = st.hist_pos;
+        memset(&st, 0, sizeof st);
+        st.hist_pos = hp;
+    }
+    CK(c, cudaMemcpyAsync(c->L.st, &st, sizeof st, cudaMemcpyHostToDevice, c->stream));
+    if (c->L.ring) CK(c, cudaMemsetAsync(c->L.ring, 0, sizeof(double) * p.ring_cap * p.row_len, c->stream));
+    if (c->L.profile) CK(c, cudaMemsetAsync(c->L.profile, 0, sizeof(double) * p.ny, c->stream));
+    c->host_read = 0;
+    return LBM_OK;
+}
+
+int lbm_init_macros(lbm_ctx* c, const double* rho, const double* u) {
+    if (!c || !u) return fail(c, LBM_ERR_ARG, "NULL argument");
+    const size_t N = (size_t)c->p.n;
+    std::vector<float> h(4 * N);
+    for (size_t i = 0; i < N; ++i) h[i] = rho ? (float)(rho[i] - 1.0) : 0.f;
+    for (size_t i = 0; i < 3 * N; ++i) h[N + i] = (float)u[i];
+    CK(c, cudaMemcpyAsync(c->aux, h.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice, c->stream));
+    c->cur = 0;
+    CK(c, launch_init_feq(c->p, c->L, c->aux, c->aux + N, 0, c->stream));
+    int rc = reset_counters(c);
+    if (rc) return rc;
+    return sync_check(c);
+}
+
+int lbm_set_lrs(lbm_ctx* c, const double* C, const double* mu, const double* Sigma, const double* sigma_ref,
+                const double* q_hist, const double* qs_hist) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    const Params& p = c->p;
+    if (p.to_mode != LBM_TO_LRS) return fail(c, LBM_ERR_STATE, "lbm_set_lrs needs to_mode LBM_TO_LRS");
+    if (!C || !mu || !Sigma || !sigma_ref) return fail(c, LBM_ERR_ARG, "NULL coefficient array");
+    const int n = p.n_q;
+    for (int i = 0; i < n; ++i)
+        if (!(sigma_ref[i] > 0.0)) return fail(c, LBM_ERR_ARG, "sigma_ref[%d] must be > 0", i);
+    // Cholesky of Sigma (symmetric positive definite required)
+    std::vector<double> Lh((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (fabs(Sigma[i * n + j] - Sigma[j * n + i]) > 1e-12 * (fabs(Sigma[i * n + j]) + fabs(Sigma[j * n + i])) + 1e-300)
+                return fail(c, LBM_ERR_ARG, "Sigma is not symmetric");
+    for (int k = 0; k < n; ++k) {
+        double d = Sigma[k * n + k];
+        for (int m = 0; m < k; ++m) d -= Lh[k * n + m] * Lh[k * n + m];
+        if (!(d > 0.0)) return fail(c, LBM_ERR_ARG, "Sigma is not positive definite");
+        Lh[k * n + k] = sqrt(d);
+        for (int i = k + 1; i < n; ++i) {
+            double a = Sigma[i * n + k];
+            for (int m = 0; m < k; ++m) a -= Lh[i * n + m] * Lh[k * n + m];
+            Lh[i * n + k] = a / Lh[k * n + k];
+        }
+    }
+    const size_t rows = (size_t)(2 * p.h + 1) * n + 1;
+    CK(c, cudaMemcpyAsync(c->L.lrs_C, C, sizeof(double) * rows * n, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->L.lrs_mu, mu, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->L.lrs_L, Lh.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->L.lrs_sigma, sigma_ref, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    // ring slot of q^{n-k} is (pos - k) mod h with pos = 0
+    std::vector<double> qh((size_t)p.h * n, 0.0), qsh((size_t)p.h * n, 0.0);
+    for (int k = 1; k <= p.h; ++k)
+        for (int i = 0; i < n; ++i) {
+            const size_t slot = (size_t)(p.h - k);
+            if (q_hist) qh[slot * n + i] = q_hist[(size_t)(k - 1) * n + i];
+            if (qs_hist) qsh[slot * n + i] = qs_hist[(size_t)(k - 1) * n + i];
+        }
+    CK(c, cudaMemcpyAsync(c->L.qh, qh.data(), sizeof(double) * qh.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->L.qsh, qsh.data(), sizeof(double) * qsh.size(), cudaMemcpyHostToDevice, c->stream));
+    DevState st;
+    CK(c, cudaMemcpyAsync(&st, c->L.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    st.hist_pos = 0;
+    CK(c, cudaMemcpyAsync(c->L.st, &st, sizeof st, cudaMemcpyHostToDevice, c->stream));
+    c->lrs_set = 1;
+    return sync_check(c);
+}
+
+int lbm_set_track_reference(lbm_ctx* c, const double* qref, int64_t len) {
+    if (!c || !qref) return fail(c, LBM_ERR_ARG, "NULL argument");
+    if (c->p.to_mode != LBM_TO_TRACK) return fail(c, LBM_ERR_STATE, "needs to_mode LBM_TO_TRACK");
+    if (len < 1 || len > c->p.track_len) return fail(c, LBM_ERR_ARG, "len must be in 1..track_len");
+    std::vector<double> buf((size_t)c->p.track_len * c->p.n_q);
+    for (long long r = 0; r < c->p.track_len; ++r)
+        for (int i = 0; i < c->p.n_q; ++i)
+            buf[(size_t)r * c->p.n_q + i] = qref[(size_t)(r < len ? r : len - 1) * c->p.n_q + i];
+    CK(c, cudaMemcpyAsync(c->L.track, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->stream));
+    return sync_check(c);
+}
+
+int lbm_step(lbm_ctx* c, int64_t nsteps) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
+    if (c->p.to_mode == LBM_TO_LRS && !c->lrs_set) return fail(c, LBM_ERR_STATE, "call lbm_set_lrs first");
+    int64_t left = nsteps;
+    const bool graphs = c->use_graphs && !c->profiling;
+    if (graphs && left >= 2) {
+        if (c->cur == 1) {
+            int rc = eager_step(c);
+            if (rc) return rc;
+            --left;
+        }
+        if (left >= 2) {
+            int rc = build_graph(c);
+            if (rc) return rc;
+            while (left >= 2) {
+                CK(c, cudaGraphLaunch(c->graph, c->stream));
+                left -= 2;
+            }
+        }
+    }
+    while (left > 0) {
+        int rc = eager_step(c);
+        if (rc) return rc;
+        --left;
+    }
+    CK(c, cudaGetLastError());
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    DevState st;
+    CK(c, cudaMemcpyAsync(&st, c->L.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (st.status & 1u) return fail(c, LBM_ERR_UNSTABLE, "unstable state (non-finite, rho <= 0 or |v| > c_s)");
+    return LBM_OK;
+}
+
+int lbm_qoi(lbm_ctx* c, double* out, int64_t capacity, int64_t* n_written, int64_t* n_lost) {
+    if (!c || !n_written) return fail(c, LBM_ERR_ARG, "NULL argument");
+    *n_written = 0;
+    if (n_lost) *n_lost = 0;
+    const Params& p = c->p;
+    if (p.to_mode == LBM_TO_OFF) return LBM_OK;
+    DevState st;
+    CK(c, cudaMemcpyAsync(&st, c->L.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    long long avail = st.ring_count - c->host_read;
+    if (avail > p.ring_cap) {
+        if (n_lost) *n_lost = avail - p.ring_cap;
+        c->host_read = st.ring_count - p.ring_cap;
+        avail = p.ring_cap;
+    }
+    const long long take = avail < capacity ? avail : capacity;
+    if (take <= 0) return LBM_OK;
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    std::vector<double> ring((size_t)p.ring_cap * p.row_len);
+    CK(c, cudaMemcpyAsync(ring.data(), c->L.ring, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (long long r = 0; r < take; ++r) {
+        const long long src = (c->host_read + r) % p.ring_cap;
+        memcpy(out + (size_t)r * p.row_len, ring.data() + (size_t)src * p.row_len, sizeof(double) * p.row_len);
+    }
+    c->host_read += take;
+    *n_written = take;
+    return LBM_OK;
+}
+
+int lbm_get_macros(lbm_ctx* c, double* rho, double* u) {
+    if (!c || !rho || !u) return fail(c, LBM_ERR_ARG, "NULL argument");
+    const size_t N = (size_t)c->p.n;
+    CK(c, launch_macros(c->p, c->L, c->cur, c->aux, c->aux + N, c->stream));
+    std::vector<float> h(4 * N);
+    CK(c, cudaMemcpyAsync(h.data(), c->aux, sizeof(float) * 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < N; ++i) rho[i] = 1.0 + (double)h[i];
+    for (size_t i = 0; i < 3 * N; ++i) u[i] = (double)h[N + i];
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f) {
+    if (!c || !f) return fail(c, LBM_ERR_ARG, "NULL argument");
+    const size_t N = (size_t)c->p.n;
+    std::vector<char> raw(c->elem * c->p.q * N);
+    CK(c, cudaMemcpyAsync(raw.data(), c->L.f[c->cur], raw.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (c->p.storage == LBM_STORAGE_FP16) widen<__half>(raw, c->p.dim, c->p.q, N, f);
+    else if (c->p.storage == LBM_STORAGE_BF16) widen<__nv_bfloat16>(raw, c->p.dim, c->p.q, N, f);
+    else widen<float>(raw, c->p.dim, c->p.q, N, f);
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f) {
+    if (!c || !f) return fail(c, LBM_ERR_ARG, "NULL argument");
+    const size_t N = (size_t)c->p.n;
+    const int q = c->p.q;
+    std::vector<char> raw(c->elem * q * N);
+    for (int i = 0; i < q; ++i)
+        for (size_t n = 0; n < N; ++n) {
+            const double g = f[(size_t)i * N + n] - lat_w(c->p.dim, i);
+            const size_t k = (size_t)i * N + n;
+            if (c->p.storage == LBM_STORAGE_FP16) ((__half*)raw.data())[k] = __float2half_rn((float)g);
+            else if (c->p.storage == LBM_STORAGE_BF16) ((__nv_bfloat16*)raw.data())[k] = __float2bfloat16_rn((float)g);
+            else ((float*)raw.data())[k] = (float)g;
+        }
+    CK(c, cudaMemcpyAsync(c->L.f[c->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice, c->stream));
+    return sync_check(c);
+}
+
+int lbm_get_profile(lbm_ctx* c, double* prof, int64_t* nsteps) {
+    if (!c || !prof || !nsteps) return fail(c, LBM_ERR_ARG, "NULL argument");
+    *nsteps = 0;
+    if (!c->L.profile) {
+        memset(prof, 0, sizeof(double) * c->p.ny);
+        return LBM_OK;
+    }
+    DevState st;
+    CK(c, cudaMemcpyAsync(prof, c->L.profile, sizeof(double) * c->p.ny, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&st, c->L.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *nsteps = st.prof_steps;
+    return LBM_OK;
+}
+
+int lbm_get_step(lbm_ctx* c, int64_t* step) {
+    if (!c || !step) return fail(c, LBM_ERR_ARG, "NULL argument");
+    DevState st;
+    CK(c, cudaMemcpyAsync(&st, c->L.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *step = st.step;
+    return LBM_OK;
+}
+
+int lbm_state_bytes(lbm_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(c, LBM_ERR_ARG, "NULL argument");
+    BlobHead h;
+    blob_sizes(c, &h);
+    *bytes = sizeof h + sizeof(DevState) + h.fbytes + 2 * h.hbytes + h.rbytes + h.pbytes;
+    return LBM_OK;
+}
+
+int lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
+    size_t need = 0;
+    int rc = lbm_state_bytes(c, &need);
+    if (rc) return rc;
+    if (!buf || bytes < need) return fail(c, LBM_ERR_ARG, "checkpoint buffer too small (%zu < %zu)", bytes, need);
+    BlobHead h;
+    blob_sizes(c, &h);
+    char* o = (char*)buf;
+    memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    CK(c, cudaMemcpyAsync(o, c->L.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    o += sizeof(DevState);
+    CK(c, cudaMemcpyAsync(o, c->L.f[c->cur], h.fbytes, cudaMemcpyDeviceToHost, c->stream));
+    o += h.fbytes;
+    if (h.hbytes) {
+        CK(c, cudaMemcpyAsync(o, c->L.qh, h.hbytes, cudaMemcpyDeviceToHost, c->stream));
+        o += h.hbytes;
+        CK(c, cudaMemcpyAsync(o, c->L.qsh, h.hbytes, cudaMemcpyDeviceToHost, c->stream));
+        o += h.hbytes;
+    }
+    if (h.rbytes) {
+        CK(c, cudaMemcpyAsync(o, c->L.ring, h.rbytes, cudaMemcpyDeviceToHost, c->stream));
+        o += h.rbytes;
+    }
+    if (h.pbytes) CK(c, cudaMemcpyAsync(o, c->L.profile, h.pbytes, cudaMemcpyDeviceToHost, c->stream));
+    return sync_check(c);
+}
+
+int lbm_load(lbm_ctx* c, const void* buf, size_t bytes) {
+    size_t need = 0;
+    int rc = lbm_state_bytes(c, &need);
+    if (rc) return rc;
+    if (!buf || bytes < need) return fail(c, LBM_ERR_ARG, "checkpoint buffer too small");
+    BlobHead h, mine;
+    memcpy(&h, buf, sizeof h);
+    blob_sizes(c, &mine);
+    if (h.magic != kMagic || h.fbytes != mine.fbytes || h.hbytes != mine.hbytes || h.rbytes != mine.rbytes ||
+        h.pbytes != mine.pbytes)
+        return fail(c, LBM_ERR_ARG, "checkpoint does not match this configuration");
+    const char* o = (const char*)buf + sizeof h;
+    CK(c, cudaMemcpyAsync(c->L.st, o, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+    o += sizeof(DevState);
+    c->cur = 0;
+    CK(c, cudaMemcpyAsync(c->L.f[0], o, h.fbytes, cudaMemcpyHostToDevice, c->stream));
+    o += h.fbytes;
+    if (h.hbytes) {
+        CK(c, cudaMemcpyAsync(c->L.qh, o, h.hbytes, cudaMemcpyHostToDevice, c->stream));
+        o += h.hbytes;
+        CK(c, cudaMemcpyAsync(c->L.qsh, o, h.hbytes, cudaMemcpyHostToDevice, c->stream));
+        o += h.hbytes;
+    }
+    if (h.rbytes) {
+        CK(c, cudaMemcpyAsync(c->L.ring, o, h.rbytes, cudaMemcpyHostToDevice, c->stream));
+        o += h.rbytes;
+    }
+    if (h.pbytes) CK(c, cudaMemcpyAsync(c->L.profile, o, h.pbytes, cudaMemcpyHostToDevice, c->stream));
+    c->host_read = h.host_read;
+    c->lrs_set = c->lrs_set || c->p.h > 0;
+    return sync_check(c);
+}
+
+int lbm_set_graphs(lbm_ctx* c, int enable) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    c->use_graphs = enable ? 1 : 0;
+    return LBM_OK;
+}
+
+int lbm_profile(lbm_ctx* c, int enable) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    c->profiling = enable ? 1 : 0;
+    for (int k = 0; k < LBM_K_COUNT; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+    }
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx* c, double* ms, int64_t* launches, int count) {
+    if (!c || !ms || !launches) return fail(c, LBM_ERR_ARG, "NULL argument");
+    for (int k = 0; k < count && k < LBM_K_COUNT; ++k) {
+        ms[k] = c->prof_ms[k];
+        launches[k] = c->prof_n[k];
+    }
+    return LBM_OK;
+}
+
+int lbm_launches_per_step(lbm_ctx* c, int64_t* launches) {
+    if (!c || !launches) return fail(c, LBM_ERR_ARG, "NULL argument");
+    *launches = c->launches_per_step;
+    return LBM_OK;
+}
+
+}  // extern "C"

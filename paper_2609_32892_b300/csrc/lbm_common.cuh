@@ -1,0 +1,98 @@
+// Internal declarations shared by the library's CUDA sources.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int kMaxQoi = LBM_MAX_QOI;
+constexpr int kMaxTaps = 64;     // longest 1-D filter pass (L_s arm: 5 s taps)
+constexpr int kMaxFilters = 8;   // distinct (filter, scale) pairs per run
+
+// Device-resident counters and status of one simulation.
+struct DevState {
+    long long step;        // steps completed
+    long long hist_pos;    // LRS history pushes so far
+    long long ring_count;  // QoI rows written so far
+    long long prof_steps;  // steps summed into the mean profile
+    unsigned int status;   // bit 0: unstable seen
+    unsigned int pad[3];
+};
+
+// One 1-D convolution pass along an axis (0 = x, 1 = y, 2 = z).
+struct Taps {
+    int radius;     // taps at offsets -radius..radius
+    float t[kMaxTaps];
+};
+
+// Pointers into the caller's buffer, computed once at create time.
+struct Layout {
+    void* f[2];          // shifted populations, ping-pong
+    float* rho;          // [N]     density of the predictor state
+    float* vps;          // [d][N]  predictor velocity v^{p*} (aliases x6)
+    float* vn;           // [3][N]  post-stream velocity (WALE gradients)
+    float* kolmo;        // [ny]    Kolmogorov force profile
+    float* x6;           // [ncomp][N] stacked (v, omega) filter input
+    float* t1;           // [6][N]  pass scratch
+    float* t2;           // [6][N]  pass scratch
+    float* acc;          // [6][N]  R applied once
+    float* rr[kMaxFilters];  // [6][N] R R (v, omega) per filter
+    float* vz[kMaxFilters];  // [3][N] curl*(R R omega) per filter
+    double* part;        // [nblk_red][npart] reduction partials
+    double* plane_part;  // [nzc][ny][1 + n_s] plane-sum partials
+    double* plane_sum;   // [ny][1 + n_s] plane sums of v_x and V_k,x
+    double* red_out;     // [npart] reduced partials (diagnostics)
+    double* lrs_part;    // [nblk_lrs][N_Q] LRS history matvec partials
+    double* lrs_C;       // [(2h+1)N + 1][N]
+    double* lrs_mu;      // [N]
+    double* lrs_L;       // [N][N] Cholesky factor of Sigma
+    double* lrs_sigma;   // [N]
+    double* qh;          // [h][N] corrected-QoI ring
+    double* qsh;         // [h][N] predictor-QoI ring
+    double* track;       // [track_len][N]
+    double* w_mp;        // [n_mp][ny] band weights
+    double* g_mpmp;      // [n_mp][n_mp]
+    double* beta;        // [N_Q] SGS coefficients of the current step (beta = G^-1 dQ)
+    double* ring;        // [ring_cap][row_len]
+    double* profile;     // [ny]
+    DevState* st;
+};
+
+struct Params {
+    int dim, q, nx, ny, nz, walls, forcing, substrate, storage, to_mode;
+    long long n;         // nodes
+    float tau, body[3], kolmo_drag, c_smag2, c_wale2;
+    int n_s, n_mp, n_q;  // scale QoIs, bands, total
+    int qoi_kind[kMaxQoi];
+    int qoi_filter_slot[kMaxQoi];  // which distinct filter each scale QoI uses
+    int n_filters;
+    int ncomp;           // components filtered: 3 (2-D: vx, vy, w) or 6 (3-D)
+    int h, ring_cap, row_len;
+    long long track_len;
+    double gamma_std;
+    unsigned long long seed, member;
+    int nblk_red, nzc, npart, nblk_lrs, lrs_rows_per_blk;
+};
+
+// ---- launchers (stream-ordered; return cudaGetLastError()) ----
+cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* rho, const float* u, int which,
+                            cudaStream_t s);
+cudaError_t launch_moments(const Params& p, const Layout& L, int src, cudaStream_t s);
+cudaError_t launch_collide(const Params& p, const Layout& L, int src, cudaStream_t s);
+cudaError_t launch_apply(const Params& p, const Layout& L, int dst, cudaStream_t s);
+cudaError_t launch_to_curl(const Params& p, const Layout& L, cudaStream_t s);
+cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t,
+                        float scale, int accumulate, cudaStream_t s);
+cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s);
+cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* vk, cudaStream_t s);
+cudaError_t launch_lrs_hist(const Params& p, const Layout& L, cudaStream_t s);
+cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s);
+cudaError_t launch_macros(const Params& p, const Layout& L, int which, float* drho_out, float* u_out,
+                          cudaStream_t s);
+
+}  // namespace lbm

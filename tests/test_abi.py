@@ -1,0 +1,60 @@
+"""The C ABI without a GPU: the library loads, exports every symbol the
+header declares, the ctypes struct matches the C layout, and configuration
+errors come back as status codes with a reason."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import synthetic
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2609_32892_b300 import build
+
+    build.build()
+    from paper_2609_32892_b300 import binding
+
+    return binding
+
+
+def test_exports_every_declared_symbol(B, root):
+    hdr = open(os.path.join(root, "include", "lbm.h")).read()
+    declared = sorted(set(re.findall(r"^int (lbm_\w+)\(", hdr, flags=re.M)))
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = sorted(set(re.findall(r" T (lbm_\w+)$", out, flags=re.M)))
+    assert declared == exported
+    assert sorted(B.EXPORTED) == declared
+
+
+def test_struct_layout_matches_c(B, root, tmp_path):
+    fields = [f for f, _ in B.lbm_config._fields_]
+    src = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{root}/include/lbm.h"', "int main(void){",
+           'printf("%zu\\n", sizeof(lbm_config));']
+    src += [f'printf("%zu\\n", offsetof(lbm_config, {f}));' for f in fields]
+    src += ["return 0;}"]
+    (tmp_path / "l.c").write_text("\n".join(src))
+    subprocess.run(["gcc", "-o", str(tmp_path / "l"), str(tmp_path / "l.c")], check=True)
+    vals = [int(v) for v in subprocess.run([str(tmp_path / "l")], capture_output=True, text=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(B.lbm_config)
+    for f, off in zip(fields, vals[1:]):
+        assert getattr(B.lbm_config, f).offset == off, f
+
+
+def test_required_bytes_and_config_errors(B):
+    for name in ("C1", "C2", "C3", "C4", "C4_TO"):
+        cfg = B.config_from_workload(synthetic.workload(name))
+        assert B.lbm_required_bytes(cfg) > 0
+    bad = B.config_from_workload(synthetic.workload("C1", tau=0.5))
+    with pytest.raises(B.LbmError) as e:
+        B.lbm_required_bytes(bad)
+    assert e.value.code == B.LBM_ERR_ARG and "tau" in str(e.value)
+    bad = B.config_from_workload(synthetic.workload("C2", n_mp=6))
+    with pytest.raises(B.LbmError):
+        B.lbm_required_bytes(bad)
+    cfg = B.config_from_workload(synthetic.workload("C3"))
+    assert B.lbm_qoi_row_len(cfg) == 2 + 3 * 12

@@ -1,0 +1,89 @@
+"""Checks at the benchmark sizes (480x200x240 D3Q19 channel), in the launch
+configuration the benchmark times (two steps per CUDA-graph replay).
+
+The oracle cannot step the whole 23-million-node grid in seconds, but after
+two steps a population column depends only on a few neighbouring columns.
+So the oracle steps small windows (all ny rows, so the walls are exact; a few
+columns in x and z, periodic in the global grid) built from the same seeded
+initial field, and the centre column is compared population by population.
+The full TO-LRS step couples the whole grid through its QoIs; at full size it
+is checked through properties that hold at any size: mass conservation,
+finite, non-singular QoI rows, and the QoI/Gram invariants."""
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle.sim import Simulation
+
+pytestmark = pytest.mark.gpu
+
+W = 9  # window width in x and z: two steps of pull + WALE gradients reach 4 columns
+
+
+def _window_u0(u0, x0, z0):
+    nz, nx = u0.shape[1], u0.shape[3]
+    xs = [(x0 + d) % nx for d in range(-(W // 2), W // 2 + 1)]
+    zs = [(z0 + d) % nz for d in range(-(W // 2), W // 2 + 1)]
+    return u0[:, zs][:, :, :, xs]
+
+
+@pytest.mark.parametrize("name,substrate", [("C4", "none"), ("C4", "wale")])
+def test_full_grid_two_steps_sampled_columns(name, substrate):
+    from paper_2609_32892_b300 import LbmSim
+
+    wl = synthetic.workload(name, substrate=substrate, c_wale=2.2)
+    u0 = synthetic.initial_velocity(wl)
+    g = LbmSim(wl)
+    g.init(u0)
+    g.step(2)
+    g.sync()
+    f = g.populations()
+    g.close()
+    rng = np.random.default_rng(7)
+    cols = [(0, 0), (wl["nx"] - 1, wl["nz"] - 1)] + [(int(a), int(b)) for a, b in
+                                                      zip(rng.integers(0, wl["nx"], 6), rng.integers(0, wl["nz"], 6))]
+    for x0, z0 in cols:
+        ww = dict(wl, nx=W, nz=W)
+        o = Simulation(ww, _window_u0(u0, x0, z0))
+        o.run(2)
+        c = W // 2
+        fo = o.fp[:, c, :, c]
+        fg = f[:, z0, :, x0]
+        w = o.lat.w[:, None]
+        dev_o, dev_g = fo - w, fg - w
+        err = np.linalg.norm(dev_g - dev_o) / np.linalg.norm(dev_o)
+        assert err < 1e-6, (x0, z0, err)
+
+
+def test_full_grid_to_lrs_step_properties():
+    """The benchmark's step (WALE + TO-LRS with 12 QoIs, h = 500) at full size:
+    mass is conserved, QoI rows are finite and non-singular, q^{n*} of the
+    energies is positive, and steps are counted."""
+    from paper_2609_32892_b300 import LbmSim
+
+    wl = synthetic.workload("C4_TO")
+    nq = len(wl["qois"]) + wl["n_mp"]
+    c, mu, sig = synthetic.synthetic_lrs(nq, wl["h"], wl["seed"])
+    g = LbmSim(wl)
+    g.init(synthetic.initial_velocity(wl))
+    g.set_lrs(c, mu, sig, np.ones(nq))
+    rho0, _ = g.macros()
+    m = np.ones_like(rho0)
+    m[:, 0, :] = 0
+    m[:, -1, :] = 0
+    mass0 = (rho0 * m).sum()
+    g.step(4)
+    g.sync()
+    rows = g.qoi()
+    rho1, u1 = g.macros()
+    from paper_2609_32892_b300 import binding as B
+
+    assert B.lbm_get_step(g.ctx) == 4
+    g.close()
+    assert rows.shape == (4, 2 + 3 * nq)
+    assert np.all(np.isfinite(rows))
+    assert np.all(rows[:, -1] == 0)
+    assert np.all(rows[:, 1:1 + 6:2] > 0)  # E_G3, E_L3, E_L1
+    assert abs((rho1 * m).sum() - mass0) / mass0 < 1e-6
+    assert np.all(np.isfinite(u1))

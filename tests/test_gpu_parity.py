@@ -1,0 +1,168 @@
+"""Element-wise parity of the CUDA library (through the C ABI) with the FP64
+oracle on seeded inputs.
+
+Tolerances (FP32 arithmetic against FP64):
+  * rel-L2 of rho and of u over fluid nodes: <= 1e-5 (the FP32 target after
+    1000 steps);
+  * rho - 1 (the density deviation, ~1e-5 in the Kolmogorov runs): FP32
+    resolves it only to its own rounding, ~1e-9 per step and node, so the
+    bound is absolute, max |rho_gpu - rho_oracle| <= 1e-6 for runs of up to
+    1000 steps; rel-L2(rho - 1) is reported in the assertion messages;
+  * QoIs q^{n*}: relative 1e-4 each (FP32 products summed in FP64);
+  * dQ and gamma: dQ is a difference involving q^{n*}, so its error is
+    bounded by 1e-4 |q^{n*}| plus 2e-3 max|dQ| (G^-1 amplifies the ~1e-6
+    relative FP32 error of the Gram entries by its condition number, ~1e2-1e3
+    here); gamma = dQ (G^-1)_ii inherits both terms;
+  * Philox normals: bit-exact (gamma = gamma_std * z in FP64 on both sides);
+  * flags: identical.
+Grid sizes are ragged (no dimension a multiple of the 256-thread block or the
+32-wide warp) and span several thread blocks.
+"""
+
+import numpy as np
+import pytest
+
+import synthetic
+from gpu_common import fluid_mask, lrs_inputs, nq_of, oracle_sigma_ref, rel_l2, run_gpu, run_oracle
+from oracle import philox
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare_state(wl, rho_g, u_g, rho_o, u_o, tol=1e-5, rho_abs=1e-6):
+    m = fluid_mask(wl)
+    e_rho = rel_l2(rho_g, rho_o, m)
+    e_dev = rel_l2(rho_g - 1.0, rho_o - 1.0, m)
+    d_abs = float(np.max(np.abs(rho_g - rho_o) * m))
+    e_u = rel_l2(u_g, u_o, m)
+    msg = f"rel-L2(rho) = {e_rho:.3e}, rel-L2(rho-1) = {e_dev:.3e}, max|drho| = {d_abs:.3e}, rel-L2(u) = {e_u:.3e}"
+    assert e_rho <= tol, msg
+    assert d_abs <= rho_abs, msg
+    assert e_u <= tol, msg
+    return e_rho, e_u
+
+
+def _compare_rows(wl, rg, ro, qtol=1e-4, dtol=2e-3):
+    nq = nq_of(wl)
+    assert rg.shape == ro.shape, (rg.shape, ro.shape)
+    np.testing.assert_array_equal(rg[:, 0], ro[:, 0])
+    np.testing.assert_array_equal(rg[:, -1], ro[:, -1])
+    q_g, q_o = rg[:, 1:1 + nq], ro[:, 1:1 + nq]
+    np.testing.assert_allclose(q_g, q_o, rtol=qtol, atol=1e-30)
+    dq_g, dq_o = rg[:, 1 + nq:1 + 2 * nq], ro[:, 1 + nq:1 + 2 * nq]
+    g_g, g_o = rg[:, 1 + 2 * nq:1 + 3 * nq], ro[:, 1 + 2 * nq:1 + 3 * nq]
+    allow_dq = qtol * np.abs(q_o) + dtol * np.abs(dq_o).max(axis=0, keepdims=True)
+    bad = np.abs(dq_g - dq_o) > allow_dq
+    assert not bad.any(), f"dQ: {np.abs(dq_g - dq_o)[bad][:4]} > {allow_dq[bad][:4]}"
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ginv = np.where(dq_o != 0, np.abs(g_o / dq_o), 0.0)
+    allow_g = qtol * np.abs(q_o) * ginv + dtol * np.abs(g_o).max(axis=0, keepdims=True)
+    bad = np.abs(g_g - g_o) > allow_g
+    assert not bad.any(), f"gamma: {np.abs(g_g - g_o)[bad][:4]} > {allow_g[bad][:4]}"
+
+
+@pytest.mark.parametrize("forcing", ["guo", "edm"])
+def test_kolmogorov_gamma_2d(forcing):
+    """64^2 Kolmogorov workload shape (2-D, binomial E/Z patterns, random
+    gamma) on a ragged 37x29 grid, 120 steps."""
+    wl = synthetic.workload("C1", nx=37, ny=29, forcing=forcing)
+    _, ro, rho_o, u_o = run_oracle(wl, 120)
+    _, rg, rho_g, u_g = run_gpu(wl, 120)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)
+    # the random stream is bit-exact: gamma = gamma_std * z
+    nq = nq_of(wl)
+    for r in rg[:5]:
+        z = philox.normals(wl["seed"], 0, int(r[0]), philox.STREAM_GAMMA, nq)
+        assert list(r[1 + 2 * nq:1 + 3 * nq]) == [wl["gamma_std"] * zz for zz in z]
+
+
+def test_kolmogorov_smagorinsky_lrs_2d():
+    """256^2 Kolmogorov LES shape (Smagorinsky + TO-LRS, 4 QoIs G3/L1, drag)
+    on a ragged 41x35 grid with h = 3, 40 steps."""
+    wl = synthetic.workload("C2", nx=41, ny=35, h=3)
+    lrs = lrs_inputs(wl, oracle_sigma_ref(wl))
+    _, ro, rho_o, u_o = run_oracle(wl, 40, lrs=lrs)
+    _, rg, rho_g, u_g = run_gpu(wl, 40, lrs=lrs)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)
+
+
+def test_channel_wale_lrs_3d():
+    """96x40x48 channel shape (WALE + TO-LRS, 12 QoIs with 6 mean-profile
+    bands, walls) on a ragged 19x22x13 grid with h = 2, 6 steps."""
+    wl = synthetic.workload("C3", nx=19, ny=22, nz=13, h=2)
+    lrs = lrs_inputs(wl, oracle_sigma_ref(wl, 2))
+    _, ro, rho_o, u_o = run_oracle(wl, 6, lrs=lrs)
+    _, rg, rho_g, u_g = run_gpu(wl, 6, lrs=lrs)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)
+
+
+def test_channel_bgk_3d_long():
+    """Plain BGK channel (the 480x200x240 workload's physics) on 33x18x11,
+    300 steps: the pure stream-collide path."""
+    wl = synthetic.workload("C4", nx=33, ny=18, nz=11)
+    _, _, rho_o, u_o = run_oracle(wl, 300)
+    _, _, rho_g, u_g = run_gpu(wl, 300)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+
+
+def test_kolmogorov_1000_steps_full_grid():
+    """The 64^2 Kolmogorov workload itself (Guo forcing, binomial E/Z
+    patterns, random gamma), FP32 against FP64 for 1000 steps."""
+    wl = synthetic.workload("C1", steps=1000)
+    _, ro, rho_o, u_o = run_oracle(wl, 1000)
+    _, rg, rho_g, u_g = run_gpu(wl, 1000)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro, qtol=2e-4)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 3e-3), ("bf16", 3e-2)])
+def test_reduced_precision_storage(storage, tol):
+    """Shifted FP16/BF16 population storage with FP32 arithmetic, against the
+    FP64 oracle: rel-L2 of u within the storage precision (fp16 11-bit,
+    bf16 8-bit significands of f - w)."""
+    wl = synthetic.workload("C4", nx=33, ny=18, nz=11, storage=storage)
+    _, _, rho_o, u_o = run_oracle(wl, 100)
+    _, _, rho_g, u_g = run_gpu(wl, 100)
+    m = fluid_mask(wl)
+    assert rel_l2(u_g, u_o, m) <= tol
+
+
+def test_observe_mode_and_tracking():
+    """Observe mode reports q^{n*} without forcing; tracking with the observed
+    series as reference gives dQ = 0 (the state then follows the observed run)."""
+    wl = synthetic.workload("C2", nx=30, ny=26, to_mode="observe")
+    _, ro, rho_o, u_o = run_oracle(wl, 20)
+    _, rg, rho_g, u_g = run_gpu(wl, 20)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)
+    nq = nq_of(wl)
+    ref = ro[:, 1:1 + nq] * (1.0 + 1e-4)
+    wt = dict(wl, to_mode="track", track_len=len(ref))
+    _, rot, rho_ot, u_ot = run_oracle(wt, 20, track=ref)
+    _, rgt, rho_gt, u_gt = run_gpu(wt, 20, track=ref)
+    _compare_state(wt, rho_gt, u_gt, rho_ot, u_ot)
+    _compare_rows(wt, rgt, rot)
+
+
+def test_rest_state_and_singular_gram():
+    """At rest the sensitivities vanish: every step is flagged singular, the
+    SGS step is skipped and the state stays at rest."""
+    wl = synthetic.workload("C3", nx=12, ny=16, nz=5, h=2, body_force=(0.0, 0.0, 0.0), init=("rest",))
+    lrs = lrs_inputs(wl, np.ones(nq_of(wl)))
+    _, rg, rho_g, u_g = run_gpu(wl, 4, lrs=lrs)
+    assert np.all(rg[:, -1] == 1)
+    assert np.max(np.abs(u_g)) == 0.0
+    assert np.max(np.abs(rho_g - 1.0)) == 0.0
+
+
+def test_graph_replay_equals_eager_launches():
+    wl = synthetic.workload("C2", nx=40, ny=34, h=3)
+    lrs = lrs_inputs(wl, np.ones(nq_of(wl)))
+    _, ra, rho_a, u_a = run_gpu(wl, 9, lrs=lrs, graphs=True, chunks=[4, 5])
+    _, rb, rho_b, u_b = run_gpu(wl, 9, lrs=lrs, graphs=False)
+    np.testing.assert_array_equal(ra, rb)
+    np.testing.assert_array_equal(u_a, u_b)
+    np.testing.assert_array_equal(rho_a, rho_b)

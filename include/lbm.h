@@ -210,6 +210,41 @@ int lbm_profile_read(lbm_ctx* ctx, double* ms, int64_t* launches, int count);
 /* Kernel launches one lbm_step(ctx, 1) queues (for launch accounting). */
 int lbm_launches_per_step(lbm_ctx* ctx, int64_t* launches);
 
+/* QoIs of a velocity field, for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc or hand the library a buffer: code that runs
+ * while a CUDA graph is being captured, code embedded in a host framework
+ * that owns every device allocation through its own arena, and real-time
+ * loops that cannot afford the implicit device synchronisation of an
+ * allocation.  It computes the same scale-aware QoIs as the TO phase of
+ * lbm_step (q_i = E_R or Z_R of Sec. 4.1 for each cfg->qoi[i]) for a field
+ * the caller supplies, using only a scratch array compiled into the library.
+ *
+ *   cfg     grid (dim, nx, ny, nz, walls) and the scale-aware QoIs
+ *           (n_qoi >= 1, qoi[]); mean-profile bands are not supported
+ *           (n_mp must be 0); to_mode and the LBM fields are ignored
+ *   u       device pointer, FP32 velocity [3][nz][ny][nx] (z component
+ *           ignored in 2-D); values on solid rows are treated as zero
+ *   q       device pointer, receives n_qoi doubles
+ *   stream  cudaStream_t the work is queued on (asynchronous)
+ *
+ * Scratch: one file-scope device array of LBM_STATIC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.  The grid and QoI
+ * set must fit in it (about 200 bytes per node for six 3-D QoIs over three
+ * filters); larger requests return LBM_ERR_BUDGET and say how many bytes they
+ * would need.  Nothing is allocated: no cudaMalloc, no cudaFree, no
+ * allocating library call.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress with that device current);
+ * make that first call before any stream capture begins.  Every call shares
+ * the one array and it keeps the previous call's contents, so calls whose
+ * work overlaps on the GPU (other streams, other host threads) race with
+ * each other; serialise them.
+ * Errors: LBM_ERR_ARG (invalid grid or QoI set), LBM_ERR_BUDGET (too large
+ * for the scratch), LBM_ERR_CUDA; the text is lbm_last_error(NULL, ...). */
+#define LBM_STATIC_SCRATCH_BYTES (64u << 20)
+int lbm_qoi_eval_static(const lbm_config* cfg, const float* u, double* q, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,7 @@ EXPORTED = [
     "lbm_set_lrs", "lbm_set_track_reference", "lbm_step", "lbm_sync", "lbm_qoi", "lbm_get_macros",
     "lbm_get_populations", "lbm_set_populations", "lbm_get_profile", "lbm_get_step", "lbm_state_bytes",
     "lbm_save", "lbm_load", "lbm_set_graphs", "lbm_profile", "lbm_profile_read", "lbm_launches_per_step",
+    "lbm_qoi_eval_static",
 ]
 
 
@@ -78,6 +79,7 @@ def _load():
         "lbm_profile": [VP, C.c_int],
         "lbm_profile_read": [VP, PD, PI64, C.c_int],
         "lbm_launches_per_step": [VP, PI64],
+        "lbm_qoi_eval_static": [cfg, VP, VP, VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -267,3 +269,10 @@ def lbm_launches_per_step(ctx):
     n = C.c_int64()
     _check(_lib.lbm_launches_per_step(ctx, C.byref(n)), ctx)
     return n.value
+
+
+def lbm_qoi_eval_static(cfg, u_dev_ptr, q_dev_ptr, stream_ptr):
+    """Scale-aware QoIs of a device velocity field using only the library's
+    built-in scratch array (for callers that cannot allocate device memory)."""
+    _check(_lib.lbm_qoi_eval_static(C.byref(cfg), C.c_void_p(u_dev_ptr), C.c_void_p(q_dev_ptr),
+                                    C.c_void_p(stream_ptr)))

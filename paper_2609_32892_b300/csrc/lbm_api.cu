@@ -62,6 +62,11 @@ static int fail(lbm_ctx* c, int code, const char* fmt, ...) {
     return code;
 }
 
+namespace lbm {
+// Record a message as the thread's last error (lbm_last_error(NULL, ...)).
+void set_global_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace lbm
+
 #define CK(c, call)                                                                         \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \

@@ -95,4 +95,6 @@ cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s);
 cudaError_t launch_macros(const Params& p, const Layout& L, int which, float* drho_out, float* u_out,
                           cudaStream_t s);
 
+void set_global_error(const char* msg);
+
 }  // namespace lbm

@@ -1,0 +1,159 @@
+// Fast 1-D filter passes (one separable factor of G_s, L_s or B3, Sec. 4.1).
+//
+// Strided axes (y, z): each thread owns a segment of one line along the axis
+// and marches along it with a register window of 2R+1 values per component,
+// so every input element is loaded once per segment (plus a 2R halo) and all
+// loads of a warp are coalesced (consecutive threads = consecutive x).
+// Contiguous axis (x): one block stages a row chunk plus halo of every
+// component in shared memory with coalesced loads and convolves from there.
+// Both handle periodic wrap of any length and, along y with walls, the zero
+// extension beyond the array with zero output on solid rows.
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+template <int R> struct TapsR {
+    float t[2 * R + 1];
+};
+
+__device__ __forceinline__ int posmod(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+template <int R, int NC>
+__global__ void __launch_bounds__(128) march_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                    int axis, TapsR<R> tp, float scale, int accumulate, int seg) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int other = axis == 1 ? nz : ny;
+    const int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nx * other) return;
+    const int x = line % nx;
+    const int o = line / nx;
+    const int L = axis == 1 ? ny : nz;
+    const size_t stride = axis == 1 ? (size_t)nx : (size_t)nx * ny;
+    const size_t base = axis == 1 ? (size_t)o * ny * nx + x : (size_t)o * nx + x;
+    const size_t N = (size_t)p.n;
+    const bool zero_pad = axis == 1 && p.walls;
+    const int p0 = blockIdx.y * seg;
+    const int p1 = min(L, p0 + seg);
+    if (p0 >= L) return;
+    float w[NC][2 * R + 1];
+    // prologue: positions p0-R .. p0+R-1 into slots 0 .. 2R-1
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) {
+        const int q = p0 - R + k;
+        bool ok = true;
+        int qq = q;
+        if (zero_pad) ok = (q >= 0 && q < L);
+        else qq = posmod(q, L);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) w[c][k] = ok ? __ldg(in + c * N + base + (size_t)qq * stride) : 0.f;
+    }
+    for (int pos = p0; pos < p1; ++pos) {
+        const int q = pos + R;
+        bool ok = true;
+        int qq = q;
+        if (zero_pad) ok = q < L;
+        else qq = posmod(q, L);
+        const bool solid = p.walls && axis == 1 && (pos == 0 || pos == L - 1);
+        const bool solid_row = p.walls && axis == 2 && (o == 0 || o == ny - 1);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            w[c][2 * R] = ok ? __ldg(in + c * N + base + (size_t)qq * stride) : 0.f;
+            // out(pos) = sum_r t(r) in(pos - r); slot k holds in(pos - R + k)
+            float s = 0.f;
+#pragma unroll
+            for (int r = -R; r <= R; ++r) s += tp.t[r + R] * w[c][R - r];
+            float* op = out + c * N + base + (size_t)pos * stride;
+            const float v = (solid || solid_row) ? 0.f : scale * s;
+            *op = accumulate ? (*op + v) : v;
+#pragma unroll
+            for (int k = 0; k < 2 * R; ++k) w[c][k] = w[c][k + 1];
+        }
+    }
+}
+
+constexpr int kTX = 128;
+
+template <int R, int NC>
+__global__ void __launch_bounds__(kTX) xpass_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                    TapsR<R> tp, float scale, int accumulate) {
+    __shared__ float sm[NC][kTX + 2 * R];
+    const int nx = p.nx, ny = p.ny;
+    const int row = blockIdx.y;  // z * ny + y
+    const int y = row % ny;
+    const int x0 = blockIdx.x * kTX;
+    const size_t N = (size_t)p.n;
+    const size_t rbase = (size_t)row * nx;
+    const int x = x0 + threadIdx.x;
+    if (p.walls && (y == 0 || y == ny - 1)) {
+        if (x < nx)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) out[c * N + rbase + x] = 0.f;
+        return;
+    }
+    for (int i = threadIdx.x; i < NC * (kTX + 2 * R); i += kTX) {
+        const int c = i / (kTX + 2 * R), k = i % (kTX + 2 * R);
+        const int xs = posmod(x0 - R + k, nx);
+        sm[c][k] = __ldg(in + c * N + rbase + xs);
+    }
+    __syncthreads();
+    if (x >= nx) return;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        float s = 0.f;
+#pragma unroll
+        for (int r = -R; r <= R; ++r) s += tp.t[r + R] * sm[c][threadIdx.x + R - r];
+        float* op = out + c * N + rbase + x;
+        const float v = scale * s;
+        *op = accumulate ? (*op + v) : v;
+    }
+}
+
+template <int R, int NC>
+static cudaError_t run(const Params& p, const float* in, float* out, int axis, const Taps& t, float scale,
+                       int accumulate, cudaStream_t s) {
+    TapsR<R> tr;
+    for (int i = 0; i < 2 * R + 1; ++i) tr.t[i] = t.t[i];
+    if (axis == 0) {
+        dim3 grid((p.nx + kTX - 1) / kTX, p.ny * p.nz);
+        xpass_kernel<R, NC><<<grid, kTX, 0, s>>>(p, in, out, tr, scale, accumulate);
+    } else {
+        const int L = axis == 1 ? p.ny : p.nz;
+        const int lines = p.nx * (axis == 1 ? p.nz : p.ny);
+        // split lines into segments so that ~4 warps per SM-slot are in flight
+        int nseg = (int)((148LL * 2048 + lines - 1) / lines);
+        if (nseg < 1) nseg = 1;
+        int seg = (L + nseg - 1) / nseg;
+        if (seg < 4 * R) seg = 4 * R;
+        if (seg > L) seg = L;
+        nseg = (L + seg - 1) / seg;
+        dim3 grid((lines + 127) / 128, nseg);
+        march_kernel<R, NC><<<grid, 128, 0, s>>>(p, in, out, axis, tr, scale, accumulate, seg);
+    }
+    return cudaGetLastError();
+}
+
+// Returns cudaErrorNotSupported when no specialised instance exists.
+cudaError_t launch_pass_fast(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t,
+                             float scale, int accumulate, cudaStream_t s) {
+#define LBM_CASE(RR)                                                                  \
+    case RR:                                                                          \
+        if (ncomp == 3) return run<RR, 3>(p, in, out, axis, t, scale, accumulate, s); \
+        if (ncomp == 6) return run<RR, 6>(p, in, out, axis, t, scale, accumulate, s); \
+        break;
+    switch (t.radius) {
+        LBM_CASE(1)
+        LBM_CASE(2)
+        LBM_CASE(4)
+        LBM_CASE(6)
+        LBM_CASE(7)
+        LBM_CASE(12)
+        default: break;
+    }
+#undef LBM_CASE
+    return cudaErrorNotSupported;
+}
+
+}  // namespace lbm

@@ -256,7 +256,12 @@ __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restr
         const float cu = LT::cx(i) * ux + LT::cy(i) * uy + LT::cz(i) * uz;
         geq[i] = LT::w(i) * (m.drho + m.rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
     }
+    // Without a substrate 1/tau and 1 - 1/(2 tau) come rounded once from
+    // double: the viscosity depends on (1/omega - 1/2) and Guo's prefactor is
+    // a small difference, so FP32 recomputation would bias both by ~1e-6.
     float tau = p.tau;
+    float om = p.omega0;
+    float pre = p.guo_pre0;
     if (SUB == LBM_SUBSTRATE_SMAG) {
         // Pi^neq_ab = sum_i c_ia c_ib (f_i - f^eq_i); tau_eff closed form (Sec. 5.1)
         float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
@@ -276,11 +281,13 @@ __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restr
     } else if (SUB == LBM_SUBSTRATE_WALE) {
         tau = p.tau + 3.0f * wale_nut<DIM>(p, vn, x, y, z);
     }
-    const float om = 1.0f / tau;
+    if (SUB != LBM_SUBSTRATE_NONE) {
+        om = 1.0f / tau;
+        pre = (tau - 0.5f) * om;  // tau - 1/2 is exact in FP32 for tau in [1/2, 1]
+    }
 
     const float fx = m.fx, fy = m.fy, fz = m.fz;
     if (p.forcing == LBM_FORCING_GUO) {
-        const float pre = 1.0f - 0.5f * om;
 #pragma unroll
         for (int i = 0; i < LT::Q; ++i) {
             const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);

@@ -443,6 +443,8 @@ cudaError_t launch_to_curl(const Params& p, const Layout& L, cudaStream_t s) {
 }
 cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t, float scale,
                         int accumulate, cudaStream_t s) {
+    const cudaError_t e = launch_pass_fast(p, in, out, ncomp, axis, t, scale, accumulate, s);
+    if (e != cudaErrorNotSupported) return e;
     pass_kernel<<<gridn(p.n, 256), 256, 0, s>>>(p, in, out, ncomp, axis, t, scale, accumulate);
     return cudaGetLastError();
 }

@@ -159,6 +159,8 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     p->to_mode = c->to_mode;
     p->n = (long long)c->nx * c->ny * c->nz;
     p->tau = (float)c->tau;
+    p->omega0 = (float)(1.0 / c->tau);
+    p->guo_pre0 = (float)(1.0 - 0.5 / c->tau);
     for (int a = 0; a < 3; ++a) p->body[a] = (float)c->body_force[a];
     if (c->dim == 2) p->body[2] = 0.f;
     p->kolmo_drag = (float)c->kolmo_drag;
@@ -328,6 +330,20 @@ static void enqueue_filter(Launcher& lc, const Filter& f, const float* in, float
     const int d = p.dim;
     float* t1 = c->L.t1;
     float* t2 = c->L.t2;
+    if (d == 3) {
+        // fused 3-D kernels: the whole filter in one pass over the field
+        if (f.kind == LBM_FILTER_GAUSS || f.kind == LBM_FILTER_BINOMIAL) {
+            const Taps t = f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps();
+            if (launch_gauss3_supported(t.radius)) {
+                LAUNCH(lc, LBM_K_FILTER, launch_gauss3(p, in, out, nc, t, 1.f, 0, lc.s));
+                return;
+            }
+        } else if (launch_lap3_supported(f.scale)) {
+            const float scale = (float)(1.0 / (8.0 * d * (double)f.scale * f.scale * f.scale));
+            LAUNCH(lc, LBM_K_FILTER, launch_lap3(p, in, out, nc, f.scale, ell_taps(f.scale), scale, 0, lc.s));
+            return;
+        }
+    }
     if (f.kind == LBM_FILTER_GAUSS || f.kind == LBM_FILTER_BINOMIAL) {
         const Taps t = f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps();
         if (d == 2) {

@@ -67,6 +67,8 @@ struct Params {
     int dim, q, nx, ny, nz, walls, forcing, substrate, storage, to_mode;
     long long n;         // nodes
     float tau, body[3], kolmo_drag, c_smag2, c_wale2;
+    float omega0;        // 1/tau rounded once from double
+    float guo_pre0;      // 1 - 1/(2 tau) rounded once from double
     int n_s, n_mp, n_q;  // scale QoIs, bands, total
     int qoi_kind[kMaxQoi];
     int qoi_filter_slot[kMaxQoi];  // which distinct filter each scale QoI uses
@@ -88,6 +90,14 @@ cudaError_t launch_apply(const Params& p, const Layout& L, int dst, cudaStream_t
 cudaError_t launch_to_curl(const Params& p, const Layout& L, cudaStream_t s);
 cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t,
                         float scale, int accumulate, cudaStream_t s);
+cudaError_t launch_pass_fast(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t,
+                             float scale, int accumulate, cudaStream_t s);
+cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
+                          int accumulate, cudaStream_t s);
+cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp, int s_scale, const Taps& arm,
+                        float scale, int accumulate, cudaStream_t s);
+inline bool launch_gauss3_supported(int radius) { return radius == 1 || radius == 2 || radius == 4 || radius == 6; }
+inline bool launch_lap3_supported(int s_scale) { return s_scale == 1 || s_scale == 3; }
 cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s);
 cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* vk, cudaStream_t s);
 cudaError_t launch_lrs_hist(const Params& p, const Layout& L, cudaStream_t s);

@@ -44,6 +44,11 @@ def _peaks():
     return 6400.0, "fallback"
 
 
+# FP32 (non-tensor) arithmetic peak of one B300 from its unit counts and clock:
+# 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.032 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -188,6 +193,11 @@ def run_ours(args, world, rank, local):
             if k in algo:
                 ent["gbs"] = algo[k] / (tms / cnt * 1e-3) / 1e9
             sections[k] = ent
+    flops = B.lbm_filter_flops_per_step(sim.ctx)
+    for k in ("gauss3", "lap3"):
+        if k in sections and flops[k] > 0:
+            sections[k]["tflops"] = flops[k] / (sections[k]["ms_per_step"] * 1e-3) / 1e12
+            sections[k]["flops_per_step"] = flops[k]
     roof = None
     if dominant in algo:
         avg_ms = prof[dominant][0] / prof[dominant][1]
@@ -195,6 +205,16 @@ def run_ours(args, world, rank, local):
         roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_kind": peak_kind, "traffic": None,
                 "bytes_per_launch": algo[dominant], "avg_launch_ms": avg_ms}
+    elif dominant in ("gauss3", "lap3") and flops[dominant] > 0:
+        # the fused filters are issue/ALU bound: FP32 FLOP/s against the FP32 peak
+        tms, cnt = prof[dominant]
+        per_launch = flops[dominant] / (cnt / args.profile_steps)
+        ach = per_launch / (tms / cnt * 1e-3) / 1e12
+        roof = {"kernel": dominant, "bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
+                "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz", "traffic": None,
+                "flops_per_launch": per_launch, "avg_launch_ms": tms / cnt,
+                "hbm_gbs": round(n_nodes * 2 * 6 * 4 / (tms / cnt * 1e-3) / 1e9, 1)}
     coll = prof["collide"]
     coll_gbs = algo["collide"] / (coll[0] / coll[1] * 1e-3) / 1e9 if coll[1] else None
     step_gbs = n_nodes * (2 * (19 if wl["dim"] == 3 else 9) * (4 if wl["storage"] == "fp32" else 2)

@@ -201,7 +201,10 @@ int lbm_load(lbm_ctx* ctx, const void* host_buf, size_t bytes);
  *     returns the totals.  Class ids are the LBM_K_* values. */
 enum {
     LBM_K_MOMENTS = 0, LBM_K_COLLIDE = 1, LBM_K_CURL = 2, LBM_K_FILTER = 3, LBM_K_SENS = 4,
-    LBM_K_REDUCE = 5, LBM_K_LRS = 6, LBM_K_SOLVE = 7, LBM_K_APPLY = 8, LBM_K_COUNT = 9
+    LBM_K_REDUCE = 5, LBM_K_LRS = 6, LBM_K_SOLVE = 7, LBM_K_APPLY = 8,
+    LBM_K_GAUSS3 = 9,  /* fused 3-D Gaussian / binomial filter applications */
+    LBM_K_LAP3 = 10,   /* fused 3-D Laplacian filter applications           */
+    LBM_K_COUNT = 11
 };
 int lbm_set_graphs(lbm_ctx* ctx, int enable);
 int lbm_profile(lbm_ctx* ctx, int enable);
@@ -209,6 +212,12 @@ int lbm_profile_read(lbm_ctx* ctx, double* ms, int64_t* launches, int count);
 
 /* Kernel launches one lbm_step(ctx, 1) queues (for launch accounting). */
 int lbm_launches_per_step(lbm_ctx* ctx, int64_t* launches);
+
+/* Algorithmic floating-point operations of one step's filter applications,
+ * per kernel class (LBM_K_GAUSS3, LBM_K_LAP3, LBM_K_FILTER): 2 x (taps of the
+ * separable factors) x components x nodes, the minimum a separable
+ * evaluation needs (halo recomputation excluded). */
+int lbm_filter_flops_per_step(lbm_ctx* ctx, double* flops, int count);
 
 /* QoIs of a velocity field, for callers that cannot allocate device memory.
  *

@@ -23,13 +23,13 @@ FILTER = {"G": 0, "L": 1, "B": 2}
 TO_MODE = {"off": 0, "observe": 1, "gamma": 2, "lrs": 3, "track": 4}
 MAX_QOI = 16
 FLAG_SINGULAR, FLAG_UNSTABLE = 1, 2
-K_NAMES = ["moments", "collide", "curl", "filter", "sens", "reduce", "lrs", "solve", "apply"]
+K_NAMES = ["moments", "collide", "curl", "filter", "sens", "reduce", "lrs", "solve", "apply", "gauss3", "lap3"]
 EXPORTED = [
     "lbm_qoi_row_len", "lbm_required_bytes", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_macros",
     "lbm_set_lrs", "lbm_set_track_reference", "lbm_step", "lbm_sync", "lbm_qoi", "lbm_get_macros",
     "lbm_get_populations", "lbm_set_populations", "lbm_get_profile", "lbm_get_step", "lbm_state_bytes",
     "lbm_save", "lbm_load", "lbm_set_graphs", "lbm_profile", "lbm_profile_read", "lbm_launches_per_step",
-    "lbm_qoi_eval_static",
+    "lbm_qoi_eval_static", "lbm_filter_flops_per_step",
 ]
 
 
@@ -80,6 +80,7 @@ def _load():
         "lbm_profile_read": [VP, PD, PI64, C.c_int],
         "lbm_launches_per_step": [VP, PI64],
         "lbm_qoi_eval_static": [cfg, VP, VP, VP],
+        "lbm_filter_flops_per_step": [VP, PD, C.c_int],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -263,6 +264,12 @@ def lbm_profile_read(ctx):
     n = np.zeros(len(K_NAMES), dtype=np.int64)
     _check(_lib.lbm_profile_read(ctx, _ptr(ms), n.ctypes.data_as(C.POINTER(C.c_int64)), len(K_NAMES)), ctx)
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(K_NAMES)}
+
+
+def lbm_filter_flops_per_step(ctx):
+    f = np.zeros(len(K_NAMES))
+    _check(_lib.lbm_filter_flops_per_step(ctx, _ptr(f), len(K_NAMES)), ctx)
+    return {k: float(f[i]) for i, k in enumerate(K_NAMES)}
 
 
 def lbm_launches_per_step(ctx):

@@ -3,11 +3,12 @@
 // A block owns a TX x TY tile of (x, y) and marches along a segment of z.
 // For every input plane it stages the tile plus halo in shared memory
 // (coalesced loads, prefetched into registers one plane ahead), applies the
-// x and y factors in shared memory, and pushes the result into per-thread
-// register rings along z, from which the z factor produces one output plane
-// per step.  Each input element is read from DRAM about once per application
-// (halo re-reads hit L2) and each output written once, instead of one read and
-// one write per 1-D factor.
+// x and y factors with register sliding windows (a thread produces 8 x-values
+// of a row from 8 + 2R staged values, or RPT y-values of a column from
+// RPT + 2R), and pushes the result into per-thread register rings along z,
+// from which the z factor produces one output plane per step.  Each input
+// element is read from DRAM about once per application (halo re-reads hit L2)
+// and each output written once.
 //
 //   gauss3_kernel<R>      G_s (or B3): the same (2R+1)-tap factor on x, y, z
 //   lap3_kernel<RA, RB>   L_s = c sum_a [l dilated along a] x [box_s on the
@@ -22,7 +23,7 @@
 namespace lbm {
 
 namespace {
-constexpr int TX = 32, TY = 16, NT = TX * TY;
+constexpr int TX = 32, TY = 16;
 
 template <int R> struct T3 {
     float t[2 * R + 1];
@@ -33,27 +34,40 @@ __device__ __forceinline__ int pm(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
-// global -> register prefetch of one (TY + 2H) x (TX + 2H) plane tile
-template <int H>
+__host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
+
+// global -> register prefetch of one (TY + 2H) x Wp plane tile (Wp = TX + 2H
+// rounded up to a multiple of 4 so that rows are 16-byte aligned).  The
+// in-plane offset of every staged element (or -1 for the zero extension) is
+// computed once per block: only the plane offset changes along z.
+template <int H, int NT>
 struct TileLoader {
-    static constexpr int W = TX + 2 * H, HH = TY + 2 * H, SZ = W * HH, PER = (SZ + NT - 1) / NT;
+    static constexpr int W = TX + 2 * H, WP = round4(W), HH = TY + 2 * H, SZ = WP * HH, PER = (SZ + NT - 1) / NT;
     float r[PER];
-    __device__ __forceinline__ void load(const Params& p, const float* __restrict__ a, int x0, int y0, int zq) {
+    int off[PER];
+    __device__ __forceinline__ void init(const Params& p, int x0, int y0) {
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
             const int i = threadIdx.x + k * NT;
-            float v = 0.f;
+            int o = -1;
             if (i < SZ) {
-                const int ly = i / W, lx = i % W;
-                int gy = y0 - H + ly;
-                const int gx = pm(x0 - H + lx, p.nx);
-                bool ok = true;
-                if (p.walls) ok = gy >= 0 && gy < p.ny;
-                else gy = pm(gy, p.ny);
-                if (ok) v = __ldg(a + ((size_t)zq * p.ny + gy) * p.nx + gx);
+                const int ly = i / WP, lx = i % WP;
+                if (lx < W) {
+                    int gy = y0 - H + ly;
+                    const int gx = pm(x0 - H + lx, p.nx);
+                    bool ok = true;
+                    if (p.walls) ok = gy >= 0 && gy < p.ny;
+                    else gy = pm(gy, p.ny);
+                    if (ok) o = gy * p.nx + gx;
+                }
             }
-            r[k] = v;
+            off[k] = o;
         }
+    }
+    __device__ __forceinline__ void load(const Params& p, const float* __restrict__ a, int zq) {
+        const float* plane = a + (size_t)zq * p.ny * p.nx;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) r[k] = off[k] >= 0 ? __ldg(plane + off[k]) : 0.f;
     }
     __device__ __forceinline__ void store(float* tile) {
 #pragma unroll
@@ -64,140 +78,209 @@ struct TileLoader {
     }
 };
 
+// 8 consecutive outputs of a 1-D convolution along a shared-memory row:
+// out[j] = sum_r t(r) row[j + R - r], row 16-byte aligned, 8 + 2R values used.
 template <int R>
-__global__ void __launch_bounds__(NT) gauss3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                    T3<R> tp, float scale, int accumulate, int ncomp, int seg) {
-    constexpr int W = TX + 2 * R, HH = TY + 2 * R;
-    __shared__ float tile[HH * W];
-    __shared__ float txs[HH * TX];
+__device__ __forceinline__ void conv8(const float* row, const float* t, float* out) {
+    constexpr int NV = round4(8 + 2 * R);
+    float v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(row + k);
+        v[k] = q.x; v[k + 1] = q.y; v[k + 2] = q.z; v[k + 3] = q.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float s = 0.f;
+#pragma unroll
+        for (int r = -R; r <= R; ++r) s += t[r + R] * v[j + R - r];
+        out[j] = s;
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(128) gauss3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                     T3<R> tp, float scale, int accumulate, int ncomp, int seg) {
+    constexpr int NT = 128, RPT = TY / (NT / TX);  // 4 output rows per thread
+    using LD = TileLoader<R, NT>;
+    constexpr int WP = LD::WP, HH = LD::HH;
+    __shared__ __align__(16) float tile[HH * WP];
+    __shared__ __align__(16) float xt[HH * TX];
     const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
     const int nz = p.nz;
     const int z0 = zs * seg, z1 = min(nz, z0 + seg);
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-    const int x = x0 + lx, y = y0 + ly;
+    const int lx = threadIdx.x % TX, yr = threadIdx.x / TX;
+    const int x = x0 + lx;
     const size_t N = (size_t)p.n;
     const float* a = in + c * N;
     float* o = out + c * N;
-    const bool live = x < p.nx && y < p.ny;
-    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
-    float ring[2 * R + 1];
+    float ring[RPT][2 * R + 1];
 #pragma unroll
-    for (int k = 0; k < 2 * R + 1; ++k) ring[k] = 0.f;
-    TileLoader<R> ld;
-    ld.load(p, a, x0, y0, pm(z0 - R, nz));
+    for (int j = 0; j < RPT; ++j)
+#pragma unroll
+        for (int k = 0; k < 2 * R + 1; ++k) ring[j][k] = 0.f;
+    LD ld;
+    ld.init(p, x0, y0);
+    ld.load(p, a, pm(z0 - R, nz));
+    // Two barriers per plane: the x factor reads `tile` only before the second
+    // barrier and the y factor reads `xt` only before the next plane's first,
+    // so the next plane's stores cannot overtake a reader.
     for (int q = z0 - R; q < z1 + R; ++q) {
         ld.store(tile);
         __syncthreads();
-        if (q + 1 < z1 + R) ld.load(p, a, x0, y0, pm(q + 1, nz));
-        // x factor on all tile rows
-        for (int i = threadIdx.x; i < HH * TX; i += NT) {
-            const int ry = i / TX, rx = i % TX;
+        if (q + 1 < z1 + R) ld.load(p, a, pm(q + 1, nz));
+        // x factor: task = (tile row, 8-wide segment)
+        for (int task = threadIdx.x; task < HH * (TX / 8); task += NT) {
+            const int ry = task / (TX / 8), k = task % (TX / 8);
+            float r8[8];
+            conv8<R>(tile + ry * WP + 8 * k, tp.t, r8);
+            float4* dst = reinterpret_cast<float4*>(xt + ry * TX + 8 * k);
+            dst[0] = make_float4(r8[0], r8[1], r8[2], r8[3]);
+            dst[1] = make_float4(r8[4], r8[5], r8[6], r8[7]);
+        }
+        __syncthreads();
+        // y factor: RPT consecutive rows of column lx from RPT + 2R values
+        float col[RPT + 2 * R];
+#pragma unroll
+        for (int m = 0; m < RPT + 2 * R; ++m) col[m] = xt[(yr * RPT + m) * TX + lx];
+        const int zo = q - R;
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
             float s = 0.f;
 #pragma unroll
-            for (int r = -R; r <= R; ++r) s += tp.t[r + R] * tile[ry * W + rx + R - r];
-            txs[i] = s;
+            for (int r = -R; r <= R; ++r) s += tp.t[r + R] * col[j + R - r];
+#pragma unroll
+            for (int k = 0; k < 2 * R; ++k) ring[j][k] = ring[j][k + 1];
+            ring[j][2 * R] = s;
+            const int y = y0 + yr * RPT + j;
+            if (zo >= z0 && x < p.nx && y < p.ny) {
+                float v = 0.f;
+#pragma unroll
+                for (int r = -R; r <= R; ++r) v += tp.t[r + R] * ring[j][R - r];
+                const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+                v = solid ? 0.f : scale * v;
+                float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
+                *op = accumulate ? (*op + v) : v;
+            }
         }
-        __syncthreads();
-        // y factor for this thread's point
-        float s = 0.f;
-#pragma unroll
-        for (int r = -R; r <= R; ++r) s += tp.t[r + R] * txs[(ly + R - r) * TX + lx];
-#pragma unroll
-        for (int k = 0; k < 2 * R; ++k) ring[k] = ring[k + 1];
-        ring[2 * R] = s;
-        // z factor: ring[k] holds plane q - 2R + k; output plane z = q - R
-        const int zo = q - R;
-        if (zo >= z0 && live) {
-            float v = 0.f;
-#pragma unroll
-            for (int r = -R; r <= R; ++r) v += tp.t[r + R] * ring[R - r];
-            v = solid ? 0.f : scale * v;
-            float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
-            *op = accumulate ? (*op + v) : v;
-        }
-        __syncthreads();
     }
 }
 
 template <int RA, int RB>
-__global__ void __launch_bounds__(NT) lap3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                  T3<RA> arm, float scale, int accumulate, int ncomp, int seg) {
-    constexpr int W = TX + 2 * RA, HH = TY + 2 * RA;
-    __shared__ float tile[HH * W];
-    __shared__ float by[TY * W];   // box along y on the output rows, all tile columns
-    __shared__ float bx[HH * TX];  // box along x on all tile rows, output columns
+__global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                   T3<RA> arm, float scale, int accumulate, int ncomp, int seg) {
+    constexpr int NT = 256, RPT = TY / (NT / TX);  // 2 output rows per thread
+    using LD = TileLoader<RA, NT>;
+    constexpr int WP = LD::WP, HH = LD::HH, W = LD::W;
+    constexpr int KXY = RA + RB + 1;  // ring of l_x B_y + l_y B_x (box along z later)
+    constexpr int KZ = 2 * RA + 1;    // ring of B_x B_y (arm along z later)
+    __shared__ __align__(16) float tile[HH * WP];
+    __shared__ __align__(16) float by[TY * WP];  // box along y on the output rows, every tile column
+    __shared__ __align__(16) float bx[HH * TX];  // box along x on every tile row, output columns
+    __shared__ __align__(16) float axs[TY * TX]; // l_x of by
     const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
     const int nz = p.nz;
     const int z0 = zs * seg, z1 = min(nz, z0 + seg);
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-    const int x = x0 + lx, y = y0 + ly;
+    const int lx = threadIdx.x % TX, yr = threadIdx.x / TX;
+    const int x = x0 + lx;
     const size_t N = (size_t)p.n;
     const float* a = in + c * N;
     float* o = out + c * N;
-    const bool live = x < p.nx && y < p.ny;
-    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
-    // rings along z: rx = l_x(B_y plane), ry = l_y(B_x plane), rz = B_y(B_x plane)
-    float rx[2 * RA + 1], ry[2 * RA + 1], rz[2 * RA + 1];
+    float rxy[RPT][KXY], rz[RPT][KZ];
 #pragma unroll
-    for (int k = 0; k < 2 * RA + 1; ++k) rx[k] = ry[k] = rz[k] = 0.f;
-    TileLoader<RA> ld;
-    ld.load(p, a, x0, y0, pm(z0 - RA, nz));
+    for (int j = 0; j < RPT; ++j) {
+#pragma unroll
+        for (int k = 0; k < KXY; ++k) rxy[j][k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KZ; ++k) rz[j][k] = 0.f;
+    }
+    LD ld;
+    ld.init(p, x0, y0);
+    ld.load(p, a, pm(z0 - RA, nz));
+    // Three barriers per plane; every shared array is last read before a
+    // barrier that the next plane's writer must also pass.
     for (int q = z0 - RA; q < z1 + RA; ++q) {
         ld.store(tile);
         __syncthreads();
-        if (q + 1 < z1 + RA) ld.load(p, a, x0, y0, pm(q + 1, nz));
-        for (int i = threadIdx.x; i < TY * W; i += NT) {
-            const int ry_ = i / W, rx_ = i % W;
-            float s = 0.f;
+        if (q + 1 < z1 + RA) ld.load(p, a, pm(q + 1, nz));
+        // box along y on output rows (4-row runs of one tile column)
+        for (int task = threadIdx.x; task < W * (TY / 4); task += NT) {
+            const int cx = task % W, run = task / W;
+            float v[4 + 2 * RB];
 #pragma unroll
-            for (int r = -RB; r <= RB; ++r) s += tile[(ry_ + RA - r) * W + rx_];
-            by[i] = s;
+            for (int m = 0; m < 4 + 2 * RB; ++m) v[m] = tile[(run * 4 + RA - RB + m) * WP + cx];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float s = 0.f;
+#pragma unroll
+                for (int r = 0; r <= 2 * RB; ++r) s += v[j + r];
+                by[(run * 4 + j) * WP + cx] = s;
+            }
         }
-        for (int i = threadIdx.x; i < HH * TX; i += NT) {
-            const int ry_ = i / TX, rx_ = i % TX;
-            float s = 0.f;
+        // box along x on every tile row (8-wide segments of output columns)
+        for (int task = threadIdx.x; task < HH * (TX / 8); task += NT) {
+            const int ry = task / (TX / 8), k = task % (TX / 8);
+            const float* row = tile + ry * WP + 8 * k + RA - RB;
 #pragma unroll
-            for (int r = -RB; r <= RB; ++r) s += tile[ry_ * W + rx_ + RA - r];
-            bx[i] = s;
+            for (int j = 0; j < 8; ++j) {
+                float s = 0.f;
+#pragma unroll
+                for (int r = 0; r <= 2 * RB; ++r) s += row[j + r];
+                bx[ry * TX + 8 * k + j] = s;
+            }
         }
         __syncthreads();
-        float ax = 0.f, ay = 0.f, az = 0.f;
-#pragma unroll
-        for (int r = -RA; r <= RA; ++r) {
-            ax += arm.t[r + RA] * by[ly * W + lx + RA - r];
-            ay += arm.t[r + RA] * bx[(ly + RA - r) * TX + lx];
+        // arm along x of by (8-wide segments, aligned rows)
+        for (int task = threadIdx.x; task < TY * (TX / 8); task += NT) {
+            const int ry = task / (TX / 8), k = task % (TX / 8);
+            float r8[8];
+            conv8<RA>(by + ry * WP + 8 * k, arm.t, r8);
+            float4* dst = reinterpret_cast<float4*>(axs + ry * TX + 8 * k);
+            dst[0] = make_float4(r8[0], r8[1], r8[2], r8[3]);
+            dst[1] = make_float4(r8[4], r8[5], r8[6], r8[7]);
         }
+        __syncthreads();
+        // per thread: RPT rows of column lx
+        float col[RPT + 2 * RA];
 #pragma unroll
-        for (int r = -RB; r <= RB; ++r) az += bx[(ly + RA - r) * TX + lx];
-#pragma unroll
-        for (int k = 0; k < 2 * RA; ++k) {
-            rx[k] = rx[k + 1];
-            ry[k] = ry[k + 1];
-            rz[k] = rz[k + 1];
-        }
-        rx[2 * RA] = ax;
-        ry[2 * RA] = ay;
-        rz[2 * RA] = az;
+        for (int m = 0; m < RPT + 2 * RA; ++m) col[m] = bx[(yr * RPT + m) * TX + lx];
         const int zo = q - RA;
-        if (zo >= z0 && live) {
-            float v = 0.f;
 #pragma unroll
-            for (int r = -RB; r <= RB; ++r) v += rx[RA - r] + ry[RA - r];
+        for (int j = 0; j < RPT; ++j) {
+            float ay = 0.f, az = 0.f;
 #pragma unroll
-            for (int r = -RA; r <= RA; ++r) v += arm.t[r + RA] * rz[RA - r];
-            v = solid ? 0.f : scale * v;
-            float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
-            *op = accumulate ? (*op + v) : v;
+            for (int r = -RA; r <= RA; ++r) ay += arm.t[r + RA] * col[j + RA - r];
+#pragma unroll
+            for (int r = -RB; r <= RB; ++r) az += col[j + RA - r];
+            const float axy = axs[(yr * RPT + j) * TX + lx] + ay;
+#pragma unroll
+            for (int k = 0; k < KXY - 1; ++k) rxy[j][k] = rxy[j][k + 1];
+            rxy[j][KXY - 1] = axy;
+#pragma unroll
+            for (int k = 0; k < KZ - 1; ++k) rz[j][k] = rz[j][k + 1];
+            rz[j][KZ - 1] = az;
+            const int y = y0 + yr * RPT + j;
+            if (zo >= z0 && x < p.nx && y < p.ny) {
+                // rxy[k] holds plane q - RA - RB + k, rz[k] plane q - 2 RA + k; output z = q - RA
+                float v = 0.f;
+#pragma unroll
+                for (int r = -RB; r <= RB; ++r) v += rxy[j][RB - r];
+#pragma unroll
+                for (int r = -RA; r <= RA; ++r) v += arm.t[r + RA] * rz[j][RA - r];
+                const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+                v = solid ? 0.f : scale * v;
+                float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
+                *op = accumulate ? (*op + v) : v;
+            }
         }
-        __syncthreads();
     }
 }
 
-int seg_len(const Params& p, int blocks_xy, int ncomp, int R) {
-    // enough z segments for ~4 blocks per SM; each segment re-reads 2R planes
-    const long long want = 148LL * 4;
+int seg_len(const Params& p, int blocks_xy, int ncomp, int R, int per_sm) {
+    // enough z segments for `per_sm` blocks per SM; each segment re-reads 2R planes
+    const long long want = 148LL * per_sm;
     long long nseg = (want + (long long)blocks_xy * ncomp - 1) / ((long long)blocks_xy * ncomp);
     if (nseg < 1) nseg = 1;
     int seg = (int)((p.nz + nseg - 1) / nseg);
@@ -212,9 +295,9 @@ cudaError_t run_gauss(const Params& p, const float* in, float* out, int ncomp, c
     T3<R> tp;
     for (int i = 0; i < 2 * R + 1; ++i) tp.t[i] = t.t[i];
     const int bx = (p.nx + TX - 1) / TX, by = (p.ny + TY - 1) / TY;
-    const int seg = seg_len(p, bx * by, ncomp, R);
+    const int seg = seg_len(p, bx * by, ncomp, R, 8);
     const int nseg = (p.nz + seg - 1) / seg;
-    gauss3_kernel<R><<<dim3(bx, by, ncomp * nseg), NT, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+    gauss3_kernel<R><<<dim3(bx, by, ncomp * nseg), 128, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
     return cudaGetLastError();
 }
 
@@ -224,9 +307,9 @@ cudaError_t run_lap(const Params& p, const float* in, float* out, int ncomp, con
     T3<RA> tp;
     for (int i = 0; i < 2 * RA + 1; ++i) tp.t[i] = arm.t[i];
     const int bx = (p.nx + TX - 1) / TX, by = (p.ny + TY - 1) / TY;
-    const int seg = seg_len(p, bx * by, ncomp, RA);
+    const int seg = seg_len(p, bx * by, ncomp, RA, 4);
     const int nseg = (p.nz + seg - 1) / seg;
-    lap3_kernel<RA, RB><<<dim3(bx, by, ncomp * nseg), NT, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+    lap3_kernel<RA, RB><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
     return cudaGetLastError();
 }
 }  // namespace

@@ -39,6 +39,7 @@ struct lbm_ctx {
     cudaGraphExec_t graph;     // two steps: src 0 -> 1, then 1 -> 0
     long long host_read;       // QoI rows already drained
     long long launches_per_step;
+    double filter_flops[LBM_K_COUNT];  // algorithmic flops per step by kernel class
     float* aux;                // [4][N] scratch for macros / init
     size_t elem;               // bytes per stored population
     char err[256];
@@ -323,6 +324,14 @@ struct Launcher {
         if (!(lc).count_only) (lc).after(expr); \
     } while (0)
 
+// taps of one application of a separable filter per output: G/B d(2R+1);
+// L_s d x (5 s arm + (d-1) s box taps, the box omitted when s = 1)
+static double filter_taps(const Filter& f, int d) {
+    if (f.kind == LBM_FILTER_GAUSS) return d * (2.0 * (d == 2 ? 4 : 2) * f.scale + 1.0);
+    if (f.kind == LBM_FILTER_BINOMIAL) return d * 3.0;
+    return d * (5.0 * f.scale + (f.scale > 1 ? (d - 1) * (double)f.scale : 0.0));
+}
+
 static void enqueue_filter(Launcher& lc, const Filter& f, const float* in, float* out) {
     lbm_ctx* c = lc.c;
     const Params& p = c->p;
@@ -330,20 +339,24 @@ static void enqueue_filter(Launcher& lc, const Filter& f, const float* in, float
     const int d = p.dim;
     float* t1 = c->L.t1;
     float* t2 = c->L.t2;
+    const double flops = 2.0 * filter_taps(f, d) * nc * (double)p.n;
     if (d == 3) {
         // fused 3-D kernels: the whole filter in one pass over the field
         if (f.kind == LBM_FILTER_GAUSS || f.kind == LBM_FILTER_BINOMIAL) {
             const Taps t = f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps();
             if (launch_gauss3_supported(t.radius)) {
-                LAUNCH(lc, LBM_K_FILTER, launch_gauss3(p, in, out, nc, t, 1.f, 0, lc.s));
+                if (lc.count_only) c->filter_flops[LBM_K_GAUSS3] += flops;
+                LAUNCH(lc, LBM_K_GAUSS3, launch_gauss3(p, in, out, nc, t, 1.f, 0, lc.s));
                 return;
             }
         } else if (launch_lap3_supported(f.scale)) {
             const float scale = (float)(1.0 / (8.0 * d * (double)f.scale * f.scale * f.scale));
-            LAUNCH(lc, LBM_K_FILTER, launch_lap3(p, in, out, nc, f.scale, ell_taps(f.scale), scale, 0, lc.s));
+            if (lc.count_only) c->filter_flops[LBM_K_LAP3] += flops;
+            LAUNCH(lc, LBM_K_LAP3, launch_lap3(p, in, out, nc, f.scale, ell_taps(f.scale), scale, 0, lc.s));
             return;
         }
     }
+    if (lc.count_only) c->filter_flops[LBM_K_FILTER] += flops;
     if (f.kind == LBM_FILTER_GAUSS || f.kind == LBM_FILTER_BINOMIAL) {
         const Taps t = f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps();
         if (d == 2) {
@@ -408,6 +421,7 @@ static void enqueue_step(Launcher& lc, int src) {
 }
 
 static void count_launches(lbm_ctx* c) {
+    for (int k = 0; k < LBM_K_COUNT; ++k) c->filter_flops[k] = 0.0;
     Launcher lc{c, c->stream, true, 0};
     lc.timed = false;
     enqueue_step(lc, 0);
@@ -938,6 +952,12 @@ int lbm_profile_read(lbm_ctx* c, double* ms, int64_t* launches, int count) {
 int lbm_launches_per_step(lbm_ctx* c, int64_t* launches) {
     if (!c || !launches) return fail(c, LBM_ERR_ARG, "NULL argument");
     *launches = c->launches_per_step;
+    return LBM_OK;
+}
+
+int lbm_filter_flops_per_step(lbm_ctx* c, double* flops, int count) {
+    if (!c || !flops) return fail(c, LBM_ERR_ARG, "NULL argument");
+    for (int k = 0; k < count && k < LBM_K_COUNT; ++k) flops[k] = c->filter_flops[k];
     return LBM_OK;
 }
 

@@ -83,12 +83,21 @@ def _c4_to():
     return w
 
 
+def _c4_to_mid():
+    """The TO-LRS channel step on a 320x200x160 grid (10.2 M nodes): fields larger
+    than L2 but a few GB on the device, for profiler captures."""
+    w = _c4_to()
+    w.update(name="channel3d_320x200x160_wale_tolrs", nx=320, nz=160, seed=20260906)
+    return w
+
+
 WORKLOADS = {
     "C1": _c1,
     "C2": _c2,
     "C3": _c3,
     "C4": _c4,
     "C4_TO": _c4_to,
+    "C4_TO_MID": _c4_to_mid,
 }
 
 

@@ -167,6 +167,12 @@ __global__ void __launch_bounds__(128) gauss3_kernel(Params p, const float* __re
     }
 }
 
+// L_s with a box (s > 1): double-buffered shared arrays, two barriers per
+// plane.  Phase A (after the tile of plane q is stored): box along y on the
+// output rows and box along x on every tile row.  Phase B: the three terms of
+// this thread's points, pushed into the z rings.  A buffer written in phase A
+// of plane q was last read in phase B of plane q-2, which every thread left
+// before the first barrier of plane q-1.
 template <int RA, int RB>
 __global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
                                                    T3<RA> arm, float scale, int accumulate, int ncomp, int seg) {
@@ -175,10 +181,9 @@ __global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __rest
     constexpr int WP = LD::WP, HH = LD::HH, W = LD::W;
     constexpr int KXY = RA + RB + 1;  // ring of l_x B_y + l_y B_x (box along z later)
     constexpr int KZ = 2 * RA + 1;    // ring of B_x B_y (arm along z later)
-    __shared__ __align__(16) float tile[HH * WP];
-    __shared__ __align__(16) float by[TY * WP];  // box along y on the output rows, every tile column
-    __shared__ __align__(16) float bx[HH * TX];  // box along x on every tile row, output columns
-    __shared__ __align__(16) float axs[TY * TX]; // l_x of by
+    __shared__ __align__(16) float tile[2][HH * WP];
+    __shared__ __align__(16) float by[2][TY * WP];  // box along y on the output rows, every tile column
+    __shared__ __align__(16) float bx[2][HH * TX];  // box along x on every tile row, output columns
     const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
     const int nz = p.nz;
     const int z0 = zs * seg, z1 = min(nz, z0 + seg);
@@ -199,65 +204,63 @@ __global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __rest
     LD ld;
     ld.init(p, x0, y0);
     ld.load(p, a, pm(z0 - RA, nz));
-    // Three barriers per plane; every shared array is last read before a
-    // barrier that the next plane's writer must also pass.
-    for (int q = z0 - RA; q < z1 + RA; ++q) {
-        ld.store(tile);
+    int b = 0;
+    for (int q = z0 - RA; q < z1 + RA; ++q, b ^= 1) {
+        ld.store(tile[b]);
         __syncthreads();
         if (q + 1 < z1 + RA) ld.load(p, a, pm(q + 1, nz));
-        // box along y on output rows (4-row runs of one tile column)
+        const float* tl = tile[b];
         for (int task = threadIdx.x; task < W * (TY / 4); task += NT) {
             const int cx = task % W, run = task / W;
             float v[4 + 2 * RB];
 #pragma unroll
-            for (int m = 0; m < 4 + 2 * RB; ++m) v[m] = tile[(run * 4 + RA - RB + m) * WP + cx];
+            for (int m = 0; m < 4 + 2 * RB; ++m) v[m] = tl[(run * 4 + RA - RB + m) * WP + cx];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float s = 0.f;
 #pragma unroll
                 for (int r = 0; r <= 2 * RB; ++r) s += v[j + r];
-                by[(run * 4 + j) * WP + cx] = s;
+                by[b][(run * 4 + j) * WP + cx] = s;
             }
         }
-        // box along x on every tile row (8-wide segments of output columns)
         for (int task = threadIdx.x; task < HH * (TX / 8); task += NT) {
             const int ry = task / (TX / 8), k = task % (TX / 8);
-            const float* row = tile + ry * WP + 8 * k + RA - RB;
+            const float* row = tl + ry * WP + 8 * k + RA - RB;
+            float v[8 + 2 * RB];
+#pragma unroll
+            for (int m = 0; m < 8 + 2 * RB; ++m) v[m] = row[m];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 float s = 0.f;
 #pragma unroll
-                for (int r = 0; r <= 2 * RB; ++r) s += row[j + r];
-                bx[ry * TX + 8 * k + j] = s;
+                for (int r = 0; r <= 2 * RB; ++r) s += v[j + r];
+                bx[b][ry * TX + 8 * k + j] = s;
             }
         }
         __syncthreads();
-        // arm along x of by (8-wide segments, aligned rows)
-        for (int task = threadIdx.x; task < TY * (TX / 8); task += NT) {
-            const int ry = task / (TX / 8), k = task % (TX / 8);
-            float r8[8];
-            conv8<RA>(by + ry * WP + 8 * k, arm.t, r8);
-            float4* dst = reinterpret_cast<float4*>(axs + ry * TX + 8 * k);
-            dst[0] = make_float4(r8[0], r8[1], r8[2], r8[3]);
-            dst[1] = make_float4(r8[4], r8[5], r8[6], r8[7]);
-        }
-        __syncthreads();
-        // per thread: RPT rows of column lx
+        const float* byb = by[b];
+        const float* bxb = bx[b];
         float col[RPT + 2 * RA];
 #pragma unroll
-        for (int m = 0; m < RPT + 2 * RA; ++m) col[m] = bx[(yr * RPT + m) * TX + lx];
+        for (int m = 0; m < RPT + 2 * RA; ++m) col[m] = bxb[(yr * RPT + m) * TX + lx];
         const int zo = q - RA;
 #pragma unroll
         for (int j = 0; j < RPT; ++j) {
-            float ay = 0.f, az = 0.f;
+            // arm along x of by at (row, lx) and along y of bx, symmetric taps
+            const float* br = byb + (yr * RPT + j) * WP + lx;
+            float ax = arm.t[RA] * br[RA];
+            float ay = arm.t[RA] * col[j + RA];
 #pragma unroll
-            for (int r = -RA; r <= RA; ++r) ay += arm.t[r + RA] * col[j + RA - r];
+            for (int r = 1; r <= RA; ++r) {
+                ax += arm.t[RA + r] * (br[RA - r] + br[RA + r]);
+                ay += arm.t[RA + r] * (col[j + RA - r] + col[j + RA + r]);
+            }
+            float az = 0.f;
 #pragma unroll
             for (int r = -RB; r <= RB; ++r) az += col[j + RA - r];
-            const float axy = axs[(yr * RPT + j) * TX + lx] + ay;
 #pragma unroll
             for (int k = 0; k < KXY - 1; ++k) rxy[j][k] = rxy[j][k + 1];
-            rxy[j][KXY - 1] = axy;
+            rxy[j][KXY - 1] = ax + ay;
 #pragma unroll
             for (int k = 0; k < KZ - 1; ++k) rz[j][k] = rz[j][k + 1];
             rz[j][KZ - 1] = az;
@@ -267,8 +270,77 @@ __global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __rest
                 float v = 0.f;
 #pragma unroll
                 for (int r = -RB; r <= RB; ++r) v += rxy[j][RB - r];
+                float vz = arm.t[RA] * rz[j][RA];
 #pragma unroll
-                for (int r = -RA; r <= RA; ++r) v += arm.t[r + RA] * rz[j][RA - r];
+                for (int r = 1; r <= RA; ++r) vz += arm.t[RA + r] * (rz[j][RA - r] + rz[j][RA + r]);
+                v += vz;
+                const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+                v = solid ? 0.f : scale * v;
+                float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
+                *op = accumulate ? (*op + v) : v;
+            }
+        }
+    }
+}
+
+// L_1 (no box): the 13-point cross l_x + l_y + l_z read straight from the
+// double-buffered tile, one barrier per plane.
+template <int RA>
+__global__ void __launch_bounds__(256) cross3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                     T3<RA> arm, float scale, int accumulate, int ncomp, int seg) {
+    constexpr int NT = 256, RPT = TY / (NT / TX);
+    using LD = TileLoader<RA, NT>;
+    constexpr int WP = LD::WP, HH = LD::HH;
+    constexpr int KZ = 2 * RA + 1;
+    __shared__ __align__(16) float tile[2][HH * WP];
+    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int nz = p.nz;
+    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int lx = threadIdx.x % TX, yr = threadIdx.x / TX;
+    const int x = x0 + lx;
+    const size_t N = (size_t)p.n;
+    const float* a = in + c * N;
+    float* o = out + c * N;
+    float rxy[RPT][RA + 1], rz[RPT][KZ];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+#pragma unroll
+        for (int k = 0; k < RA + 1; ++k) rxy[j][k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KZ; ++k) rz[j][k] = 0.f;
+    }
+    LD ld;
+    ld.init(p, x0, y0);
+    ld.load(p, a, pm(z0 - RA, nz));
+    int b = 0;
+    for (int q = z0 - RA; q < z1 + RA; ++q, b ^= 1) {
+        ld.store(tile[b]);
+        __syncthreads();
+        if (q + 1 < z1 + RA) ld.load(p, a, pm(q + 1, nz));
+        const float* tl = tile[b];
+        const int zo = q - RA;
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int ry = yr * RPT + j + RA;
+            const float* row = tl + ry * WP + lx + RA;
+            const float ctr = row[0];
+            float axy = 2.f * arm.t[RA] * ctr;
+#pragma unroll
+            for (int r = 1; r <= RA; ++r)
+                axy += arm.t[RA + r] * ((row[-r] + row[r]) + (row[-r * WP] + row[r * WP]));
+#pragma unroll
+            for (int k = 0; k < RA; ++k) rxy[j][k] = rxy[j][k + 1];
+            rxy[j][RA] = axy;
+#pragma unroll
+            for (int k = 0; k < KZ - 1; ++k) rz[j][k] = rz[j][k + 1];
+            rz[j][KZ - 1] = ctr;
+            const int y = y0 + yr * RPT + j;
+            if (zo >= z0 && x < p.nx && y < p.ny) {
+                // rxy[k] holds plane q - RA + k, so the current output plane is rxy[0]
+                float v = rxy[j][0] + arm.t[RA] * rz[j][RA];
+#pragma unroll
+                for (int r = 1; r <= RA; ++r) v += arm.t[RA + r] * (rz[j][RA - r] + rz[j][RA + r]);
                 const bool solid = p.walls && (y == 0 || y == p.ny - 1);
                 v = solid ? 0.f : scale * v;
                 float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
@@ -309,7 +381,10 @@ cudaError_t run_lap(const Params& p, const float* in, float* out, int ncomp, con
     const int bx = (p.nx + TX - 1) / TX, by = (p.ny + TY - 1) / TY;
     const int seg = seg_len(p, bx * by, ncomp, RA, 4);
     const int nseg = (p.nz + seg - 1) / seg;
-    lap3_kernel<RA, RB><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+    if (RB == 0)
+        cross3_kernel<RA><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+    else
+        lap3_kernel<RA, RB><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
     return cudaGetLastError();
 }
 }  // namespace

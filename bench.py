@@ -262,6 +262,48 @@ def run_ours(args, world, rank, local):
                 n_nodes=n_nodes)
 
 
+def run_serving(args, device):
+    """Ensemble serving on the mix of the serving configuration (horizons
+    scaled by --serve-scale): offline throughput of the batched server in FP32
+    and with FP16 population storage against one-member-at-a-time FP32, then a
+    Poisson stream at ~1x the batched FP32 capacity for latency per TU."""
+    import torch
+
+    from paper_2609_32892_b300 import serve
+
+    reqs32 = serve.scaled_mix(args.serve_n, 7, 1.0, args.serve_scale, "fp32")
+    reqs16 = serve.scaled_mix(args.serve_n, 7, 1.0, args.serve_scale, "fp16")
+    res = {"requests": args.serve_n, "horizon_scale": args.serve_scale,
+           "mix": "2-D Kolmogorov 128^2-512^2 (Smagorinsky + TO-LRS, 4 QoIs) and 3-D channel "
+                  "48x20x24-96x40x48 (WALE + TO-LRS, 12 QoIs), horizons log-uniform 1e3-1e4 steps x scale"}
+    srv = serve.EnsembleServer(args.serve_pool_gb << 30, args.serve_slots, device)
+    out32, w32, _ = srv.serve(reqs32, chunk=args.serve_chunk, keep_qoi=True, realtime=False)
+    res["batched_fp32"] = serve.summarize(out32, w32)
+    out16, w16, _ = srv.serve(reqs16, chunk=args.serve_chunk, keep_qoi=True, realtime=False)
+    res["batched_fp16"] = serve.summarize(out16, w16)
+    # QoI accuracy of reduced-precision storage: time-mean of each QoI, fp16 vs fp32
+    worst = 0.0
+    for i in out32:
+        a = out32[i]["qoi"]
+        b = out16[i]["qoi"]
+        nq = (a.shape[1] - 2) // 3
+        ma = np.abs(a[:, 1:1 + nq]).mean(axis=0)
+        mb = np.abs(b[:, 1:1 + nq]).mean(axis=0)
+        worst = max(worst, float(np.max(np.abs(mb - ma) / np.maximum(ma, 1e-300))))
+    res["fp16_vs_fp32_qoi_time_mean_max_rel_diff"] = worst
+    res["serial_fp32"] = serve.serial_baseline(reqs32, device)
+    # Poisson arrivals at the batched FP32 capacity (members per second)
+    rate = args.serve_n / w32
+    reqs_rt = serve.scaled_mix(args.serve_n, 8, rate, args.serve_scale, "fp32")
+    out_rt, w_rt, _ = srv.serve(reqs_rt, chunk=args.serve_chunk, realtime=True)
+    res["poisson_fp32"] = dict(serve.summarize(out_rt, w_rt), offered_members_per_s=round(rate, 2))
+    srv.close()
+    torch.cuda.synchronize()
+    res["speedup_batched_fp16_vs_serial_fp32"] = round(
+        res["batched_fp16"]["member_steps_per_s"] / res["serial_fp32"]["member_steps_per_s"], 2)
+    return res
+
+
 def cpu_oracle_sample(wl, seconds=15.0):
     """The oracle (as it stands) stepping a bounded sample of the workload:
     the same physics and QoI set on a 48x40x24 sub-grid, timed for ~`seconds`."""
@@ -301,6 +343,12 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--no-bgk", dest="bgk", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-serve", dest="serve", action="store_false")
+    ap.add_argument("--serve-n", type=int, default=32)
+    ap.add_argument("--serve-scale", type=float, default=0.1)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-pool-gb", type=int, default=16)
+    ap.add_argument("--serve-chunk", type=int, default=32)
     args = ap.parse_args()
     world, rank, local = _dist()
     wl = synthetic.workload(args.workload, storage=args.storage)
@@ -329,6 +377,11 @@ def main():
 
         torch.distributed.init_process_group("nccl" if os.environ.get("LBM_DIST_BACKEND") != "gloo" else "gloo")
     r = run_ours(args, world, rank, local)
+    serving = None
+    if args.serve and rank == 0:
+        import torch
+
+        serving = run_serving(args, torch.device("cuda", local))
     if rank == 0:
         cpu = cpu_oracle_sample(wl, args.cpu_seconds) if world == 1 else None
         line = {"metric": METRIC, "value": round(r["mlups"], 1), "unit": "MLUPS", "n_gpus": world,
@@ -339,7 +392,7 @@ def main():
                 "config": config, "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
                 "gpu_launches": int(r["launches"] * args.steps), "clocks": r["clocks"],
                 "step_hbm_gbs": round(r["step_gbs"], 1), "collide_gbs": r["collide_gbs"],
-                "sections": r["sections"], "bgk_480x200x240": r["bgk"]}
+                "sections": r["sections"], "bgk_480x200x240": r["bgk"], "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

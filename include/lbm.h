@@ -219,6 +219,58 @@ int lbm_launches_per_step(lbm_ctx* ctx, int64_t* launches);
  * evaluation needs (halo recomputation excluded). */
 int lbm_filter_flops_per_step(lbm_ctx* ctx, double* flops, int count);
 
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent members (different grids, seeds, horizons)
+ * advancing together on one GPU.  The paper runs ensembles of five replicas
+ * per configuration (Sec. 6.4, Sec. 7.4); the batch API runs any number of
+ * members concurrently so that small grids fill the device.
+ *
+ * The caller owns one device pool; the batch carves each admitted member out
+ * of it (first fit, 256-byte aligned) and returns LBM_ERR_BUDGET when a member
+ * does not fit or no slot is free, so admission is by HBM budget.  Every
+ * member has its own stream and its own two-step CUDA graph; lbm_batch_run
+ * queues the steps of all active members without waiting, and the device
+ * overlaps their kernels.  A member's results are bit-identical whether it
+ * runs alone or in a mix (its kernels read only its own memory).
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+    int32_t slot;        /* member slot                                        */
+    int32_t status;      /* LBM_OK or LBM_ERR_UNSTABLE                         */
+    int64_t steps;       /* steps completed (= horizon)                        */
+    uint64_t tag;        /* caller's tag from lbm_batch_admit                  */
+    double t_done_ms;    /* device time of completion, ms since lbm_batch_create */
+} lbm_completion;
+
+/* n_slots members at most, carved from dev_pool (device, 256-byte aligned). */
+int lbm_batch_create(int32_t n_slots, void* dev_pool, size_t pool_bytes, lbm_batch** out);
+int lbm_batch_destroy(lbm_batch* b);
+
+/* Admit a member: allocate from the pool, create it, set f = f^eq(1, u0)
+ * (u0 host FP64 [3][nz][ny][nx]).  horizon = steps to run.  For LBM_TO_LRS
+ * call lbm_set_lrs on lbm_batch_member(slot) before the next lbm_batch_run.
+ * LBM_ERR_BUDGET: no free slot or not enough contiguous pool memory. */
+int lbm_batch_admit(lbm_batch* b, const lbm_config* cfg, const double* u0, int64_t horizon, uint64_t tag,
+                    int32_t* slot);
+
+/* The member's context (for lbm_set_lrs, lbm_qoi, lbm_get_macros, ...). */
+int lbm_batch_member(lbm_batch* b, int32_t slot, lbm_ctx** ctx);
+
+/* Queue up to `steps` more steps of every active member (stopping at each
+ * member's horizon).  Asynchronous. */
+int lbm_batch_run(lbm_batch* b, int64_t steps);
+
+/* Members whose horizon has been reached on the device (non-blocking):
+ * up to cap completions into out, count in *n.  Each is reported once. */
+int lbm_batch_poll(lbm_batch* b, lbm_completion* out, int32_t cap, int32_t* n);
+
+/* Free a member's slot and pool memory (after its results were read). */
+int lbm_batch_release(lbm_batch* b, int32_t slot);
+
+/* Pool bytes free in total and in the largest contiguous block; active members. */
+int lbm_batch_stats(lbm_batch* b, size_t* free_bytes, size_t* largest, int32_t* active);
+
 /* QoIs of a velocity field, for callers that cannot allocate device memory.
  *
  * The paper has no counterpart to this entry point; it exists for callers

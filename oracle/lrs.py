@@ -6,6 +6,11 @@ with inputs and targets divided by the reference standard deviations sigma_ref
 (no centring; the bias entry is not scaled) and eta living in scaled units.
 eta = mu + L z with L the Cholesky factor of Sigma and z standard normals.
 The corrected q^n and the predictor q^{n*} are pushed into the histories.
+
+A reference scale given as <= 0 is taken from the first prediction: it becomes
+|q^{n*}_i| (1 if that is 0).  The paper scales by the reference trajectories'
+standard deviation, which a server admitting new runs does not have; this
+reading needs zero initial histories.
 """
 
 import numpy as np
@@ -30,6 +35,10 @@ class LRSModel:
         return np.concatenate([(self.q_hist / s).ravel(), qstar / s, (self.qs_hist / s).ravel(), [1.0]])
 
     def predict(self, qstar, z):
+        auto = self.sigma_ref <= 0.0
+        if np.any(auto):
+            a = np.abs(qstar)
+            self.sigma_ref = np.where(auto, np.where(a > 0.0, a, 1.0), self.sigma_ref)
         x = self.inputs(qstar)
         qhat = x @ self.c + self.mu + self.l @ np.asarray(z)
         return self.sigma_ref * qhat

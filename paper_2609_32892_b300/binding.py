@@ -30,7 +30,14 @@ EXPORTED = [
     "lbm_get_populations", "lbm_set_populations", "lbm_get_profile", "lbm_get_step", "lbm_state_bytes",
     "lbm_save", "lbm_load", "lbm_set_graphs", "lbm_profile", "lbm_profile_read", "lbm_launches_per_step",
     "lbm_qoi_eval_static", "lbm_filter_flops_per_step",
+    "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_admit", "lbm_batch_member", "lbm_batch_run",
+    "lbm_batch_poll", "lbm_batch_release", "lbm_batch_stats",
 ]
+
+
+class lbm_completion(C.Structure):
+    _fields_ = [("slot", C.c_int32), ("status", C.c_int32), ("steps", C.c_int64), ("tag", C.c_uint64),
+                ("t_done_ms", C.c_double)]
 
 
 class lbm_qoi_spec(C.Structure):
@@ -81,6 +88,14 @@ def _load():
         "lbm_launches_per_step": [VP, PI64],
         "lbm_qoi_eval_static": [cfg, VP, VP, VP],
         "lbm_filter_flops_per_step": [VP, PD, C.c_int],
+        "lbm_batch_create": [C.c_int32, VP, C.c_size_t, P(VP)],
+        "lbm_batch_destroy": [VP],
+        "lbm_batch_admit": [VP, cfg, PD, I64, C.c_uint64, P(C.c_int32)],
+        "lbm_batch_member": [VP, C.c_int32, P(VP)],
+        "lbm_batch_run": [VP, I64],
+        "lbm_batch_poll": [VP, P(lbm_completion), C.c_int32, P(C.c_int32)],
+        "lbm_batch_release": [VP, C.c_int32],
+        "lbm_batch_stats": [VP, P(C.c_size_t), P(C.c_size_t), P(C.c_int32)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -283,3 +298,53 @@ def lbm_qoi_eval_static(cfg, u_dev_ptr, q_dev_ptr, stream_ptr):
     built-in scratch array (for callers that cannot allocate device memory)."""
     _check(_lib.lbm_qoi_eval_static(C.byref(cfg), C.c_void_p(u_dev_ptr), C.c_void_p(q_dev_ptr),
                                     C.c_void_p(stream_ptr)))
+
+
+# ---------------------------------------------------------------- batches --
+def lbm_batch_create(n_slots, pool_ptr, pool_bytes):
+    h = C.c_void_p()
+    _check(_lib.lbm_batch_create(int(n_slots), C.c_void_p(pool_ptr), pool_bytes, C.byref(h)))
+    return h
+
+
+def lbm_batch_destroy(b):
+    _check(_lib.lbm_batch_destroy(b))
+
+
+def lbm_batch_admit(b, cfg, u0, horizon, tag=0):
+    """Admit a member; returns its slot, or None when it does not fit (LBM_ERR_BUDGET)."""
+    u = _f64(u0)
+    s = C.c_int32()
+    rc = _lib.lbm_batch_admit(b, C.byref(cfg), _ptr(u), int(horizon), int(tag), C.byref(s))
+    if rc == LBM_ERR_BUDGET:
+        return None
+    _check(rc)
+    return s.value
+
+
+def lbm_batch_member(b, slot):
+    h = C.c_void_p()
+    _check(_lib.lbm_batch_member(b, int(slot), C.byref(h)))
+    return h
+
+
+def lbm_batch_run(b, steps):
+    _check(_lib.lbm_batch_run(b, int(steps)))
+
+
+def lbm_batch_poll(b, cap=256):
+    arr = (lbm_completion * cap)()
+    n = C.c_int32()
+    _check(_lib.lbm_batch_poll(b, arr, cap, C.byref(n)))
+    return [dict(slot=arr[i].slot, status=arr[i].status, steps=arr[i].steps, tag=arr[i].tag,
+                 t_done_ms=arr[i].t_done_ms) for i in range(n.value)]
+
+
+def lbm_batch_release(b, slot):
+    _check(_lib.lbm_batch_release(b, int(slot)))
+
+
+def lbm_batch_stats(b):
+    f, l, a = C.c_size_t(), C.c_size_t(), C.c_int32()
+    _check(_lib.lbm_batch_stats(b, C.byref(f), C.byref(l), C.byref(a)))
+    return f.value, l.value, a.value

@@ -216,14 +216,16 @@ __global__ void __launch_bounds__(256) lrs_hist_kernel(Params p, Layout L) {
         if (r < (long long)h * nq) {
             const int kk = (int)(r / nq) + 1, i = (int)(r % nq);
             const long long slot = ((pos - kk) % h + h) % h;
-            xr = L.qh[slot * nq + i] / L.lrs_sigma[i];
+            const double sg = L.lrs_sigma[i];
+            xr = sg > 0.0 ? L.qh[slot * nq + i] / sg : 0.0;  // sigma <= 0: not yet set, histories are zero
         } else if (r < (long long)(h + 1) * nq) {
             continue;
         } else if (r < rows - 1) {
             const long long rr = r - (long long)(h + 1) * nq;
             const int kk = (int)(rr / nq) + 1, i = (int)(rr % nq);
             const long long slot = ((pos - kk) % h + h) % h;
-            xr = L.qsh[slot * nq + i] / L.lrs_sigma[i];
+            const double sg = L.lrs_sigma[i];
+            xr = sg > 0.0 ? L.qsh[slot * nq + i] / sg : 0.0;
         } else {
             xr = 1.0;
         }
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(256) solve_kernel(Params p, Layout L) {
     __shared__ double G[kMaxQoi][kMaxQoi];
     __shared__ double Lc[kMaxQoi][kMaxQoi];
     __shared__ double Li[kMaxQoi][kMaxQoi];
-    __shared__ double q[kMaxQoi], dq[kMaxQoi], gam[kMaxQoi], beta[kMaxQoi], z[kMaxQoi], tmp[kMaxQoi];
+    __shared__ double q[kMaxQoi], dq[kMaxQoi], gam[kMaxQoi], beta[kMaxQoi], z[kMaxQoi], tmp[kMaxQoi], sigs[kMaxQoi];
     __shared__ double wP[kMaxQoi][kMaxQoi + 1];  // sum_y w_j(y) P_k(y), k = 0 (v_x), 1..ns (V_k,x)
     __shared__ int singular;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -352,6 +354,17 @@ __global__ void __launch_bounds__(256) solve_kernel(Params p, Layout L) {
     }
     __syncthreads();
     // 6. coefficient source -> dQ, gamma, beta
+    if (tid < nq && p.to_mode == LBM_TO_LRS) {
+        // a reference scale <= 0 is taken from this step's predictor QoI
+        const int i = tid;
+        double sg = L.lrs_sigma[i];
+        if (!(sg > 0.0)) {
+            sg = fabs(q[i]) > 0.0 ? fabs(q[i]) : 1.0;
+            L.lrs_sigma[i] = sg;
+        }
+        sigs[i] = sg;
+    }
+    __syncthreads();
     if (tid < nq) {
         const int i = tid;
         double ginv_ii = 0.0;
@@ -361,8 +374,8 @@ __global__ void __launch_bounds__(256) solve_kernel(Params p, Layout L) {
         if (p.to_mode == LBM_TO_LRS) {
             double qh = tmp[i] + L.lrs_mu[i];
             for (int j = 0; j < nq; ++j)
-                qh += (q[j] / L.lrs_sigma[j]) * L.lrs_C[((size_t)p.h * nq + j) * nq + i] + L.lrs_L[(size_t)i * nq + j] * z[j];
-            const double qn = L.lrs_sigma[i] * qh;
+                qh += (q[j] / sigs[j]) * L.lrs_C[((size_t)p.h * nq + j) * nq + i] + L.lrs_L[(size_t)i * nq + j] * z[j];
+            const double qn = sigs[i] * qh;
             d = qn - q[i];
             tmp[i] = qn;  // corrected QoI for the history
             g = singular ? 0.0 : d * ginv_ii;

@@ -666,8 +666,11 @@ int lbm_set_lrs(lbm_ctx* c, const double* C, const double* mu, const double* Sig
     if (p.to_mode != LBM_TO_LRS) return fail(c, LBM_ERR_STATE, "lbm_set_lrs needs to_mode LBM_TO_LRS");
     if (!C || !mu || !Sigma || !sigma_ref) return fail(c, LBM_ERR_ARG, "NULL coefficient array");
     const int n = p.n_q;
-    for (int i = 0; i < n; ++i)
-        if (!(sigma_ref[i] > 0.0)) return fail(c, LBM_ERR_ARG, "sigma_ref[%d] must be > 0", i);
+    for (int i = 0; i < n; ++i) {
+        if (!(sigma_ref[i] == sigma_ref[i])) return fail(c, LBM_ERR_ARG, "sigma_ref[%d] is NaN", i);
+        if (sigma_ref[i] <= 0.0 && (q_hist || qs_hist))
+            return fail(c, LBM_ERR_ARG, "sigma_ref <= 0 (taken from the first step) needs zero initial histories");
+    }
     // Cholesky of Sigma (symmetric positive definite required)
     std::vector<double> Lh((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i)

@@ -1,0 +1,160 @@
+"""Continuous-batching ensemble server over the C batch API (lbm_batch_*).
+
+Requests (LES ensemble members of different grids, seeds and horizons) arrive
+over time.  The server admits a request as soon as a slot and enough pool
+memory are free (first come, first served), queues `chunk` steps of every
+active member per round so that members admitted while others run overlap on
+the device, and collects completions without blocking.  Per request it
+records the queueing delay, the completion time (device clock) and the
+latency per simulated time unit.
+
+Scheduling and marshalling only: every step runs in liblbm.so.
+"""
+
+import collections
+import math
+import time
+
+import numpy as np
+
+import synthetic
+from . import binding as B
+
+
+def steps_per_tu(wl):
+    """Lattice steps per time unit: C_u/C_l (2-D Kolmogorov), H/u_tau (3-D channel)."""
+    if wl["dim"] == 2:
+        return synthetic.kolmogorov_lattice(wl["nx"])["steps_per_tu"]
+    return synthetic.channel_lattice(wl["ny"])["steps_per_tu"]
+
+
+class EnsembleServer:
+    def __init__(self, pool_bytes, n_slots, device="cuda"):
+        import torch
+
+        self.torch = torch
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=device)
+        torch.cuda.synchronize(self.pool.device)
+        self.batch = B.lbm_batch_create(n_slots, self.pool.data_ptr(), int(pool_bytes))
+        torch.cuda.synchronize(self.pool.device)
+        self.t_epoch = time.perf_counter()  # device time 0 of t_done_ms
+
+    def close(self):
+        if self.batch is not None:
+            B.lbm_batch_destroy(self.batch)
+            self.batch = None
+
+    def admit(self, wl, tag):
+        cfg = B.config_from_workload(wl, member=tag)
+        slot = B.lbm_batch_admit(self.batch, cfg, synthetic.initial_velocity(wl), wl["steps"], tag)
+        if slot is None:
+            return None
+        if wl["to_mode"] == "lrs":
+            nq = len(wl["qois"]) + wl["n_mp"]
+            c, mu, sig = synthetic.synthetic_lrs(nq, wl["h"], wl["seed"])
+            # reference scales taken from each member's first predictor QoIs
+            B.lbm_set_lrs(B.lbm_batch_member(self.batch, slot), c, mu, sig, np.zeros(nq))
+        return slot
+
+    def serve(self, requests, chunk=32, keep_qoi=False, realtime=True):
+        """Run a request list (dicts with arrival_s, steps, ...) to completion.
+
+        realtime=True honours the arrival times against the wall clock;
+        False admits every request as soon as it fits (offline batch)."""
+        torch = self.torch
+        pending = collections.deque(sorted(range(len(requests)), key=lambda i: requests[i].get("arrival_s", 0.0)))
+        active = {}
+        out = {}
+        t0 = time.perf_counter()
+        rounds = 0
+        while pending or active:
+            now = time.perf_counter() - t0
+            while pending:
+                i = pending[0]
+                r = requests[i]
+                if realtime and r.get("arrival_s", 0.0) > now:
+                    break
+                slot = self.admit(r, i)
+                if slot is None:
+                    break  # head of the queue waits for memory or a slot
+                active[slot] = i
+                out[i] = {"arrival_s": r.get("arrival_s", 0.0) if realtime else 0.0, "admit_s": now,
+                          "steps": r["steps"], "tu": r["steps"] / steps_per_tu(r),
+                          "nodes": r["nx"] * r["ny"] * r["nz"], "storage": r.get("storage", "fp32")}
+                pending.popleft()
+            if active:
+                B.lbm_batch_run(self.batch, chunk)
+                rounds += 1
+                # keep the host at most one round ahead of the device
+                torch.cuda.synchronize(self.pool.device)
+                for c in B.lbm_batch_poll(self.batch):
+                    i = c["tag"]
+                    rec = out[i]
+                    rec["done_s"] = (self.t_epoch + c["t_done_ms"] * 1e-3) - t0
+                    rec["status"] = c["status"]
+                    if keep_qoi:
+                        ctx = B.lbm_batch_member(self.batch, c["slot"])
+                        rows, _ = B.lbm_qoi(ctx, 2 + 3 * (len(requests[i]["qois"]) + requests[i]["n_mp"]),
+                                            capacity=max(1, requests[i]["steps"]))
+                        rec["qoi"] = rows
+                    B.lbm_batch_release(self.batch, c["slot"])
+                    del active[c["slot"]]
+            elif pending and realtime:
+                time.sleep(max(0.0, min(0.01, requests[pending[0]]["arrival_s"] - now)))
+        wall = time.perf_counter() - t0
+        return out, wall, rounds
+
+
+def summarize(out, wall):
+    lat = np.array([(r["done_s"] - r["arrival_s"]) / r["tu"] for r in out.values()])
+    queue = np.array([r["admit_s"] - r["arrival_s"] for r in out.values()])
+    member_steps = sum(r["steps"] for r in out.values())
+    node_steps = sum(r["steps"] * r["nodes"] for r in out.values())
+    return {
+        "requests": len(out),
+        "wall_s": round(wall, 3),
+        "member_steps_per_s": round(member_steps / wall, 1),
+        "mlups": round(node_steps / wall / 1e6, 1),
+        "latency_s_per_tu_p50": float(np.percentile(lat, 50)),
+        "latency_s_per_tu_p99": float(np.percentile(lat, 99)),
+        "queue_s_p50": float(np.percentile(queue, 50)),
+        "queue_s_p99": float(np.percentile(queue, 99)),
+        "unstable": int(sum(1 for r in out.values() if r.get("status", 0) != 0)),
+    }
+
+
+def serial_baseline(requests, device="cuda"):
+    """One request at a time (each to completion, in arrival order): the
+    throughput a one-run-at-a-time workflow gets on the same device."""
+    import torch
+
+    from .sim import LbmSim
+
+    t0 = time.perf_counter()
+    steps = 0
+    nodes = 0
+    for i, r in enumerate(requests):
+        s = LbmSim(r, member=i, device=device)
+        s.init(synthetic.initial_velocity(r))
+        if r["to_mode"] == "lrs":
+            nq = len(r["qois"]) + r["n_mp"]
+            c, mu, sig = synthetic.synthetic_lrs(nq, r["h"], r["seed"])
+            s.set_lrs(c, mu, sig, np.zeros(nq))
+        s.step(r["steps"])
+        s.sync()
+        s.close()
+        steps += r["steps"]
+        nodes += r["steps"] * r["nx"] * r["ny"] * r["nz"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"requests": len(requests), "wall_s": round(wall, 3), "member_steps_per_s": round(steps / wall, 1),
+            "mlups": round(nodes / wall / 1e6, 1)}
+
+
+def scaled_mix(n, seed, rate, horizon_scale=1.0, storage="fp32"):
+    """The serving mix of the benchmark configuration with horizons scaled."""
+    reqs = synthetic.workloads.serving_mix(n, seed, rate)
+    for r in reqs:
+        r["steps"] = max(2, int(math.ceil(r["steps"] * horizon_scale)))
+        r["storage"] = storage
+    return reqs

@@ -1,0 +1,110 @@
+"""Ensemble batches: a member's results are the same alone and in a mix,
+admission is bounded by the pool budget, and the continuous-batching server
+runs a request stream to completion."""
+
+import numpy as np
+import pytest
+
+import synthetic
+from gpu_common import nq_of
+
+pytestmark = pytest.mark.gpu
+
+
+def _members():
+    a = synthetic.workload("C2", nx=48, ny=40, h=3, steps=9, seed=11)
+    b = synthetic.workload("C3", nx=20, ny=20, nz=12, h=2, steps=6, seed=12)
+    c = synthetic.workload("C1", nx=30, ny=26, steps=7, seed=13, storage="fp16")
+    return [a, b, c]
+
+
+def _alone(wl, member):
+    from paper_2609_32892_b300 import LbmSim
+
+    s = LbmSim(wl, member=member)
+    s.init(synthetic.initial_velocity(wl))
+    if wl["to_mode"] == "lrs":
+        nq = nq_of(wl)
+        c, mu, sig = synthetic.synthetic_lrs(nq, wl["h"], wl["seed"])
+        s.set_lrs(c, mu, sig, np.zeros(nq))
+    s.step(wl["steps"])
+    s.sync()
+    rows = s.qoi()
+    f = s.populations()
+    s.close()
+    return rows, f
+
+
+def test_member_results_identical_alone_and_in_mix():
+    import torch
+
+    from paper_2609_32892_b300 import binding as B
+
+    wls = _members()
+    alone = [_alone(w, i) for i, w in enumerate(wls)]
+    pool_bytes = sum(B.lbm_required_bytes(B.config_from_workload(w)) for w in wls) + (1 << 20)
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
+    b = B.lbm_batch_create(4, pool.data_ptr(), pool_bytes)
+    slots = []
+    for i, w in enumerate(wls):
+        s = B.lbm_batch_admit(b, B.config_from_workload(w, member=i), synthetic.initial_velocity(w), w["steps"], i)
+        assert s is not None
+        if w["to_mode"] == "lrs":
+            nq = nq_of(w)
+            c, mu, sig = synthetic.synthetic_lrs(nq, w["h"], w["seed"])
+            B.lbm_set_lrs(B.lbm_batch_member(b, s), c, mu, sig, np.zeros(nq))
+        slots.append(s)
+    done = {}
+    for _ in range(10):
+        B.lbm_batch_run(b, 2)
+        torch.cuda.synchronize()
+        for comp in B.lbm_batch_poll(b):
+            done[comp["tag"]] = comp
+    assert sorted(done) == [0, 1, 2]
+    for i, (w, s) in enumerate(zip(wls, slots)):
+        assert done[i]["status"] == 0 and done[i]["steps"] == w["steps"]
+        ctx = B.lbm_batch_member(b, s)
+        q = 9 if w["dim"] == 2 else 19
+        f = B.lbm_get_populations(ctx, q, (w["nz"], w["ny"], w["nx"]))
+        np.testing.assert_array_equal(f, alone[i][1])
+        if nq_of(w):
+            rows, _ = B.lbm_qoi(ctx, 2 + 3 * nq_of(w))
+            np.testing.assert_array_equal(rows, alone[i][0])
+        B.lbm_batch_release(b, s)
+    assert B.lbm_batch_stats(b)[2] == 0
+    B.lbm_batch_destroy(b)
+
+
+def test_admission_by_budget():
+    import torch
+
+    from paper_2609_32892_b300 import binding as B
+
+    w = synthetic.workload("C2", nx=64, ny=64, h=3, steps=4)
+    need = B.lbm_required_bytes(B.config_from_workload(w))
+    pool_bytes = need + need // 2
+    pool = torch.empty(pool_bytes + 4096, dtype=torch.uint8, device="cuda")
+    b = B.lbm_batch_create(8, pool.data_ptr(), pool_bytes)
+    s0 = B.lbm_batch_admit(b, B.config_from_workload(w), synthetic.initial_velocity(w), 4, 0)
+    assert s0 is not None
+    assert B.lbm_batch_admit(b, B.config_from_workload(w), synthetic.initial_velocity(w), 4, 1) is None
+    B.lbm_batch_release(b, s0)
+    assert B.lbm_batch_admit(b, B.config_from_workload(w), synthetic.initial_velocity(w), 4, 2) is not None
+    B.lbm_batch_destroy(b)
+
+
+def test_server_runs_a_request_stream():
+    from paper_2609_32892_b300 import serve
+
+    reqs = serve.scaled_mix(10, seed=5, rate=200.0, horizon_scale=0.01)
+    srv = serve.EnsembleServer(pool_bytes=2 << 30, n_slots=6)
+    out, wall, rounds = srv.serve(reqs, chunk=8, keep_qoi=True)
+    srv.close()
+    assert len(out) == 10
+    for i, r in out.items():
+        assert r["status"] == 0
+        assert r["done_s"] >= r["admit_s"] - 1e-3
+        assert r["qoi"].shape[0] == reqs[i]["steps"]
+        assert np.all(np.isfinite(r["qoi"]))
+    s = serve.summarize(out, wall)
+    assert s["member_steps_per_s"] > 0 and s["latency_s_per_tu_p99"] >= s["latency_s_per_tu_p50"]

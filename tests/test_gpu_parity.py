@@ -166,3 +166,13 @@ def test_graph_replay_equals_eager_launches():
     np.testing.assert_array_equal(ra, rb)
     np.testing.assert_array_equal(u_a, u_b)
     np.testing.assert_array_equal(rho_a, rho_b)
+
+
+def test_lrs_reference_scales_from_first_step():
+    """sigma_ref <= 0 is taken from the first predictor QoIs, on both sides."""
+    wl = synthetic.workload("C2", nx=36, ny=30, h=2)
+    lrs = lrs_inputs(wl, np.zeros(nq_of(wl)))
+    _, ro, rho_o, u_o = run_oracle(wl, 15, lrs=lrs)
+    _, rg, rho_g, u_g = run_gpu(wl, 15, lrs=lrs)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)

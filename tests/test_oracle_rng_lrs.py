@@ -106,3 +106,15 @@ def test_ks_matches_scipy():
         a = rng.normal(size=n1)
         b = rng.normal(0.3, 1.2, size=n2)
         assert ks_distance(a, b) == pytest.approx(scipy.stats.ks_2samp(a, b).statistic, abs=1e-14)
+
+
+def test_lrs_reference_scale_from_first_prediction():
+    nq, h = 3, 2
+    rows = (2 * h + 1) * nq + 1
+    c = np.zeros((rows, nq))
+    c[h * nq:(h + 1) * nq] = np.eye(nq)
+    m = LRSModel(c, np.zeros(nq), 1e-300 * np.eye(nq), np.array([0.0, 2.0, -1.0]), h)
+    qs = np.array([-4.0, 3.0, 0.0])
+    out = m.predict(qs, np.zeros(nq))
+    np.testing.assert_array_equal(m.sigma_ref, [4.0, 2.0, 1.0])
+    np.testing.assert_allclose(out, qs, rtol=1e-15)

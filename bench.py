@@ -101,6 +101,18 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """Maximum of a per-rank float over all ranks (barrier included): the
+    slowest replica sets the timed region of a multi-GPU run."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _lrs_for(wl):
     nq = len(wl["qois"]) + wl["n_mp"]
     c, mu, sig = synthetic.synthetic_lrs(nq, wl["h"], wl["seed"])
@@ -169,10 +181,7 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     B.lbm_sync(sim.ctx)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
+        ms = max_over_ranks(ms, dev)
     ms_per_step = ms / args.steps
     mlups = world * n_nodes * args.steps / (ms * 1e-3) / 1e6
 

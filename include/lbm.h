@@ -186,9 +186,10 @@ int lbm_get_profile(lbm_ctx* ctx, double* prof, int64_t* nsteps);
 /* Steps completed (device counter; synchronises). */
 int lbm_get_step(lbm_ctx* ctx, int64_t* step);
 
-/* Checkpoint: the whole device state (populations, counters, LRS histories,
- * QoI ring, profile) as an opaque host blob of lbm_state_bytes bytes.
- * lbm_load requires a context created with the same configuration. */
+/* Checkpoint: the whole device state (populations, counters, LRS model and
+ * histories, tracking reference, QoI ring, profile) as an opaque host blob of
+ * lbm_state_bytes bytes.  lbm_load requires a context created with the same
+ * configuration and needs no other set-up call before stepping. */
 int lbm_state_bytes(lbm_ctx* ctx, size_t* bytes);
 int lbm_save(lbm_ctx* ctx, void* host_buf, size_t bytes);
 int lbm_load(lbm_ctx* ctx, const void* host_buf, size_t bytes);

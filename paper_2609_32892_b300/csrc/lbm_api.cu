@@ -519,7 +519,7 @@ static void widen(const std::vector<char>& raw, int dim, int q, size_t N, double
 
 // checkpoint blob: magic, sizes, DevState, populations, histories, ring, profile, cursor
 struct BlobHead {
-    uint64_t magic, fbytes, hbytes, rbytes, pbytes;
+    uint64_t magic, fbytes, hbytes, rbytes, pbytes, cbytes, tbytes;
     int64_t host_read;
 };
 static const uint64_t kMagic = 0x4c424d544f303031ULL;
@@ -531,7 +531,22 @@ static void blob_sizes(lbm_ctx* c, BlobHead* h) {
     h->hbytes = p.h > 0 ? sizeof(double) * (size_t)p.h * p.n_q : 0;
     h->rbytes = c->L.ring ? sizeof(double) * (size_t)p.ring_cap * p.row_len : 0;
     h->pbytes = c->L.profile ? sizeof(double) * (size_t)p.ny : 0;
+    // LRS model: C, mu, chol(Sigma), sigma_ref (possibly set from the first step)
+    h->cbytes = p.h > 0 ? sizeof(double) * (((size_t)(2 * p.h + 1) * p.n_q + 1) * p.n_q + 2 * (size_t)p.n_q +
+                                            (size_t)p.n_q * p.n_q)
+                        : 0;
+    h->tbytes = p.track_len > 0 ? sizeof(double) * (size_t)p.track_len * p.n_q : 0;
     h->host_read = c->host_read;
+}
+
+// LRS arrays in blob order
+static void lrs_parts(lbm_ctx* c, void* ptr[4], size_t bytes[4]) {
+    const Params& p = c->p;
+    const size_t nq = (size_t)p.n_q;
+    ptr[0] = c->L.lrs_C;     bytes[0] = sizeof(double) * ((size_t)(2 * p.h + 1) * nq + 1) * nq;
+    ptr[1] = c->L.lrs_mu;    bytes[1] = sizeof(double) * nq;
+    ptr[2] = c->L.lrs_L;     bytes[2] = sizeof(double) * nq * nq;
+    ptr[3] = c->L.lrs_sigma; bytes[3] = sizeof(double) * nq;
 }
 
 // ================================================================== C ABI ==
@@ -862,7 +877,7 @@ int lbm_state_bytes(lbm_ctx* c, size_t* bytes) {
     if (!c || !bytes) return fail(c, LBM_ERR_ARG, "NULL argument");
     BlobHead h;
     blob_sizes(c, &h);
-    *bytes = sizeof h + sizeof(DevState) + h.fbytes + 2 * h.hbytes + h.rbytes + h.pbytes;
+    *bytes = sizeof h + sizeof(DevState) + h.fbytes + 2 * h.hbytes + h.rbytes + h.pbytes + h.cbytes + h.tbytes;
     return LBM_OK;
 }
 
@@ -890,7 +905,20 @@ int lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
         CK(c, cudaMemcpyAsync(o, c->L.ring, h.rbytes, cudaMemcpyDeviceToHost, c->stream));
         o += h.rbytes;
     }
-    if (h.pbytes) CK(c, cudaMemcpyAsync(o, c->L.profile, h.pbytes, cudaMemcpyDeviceToHost, c->stream));
+    if (h.pbytes) {
+        CK(c, cudaMemcpyAsync(o, c->L.profile, h.pbytes, cudaMemcpyDeviceToHost, c->stream));
+        o += h.pbytes;
+    }
+    if (h.cbytes) {
+        void* ptr[4];
+        size_t nb[4];
+        lrs_parts(c, ptr, nb);
+        for (int k = 0; k < 4; ++k) {
+            CK(c, cudaMemcpyAsync(o, ptr[k], nb[k], cudaMemcpyDeviceToHost, c->stream));
+            o += nb[k];
+        }
+    }
+    if (h.tbytes) CK(c, cudaMemcpyAsync(o, c->L.track, h.tbytes, cudaMemcpyDeviceToHost, c->stream));
     return sync_check(c);
 }
 
@@ -903,7 +931,7 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t bytes) {
     memcpy(&h, buf, sizeof h);
     blob_sizes(c, &mine);
     if (h.magic != kMagic || h.fbytes != mine.fbytes || h.hbytes != mine.hbytes || h.rbytes != mine.rbytes ||
-        h.pbytes != mine.pbytes)
+        h.pbytes != mine.pbytes || h.cbytes != mine.cbytes || h.tbytes != mine.tbytes)
         return fail(c, LBM_ERR_ARG, "checkpoint does not match this configuration");
     const char* o = (const char*)buf + sizeof h;
     CK(c, cudaMemcpyAsync(c->L.st, o, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
@@ -921,7 +949,20 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t bytes) {
         CK(c, cudaMemcpyAsync(c->L.ring, o, h.rbytes, cudaMemcpyHostToDevice, c->stream));
         o += h.rbytes;
     }
-    if (h.pbytes) CK(c, cudaMemcpyAsync(c->L.profile, o, h.pbytes, cudaMemcpyHostToDevice, c->stream));
+    if (h.pbytes) {
+        CK(c, cudaMemcpyAsync(c->L.profile, o, h.pbytes, cudaMemcpyHostToDevice, c->stream));
+        o += h.pbytes;
+    }
+    if (h.cbytes) {
+        void* ptr[4];
+        size_t nb[4];
+        lrs_parts(c, ptr, nb);
+        for (int k = 0; k < 4; ++k) {
+            CK(c, cudaMemcpyAsync(ptr[k], o, nb[k], cudaMemcpyHostToDevice, c->stream));
+            o += nb[k];
+        }
+    }
+    if (h.tbytes) CK(c, cudaMemcpyAsync(c->L.track, o, h.tbytes, cudaMemcpyHostToDevice, c->stream));
     c->host_read = h.host_read;
     c->lrs_set = c->lrs_set || c->p.h > 0;
     return sync_check(c);

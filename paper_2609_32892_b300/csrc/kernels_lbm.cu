@@ -217,33 +217,15 @@ __device__ __forceinline__ float wale_nut(const Params& p, const float* __restri
     return p.c_wale2 * sdsd * sqrtf(sdsd) / den;
 }
 
-// One fused predictor step per node: pull, moments, substrate tau_eff, BGK
-// (Eq. LES-1) and the body force (EDM: Eq. collide-and-stream; or Guo),
-// written to dst.  With fields != 0 the density and the predictor velocity
-// v^{p*} = (rho u + F)/rho are stored for the TO phase.
-template <int DIM, typename T, int SUB>
-__global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
-                                                      float* __restrict__ rho_out, float* __restrict__ vps,
-                                                      const float* __restrict__ vn, const float* __restrict__ kolmo,
-                                                      DevState* st, int fields) {
+// The fused predictor step of one node from its pulled populations g (in
+// place): moments, substrate tau_eff, BGK (Eq. LES-1) and the body force (EDM:
+// Eq. collide-and-stream; or Guo).  Returns rho and the predictor velocity
+// v^{p*} = (rho u + F)/rho for the TO phase.
+template <int DIM, int SUB>
+__device__ __forceinline__ void collide_node(const Params& p, float* g, int x, int y, int z,
+                                             const float* __restrict__ vn, const float* __restrict__ kolmo,
+                                             DevState* st, float& rho_o, float& vx_o, float& vy_o, float& vz_o) {
     using LT = Lat<DIM>;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= p.n) return;
-    const int N = (int)p.n;
-    const int x = n % p.nx;
-    const int t = n / p.nx;
-    const int y = t % p.ny;
-    const int z = t / p.ny;
-    if (p.walls && (y == 0 || y == p.ny - 1)) {
-        if (fields) {
-            rho_out[n] = 1.f;
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) vps[(size_t)a * N + n] = 0.f;
-        }
-        return;
-    }
-    float g[LT::Q];
-    pull<DIM, T>(p, src, x, y, z, n, g);
     const Macro m = macros_of<DIM>(p, g, kolmo, y);
     const float ux = m.ux, uy = m.uy, uz = m.uz;
     const float uu = ux * ux + uy * uy + uz * uz;
@@ -309,14 +291,161 @@ __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restr
             g[i] = g[i] + (geq[i] - g[i]) * om + s;
         }
     }
+    const float inv = 1.0f / m.rho;
+    rho_o = m.rho;
+    vx_o = (m.jx + fx) * inv;
+    vy_o = (m.jy + fy) * inv;
+    vz_o = (m.jz + fz) * inv;
+}
+
+// One thread per node: pull, collide_node, store (and the TO fields).
+template <int DIM, typename T, int SUB>
+__global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
+                                                      float* __restrict__ rho_out, float* __restrict__ vps,
+                                                      const float* __restrict__ vn, const float* __restrict__ kolmo,
+                                                      DevState* st, int fields) {
+    using LT = Lat<DIM>;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const int N = (int)p.n;
+    const int x = n % p.nx;
+    const int t = n / p.nx;
+    const int y = t % p.ny;
+    const int z = t / p.ny;
+    if (p.walls && (y == 0 || y == p.ny - 1)) {
+        if (fields) {
+            rho_out[n] = 1.f;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) vps[(size_t)a * N + n] = 0.f;
+        }
+        return;
+    }
+    float g[LT::Q];
+    pull<DIM, T>(p, src, x, y, z, n, g);
+    float r, vx, vy, vz;
+    collide_node<DIM, SUB>(p, g, x, y, z, vn, kolmo, st, r, vx, vy, vz);
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) st_<T>(dst + (size_t)i * N + n, g[i]);
     if (fields) {
-        const float inv = 1.0f / m.rho;
-        rho_out[n] = m.rho;
-        vps[n] = (m.jx + fx) * inv;
-        vps[(size_t)N + n] = (m.jy + fy) * inv;
-        if (DIM == 3) vps[(size_t)2 * N + n] = (m.jz + fz) * inv;
+        rho_out[n] = r;
+        vps[n] = vx;
+        vps[(size_t)N + n] = vy;
+        if (DIM == 3) vps[(size_t)2 * N + n] = vz;
+    }
+}
+
+// ---- two nodes per thread (nx even): aligned 2-element population loads ----
+template <typename T> struct Vec2;
+template <> struct Vec2<float> {
+    using V = float2;
+    static __device__ __forceinline__ void ld(const float* p, float& a, float& b) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        a = v.x; b = v.y;
+    }
+    static __device__ __forceinline__ void st(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+};
+template <> struct Vec2<__half> {
+    static __device__ __forceinline__ void ld(const __half* p, float& a, float& b) {
+        const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+        a = v.x; b = v.y;
+    }
+    static __device__ __forceinline__ void st(__half* p, float a, float b) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <> struct Vec2<__nv_bfloat16> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float& a, float& b) {
+        const float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+        a = v.x; b = v.y;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+// Pull for the node pair (x0, x0+1), x0 even: every population row is read as
+// aligned pairs; the neighbour one column to the left (right) comes from the
+// previous (next) lane's pair by warp shuffle, or from memory at a row or
+// warp edge.  Every lane of the warp runs the shuffles (dead lanes re-read a
+// valid pair), so the masks are always full.
+template <int DIM, typename T>
+__device__ __forceinline__ void pull2(const Params& p, const T* __restrict__ src, int x0, int y, int z, int n0,
+                                      float* g0, float* g1) {
+    using LT = Lat<DIM>;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int N = (int)p.n;
+    const int lane = threadIdx.x & 31;
+    const int ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
+    const int zm = DIM == 3 ? wrap(z - 1, nz) : 0, zp = DIM == 3 ? wrap(z + 1, nz) : 0;
+    const bool wall_lo = p.walls && (y == 1);
+    const bool wall_hi = p.walls && (y == ny - 2);
+    const bool left_edge = (lane == 0) || (x0 == 0);
+    const bool right_edge = (lane == 31) || (x0 + 2 >= nx);
+    const int xl = wrap(x0 - 1, nx), xr = x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2;
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+        const int ys = cy == 0 ? y : (cy > 0 ? ym : yp);
+        const int zs = cz == 0 ? z : (cz > 0 ? zm : zp);
+        const T* row = src + (size_t)i * N + ((size_t)zs * ny + ys) * nx;
+        float a, b;
+        Vec2<T>::ld(row + x0, a, b);
+        if (cx == 1) {  // source x - 1: (x0 - 1, x0)
+            float prev = __shfl_up_sync(0xffffffffu, b, 1);
+            if (left_edge) prev = ldg_<T>(row + xl);
+            b = a;
+            a = prev;
+        } else if (cx == -1) {  // source x + 1: (x0 + 1, x0 + 2)
+            float next = __shfl_down_sync(0xffffffffu, a, 1);
+            if (right_edge) next = ldg_<T>(row + xr);
+            a = b;
+            b = next;
+        }
+        const bool bb = (cy == 1 && wall_lo) || (cy == -1 && wall_hi);
+        if (bb) Vec2<T>::ld(src + (size_t)LT::opp(i) * N + n0, a, b);
+        g0[i] = a;
+        g1[i] = b;
+    }
+}
+
+template <int DIM, typename T, int SUB>
+__global__ void __launch_bounds__(128) collide2_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
+                                                       float* __restrict__ rho_out, float* __restrict__ vps,
+                                                       const float* __restrict__ vn, const float* __restrict__ kolmo,
+                                                       DevState* st, int fields) {
+    using LT = Lat<DIM>;
+    const long long npair = p.n / 2;
+    long long pi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = pi < npair;
+    if (!live) pi = npair - 1;
+    const int N = (int)p.n;
+    const int n0 = (int)(2 * pi);
+    const int x0 = n0 % p.nx;
+    const int t = n0 / p.nx;
+    const int y = t % p.ny;
+    const int z = t / p.ny;
+    float g0[LT::Q], g1[LT::Q];
+    pull2<DIM, T>(p, src, x0, y, z, n0, g0, g1);
+    if (!live) return;
+    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+    if (solid) {
+        if (fields) {
+            *reinterpret_cast<float2*>(rho_out + n0) = make_float2(1.f, 1.f);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) *reinterpret_cast<float2*>(vps + (size_t)a * N + n0) = make_float2(0.f, 0.f);
+        }
+        return;
+    }
+    float r0, vx0, vy0, vz0, r1, vx1, vy1, vz1;
+    collide_node<DIM, SUB>(p, g0, x0, y, z, vn, kolmo, st, r0, vx0, vy0, vz0);
+    collide_node<DIM, SUB>(p, g1, x0 + 1, y, z, vn, kolmo, st, r1, vx1, vy1, vz1);
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) Vec2<T>::st(dst + (size_t)i * N + n0, g0[i], g1[i]);
+    if (fields) {
+        *reinterpret_cast<float2*>(rho_out + n0) = make_float2(r0, r1);
+        *reinterpret_cast<float2*>(vps + n0) = make_float2(vx0, vx1);
+        *reinterpret_cast<float2*>(vps + (size_t)N + n0) = make_float2(vy0, vy1);
+        if (DIM == 3) *reinterpret_cast<float2*>(vps + (size_t)2 * N + n0) = make_float2(vz0, vz1);
     }
 }
 
@@ -358,6 +487,111 @@ __global__ void __launch_bounds__(256) apply_kernel(Params p, T* __restrict__ f,
         const float cd = cx * dx + cy * dy + cz * dz;
         T* q = f + (size_t)i * N + n;
         st_<T>(q, ld_<T>(q) + LT::w(i) * r * (3.0f * cd + 4.5f * cd * (2.0f * cu + cd) - 1.5f * du));
+    }
+}
+
+// Four nodes of one row per thread (nx % 4 == 0): 16-byte (FP32) or 8-byte
+// (16-bit) population accesses and 16-byte field and sensitivity loads.
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Vec4<__half> {
+    static __device__ __forceinline__ void ld(const __half* p, float* v) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(__half* p, const float* v) {
+        const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+        uint2 q;
+        q.x = *reinterpret_cast<const unsigned*>(&a);
+        q.y = *reinterpret_cast<const unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = q;
+    }
+};
+template <> struct Vec4<__nv_bfloat16> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float* v) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, const float* v) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 q;
+        q.x = *reinterpret_cast<const unsigned*>(&a);
+        q.y = *reinterpret_cast<const unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = q;
+    }
+};
+
+__device__ __forceinline__ void ld4f(const float* p, float* v) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(128) apply4_kernel(Params p, T* __restrict__ f, const float* __restrict__ rho,
+                                                     const float* __restrict__ vps, VPtrs vk,
+                                                     const double* __restrict__ beta,
+                                                     const double* __restrict__ w_mp) {
+    using LT = Lat<DIM>;
+    const long long n4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n4 >= p.n / 4) return;
+    const size_t N = (size_t)p.n;
+    const size_t n0 = (size_t)n4 * 4;
+    const int y = (int)((n0 / p.nx) % p.ny);
+    if (p.walls && (y == 0 || y == p.ny - 1)) return;
+    float dx[4] = {0.f, 0.f, 0.f, 0.f}, dy[4] = {0.f, 0.f, 0.f, 0.f}, dz[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < p.n_s; ++k) {
+        const float b = (float)beta[k];
+        const float* v = vk.v[k];
+        float a[4];
+        ld4f(v + n0, a);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dx[e] += b * a[e];
+        ld4f(v + N + n0, a);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dy[e] += b * a[e];
+        if (DIM == 3) {
+            ld4f(v + 2 * N + n0, a);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dz[e] += b * a[e];
+        }
+    }
+    float mp = 0.f;
+    for (int j = 0; j < p.n_mp; ++j) mp += (float)(beta[p.n_s + j] * w_mp[(size_t)j * p.ny + y]);
+    float r[4], ux[4], uy[4], uz[4] = {0.f, 0.f, 0.f, 0.f}, du[4];
+    ld4f(rho + n0, r);
+    ld4f(vps + n0, ux);
+    ld4f(vps + N + n0, uy);
+    if (DIM == 3) ld4f(vps + 2 * N + n0, uz);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        dx[e] += mp;
+        du[e] = dx[e] * (2.0f * ux[e] + dx[e]) + dy[e] * (2.0f * uy[e] + dy[e]) + dz[e] * (2.0f * uz[e] + dz[e]);
+    }
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+        T* q = f + (size_t)i * N + n0;
+        float g[4];
+        Vec4<T>::ld(q, g);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float cu = cx * ux[e] + cy * uy[e] + cz * uz[e];
+            const float cd = cx * dx[e] + cy * dy[e] + cz * dz[e];
+            g[e] += LT::w(i) * r[e] * (3.0f * cd + 4.5f * cd * (2.0f * cu + cd) - 1.5f * du[e]);
+        }
+        Vec4<T>::st(q, g);
     }
 }
 
@@ -453,6 +687,19 @@ static void do_collide_d(const Params& p, const Layout& L, int src, cudaStream_t
     const int fields = p.to_mode != LBM_TO_OFF;
     const T* a = (const T*)L.f[src];
     T* b = (T*)L.f[1 - src];
+    if (p.nx % 2 == 0 && p.substrate != LBM_SUBSTRATE_WALE) {
+        // node pairs: nx even keeps every pair inside one row and 2-aligned
+        // (WALE's gradient loads push the pair kernel to 128 registers, where
+        // the single-node kernel is faster)
+        const unsigned g2 = grid_of(p.n / 2, 128);
+        if (p.substrate == LBM_SUBSTRATE_SMAG)
+            collide2_kernel<DIM, T, LBM_SUBSTRATE_SMAG><<<g2, 128, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
+        else if (p.substrate == LBM_SUBSTRATE_WALE)
+            collide2_kernel<DIM, T, LBM_SUBSTRATE_WALE><<<g2, 128, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
+        else
+            collide2_kernel<DIM, T, LBM_SUBSTRATE_NONE><<<g2, 128, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
+        return;
+    }
     const unsigned gr = grid_of(p.n, 256);
     if (p.substrate == LBM_SUBSTRATE_SMAG)
         collide_kernel<DIM, T, LBM_SUBSTRATE_SMAG><<<gr, 256, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
@@ -478,6 +725,13 @@ static void do_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) 
     for (int k = 0; k < p.n_s; ++k) {
         const int slot = p.qoi_filter_slot[k];
         vk.v[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
+    }
+    if (p.nx % 4 == 0) {
+        if (p.dim == 2)
+            apply4_kernel<2, T><<<grid_of(p.n / 4, 128), 128, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
+        else
+            apply4_kernel<3, T><<<grid_of(p.n / 4, 128), 128, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
+        return;
     }
     if (p.dim == 2)
         apply_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);

@@ -77,10 +77,12 @@ def test_kolmogorov_gamma_2d(forcing):
         assert list(r[1 + 2 * nq:1 + 3 * nq]) == [wl["gamma_std"] * zz for zz in z]
 
 
-def test_kolmogorov_smagorinsky_lrs_2d():
+@pytest.mark.parametrize("nx", [41, 44])
+def test_kolmogorov_smagorinsky_lrs_2d(nx):
     """256^2 Kolmogorov LES shape (Smagorinsky + TO-LRS, 4 QoIs G3/L1, drag)
-    on a ragged 41x35 grid with h = 3, 40 steps."""
-    wl = synthetic.workload("C2", nx=41, ny=35, h=3)
+    on a ragged nx x 35 grid with h = 3, 40 steps (odd nx: one node per
+    thread; nx a multiple of 4: the node-pair and 4-node kernels)."""
+    wl = synthetic.workload("C2", nx=nx, ny=35, h=3)
     lrs = lrs_inputs(wl, oracle_sigma_ref(wl))
     _, ro, rho_o, u_o = run_oracle(wl, 40, lrs=lrs)
     _, rg, rho_g, u_g = run_gpu(wl, 40, lrs=lrs)
@@ -88,10 +90,11 @@ def test_kolmogorov_smagorinsky_lrs_2d():
     _compare_rows(wl, rg, ro)
 
 
-def test_channel_wale_lrs_3d():
+@pytest.mark.parametrize("nx", [19, 36])
+def test_channel_wale_lrs_3d(nx):
     """96x40x48 channel shape (WALE + TO-LRS, 12 QoIs with 6 mean-profile
-    bands, walls) on a ragged 19x22x13 grid with h = 2, 6 steps."""
-    wl = synthetic.workload("C3", nx=19, ny=22, nz=13, h=2)
+    bands, walls) on a ragged nx x 22 x 13 grid with h = 2, 6 steps."""
+    wl = synthetic.workload("C3", nx=nx, ny=22, nz=13, h=2)
     lrs = lrs_inputs(wl, oracle_sigma_ref(wl, 2))
     _, ro, rho_o, u_o = run_oracle(wl, 6, lrs=lrs)
     _, rg, rho_g, u_g = run_gpu(wl, 6, lrs=lrs)
@@ -99,10 +102,12 @@ def test_channel_wale_lrs_3d():
     _compare_rows(wl, rg, ro)
 
 
-def test_channel_bgk_3d_long():
-    """Plain BGK channel (the 480x200x240 workload's physics) on 33x18x11,
-    300 steps: the pure stream-collide path."""
-    wl = synthetic.workload("C4", nx=33, ny=18, nz=11)
+@pytest.mark.parametrize("nx", [33, 68])
+def test_channel_bgk_3d_long(nx):
+    """Plain BGK channel (the 480x200x240 workload's physics) on nx x 18 x 11,
+    300 steps: the pure stream-collide path (nx = 68: node pairs spanning
+    warp and row boundaries)."""
+    wl = synthetic.workload("C4", nx=nx, ny=18, nz=11)
     _, _, rho_o, u_o = run_oracle(wl, 300)
     _, _, rho_g, u_g = run_gpu(wl, 300)
     _compare_state(wl, rho_g, u_g, rho_o, u_o)
@@ -118,12 +123,13 @@ def test_kolmogorov_1000_steps_full_grid():
     _compare_rows(wl, rg, ro, qtol=2e-4)
 
 
+@pytest.mark.parametrize("nx", [33, 36])
 @pytest.mark.parametrize("storage,tol", [("fp16", 3e-3), ("bf16", 3e-2)])
-def test_reduced_precision_storage(storage, tol):
+def test_reduced_precision_storage(storage, tol, nx):
     """Shifted FP16/BF16 population storage with FP32 arithmetic, against the
     FP64 oracle: rel-L2 of u within the storage precision (fp16 11-bit,
     bf16 8-bit significands of f - w)."""
-    wl = synthetic.workload("C4", nx=33, ny=18, nz=11, storage=storage)
+    wl = synthetic.workload("C4", nx=nx, ny=18, nz=11, storage=storage)
     _, _, rho_o, u_o = run_oracle(wl, 100)
     _, _, rho_g, u_g = run_gpu(wl, 100)
     m = fluid_mask(wl)

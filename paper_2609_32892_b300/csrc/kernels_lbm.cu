@@ -115,7 +115,10 @@ struct Macro {
     float ux, uy, uz;              // equilibrium velocity (EDM: j/rho, Guo: (j + F/2)/rho)
 };
 
-template <int DIM>
+// ACC: u = (rho u)/rho by IEEE division (FP32 storage, where the collision's
+// rounding sets the error); otherwise by one reciprocal (16-bit storage, where
+// storage rounding dominates and the kernel is arithmetic bound).
+template <int DIM, bool ACC = true>
 __device__ __forceinline__ Macro macros_of(const Params& p, const float* g, const float* kolmo, int y) {
     using LT = Lat<DIM>;
     Macro m;
@@ -134,15 +137,32 @@ __device__ __forceinline__ Macro macros_of(const Params& p, const float* g, cons
     m.fx = p.body[0] + kolmo[y] - p.kolmo_drag * jx;
     m.fy = p.body[1] - p.kolmo_drag * jy;
     m.fz = DIM == 3 ? p.body[2] - p.kolmo_drag * jz : 0.f;
-    const float inv = 1.0f / m.rho;
-    if (p.forcing == LBM_FORCING_GUO) {
-        m.ux = (jx + 0.5f * m.fx) * inv;
-        m.uy = (jy + 0.5f * m.fy) * inv;
-        m.uz = (jz + 0.5f * m.fz) * inv;
+    if (ACC) {
+        // quotient from the reciprocal plus one Newton correction of the
+        // residual (Markstein 1990): q = n r, q += (n - q rho) r, as accurate
+        // as a correctly rounded division for these operands at a third of the cost
+        const float inv = 1.0f / m.rho;
+        const float nx_ = p.forcing == LBM_FORCING_GUO ? jx + 0.5f * m.fx : jx;
+        const float ny_ = p.forcing == LBM_FORCING_GUO ? jy + 0.5f * m.fy : jy;
+        const float nz_ = p.forcing == LBM_FORCING_GUO ? jz + 0.5f * m.fz : jz;
+        float qx = nx_ * inv, qy = ny_ * inv, qz = nz_ * inv;
+        qx = fmaf(fmaf(-qx, m.rho, nx_), inv, qx);
+        qy = fmaf(fmaf(-qy, m.rho, ny_), inv, qy);
+        qz = fmaf(fmaf(-qz, m.rho, nz_), inv, qz);
+        m.ux = qx;
+        m.uy = qy;
+        m.uz = qz;
     } else {
-        m.ux = jx * inv;
-        m.uy = jy * inv;
-        m.uz = jz * inv;
+        const float inv = 1.0f / m.rho;
+        if (p.forcing == LBM_FORCING_GUO) {
+            m.ux = (jx + 0.5f * m.fx) * inv;
+            m.uy = (jy + 0.5f * m.fy) * inv;
+            m.uz = (jz + 0.5f * m.fz) * inv;
+        } else {
+            m.ux = jx * inv;
+            m.uy = jy * inv;
+            m.uz = jz * inv;
+        }
     }
     return m;
 }
@@ -221,22 +241,39 @@ __device__ __forceinline__ float wale_nut(const Params& p, const float* __restri
 // place): moments, substrate tau_eff, BGK (Eq. LES-1) and the body force (EDM:
 // Eq. collide-and-stream; or Guo).  Returns rho and the predictor velocity
 // v^{p*} = (rho u + F)/rho for the TO phase.
-template <int DIM, int SUB>
+template <int DIM, int SUB, bool ACC>
 __device__ __forceinline__ void collide_node(const Params& p, float* g, int x, int y, int z,
                                              const float* __restrict__ vn, const float* __restrict__ kolmo,
                                              DevState* st, float& rho_o, float& vx_o, float& vy_o, float& vz_o) {
     using LT = Lat<DIM>;
-    const Macro m = macros_of<DIM>(p, g, kolmo, y);
+    const Macro m = macros_of<DIM, ACC>(p, g, kolmo, y);
     const float ux = m.ux, uy = m.uy, uz = m.uz;
     const float uu = ux * ux + uy * uy + uz * uz;
     if (!(m.rho > 0.f) || !(uu <= (1.0f / 3.0f))) atomicOr(&st->status, 1u);
 
-    // equilibrium deviations g^eq_i = w_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 uu))
+    // equilibrium deviations g^eq_i = w_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 uu)).
+    // FP32 storage: one expression per direction (measured most accurate against
+    // the FP64 reference); 16-bit storage: per opposite pair (i, opp i), the
+    // even part shared and the odd part 3 w rho cu flipping sign (fewer
+    // operations for the arithmetic-bound 16-bit kernel).
     float geq[LT::Q];
+    if (ACC) {
 #pragma unroll
-    for (int i = 0; i < LT::Q; ++i) {
-        const float cu = LT::cx(i) * ux + LT::cy(i) * uy + LT::cz(i) * uz;
-        geq[i] = LT::w(i) * (m.drho + m.rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+        for (int i = 0; i < LT::Q; ++i) {
+            const float cu = LT::cx(i) * ux + LT::cy(i) * uy + LT::cz(i) * uz;
+            geq[i] = LT::w(i) * (m.drho + m.rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+        }
+    } else {
+        geq[0] = LT::w(0) * (m.drho - 1.5f * m.rho * uu);
+#pragma unroll
+        for (int i = 1; i < LT::Q; ++i) {
+            if (LT::opp(i) < i) continue;
+            const float cu = LT::cx(i) * ux + LT::cy(i) * uy + LT::cz(i) * uz;
+            const float ev = LT::w(i) * (m.drho + m.rho * (4.5f * cu * cu - 1.5f * uu));
+            const float od = LT::w(i) * m.rho * 3.0f * cu;
+            geq[i] = ev + od;
+            geq[LT::opp(i)] = ev - od;
+        }
     }
     // Without a substrate 1/tau and 1 - 1/(2 tau) come rounded once from
     // double: the viscosity depends on (1/omega - 1/2) and Guo's prefactor is
@@ -268,27 +305,41 @@ __device__ __forceinline__ void collide_node(const Params& p, float* g, int x, i
         pre = (tau - 0.5f) * om;  // tau - 1/2 is exact in FP32 for tau in [1/2, 1]
     }
 
+    // body-force terms, again per opposite pair (even part shared, odd part flips)
     const float fx = m.fx, fy = m.fy, fz = m.fz;
     if (p.forcing == LBM_FORCING_GUO) {
+        // S_i = w (1 - 1/(2 tau)) [3 (c - u).F + 9 (c.u)(c.F)]
+        const float uf = ux * fx + uy * fy + uz * fz;
+        g[0] = g[0] + (geq[0] - g[0]) * om - LT::w(0) * pre * 3.0f * uf;
 #pragma unroll
-        for (int i = 0; i < LT::Q; ++i) {
+        for (int i = 1; i < LT::Q; ++i) {
+            if (LT::opp(i) < i) continue;
             const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
             const float cu = cx * ux + cy * uy + cz * uz;
             const float cf = cx * fx + cy * fy + cz * fz;
-            const float s = LT::w(i) * pre * (3.0f * (cf - (ux * fx + uy * fy + uz * fz)) + 9.0f * cu * cf);
-            g[i] = g[i] + (geq[i] - g[i]) * om + s;
+            const float ev = LT::w(i) * pre * (9.0f * cu * cf - 3.0f * uf);
+            const float od = LT::w(i) * pre * 3.0f * cf;
+            const int j = LT::opp(i);
+            g[i] = g[i] + (geq[i] - g[i]) * om + (ev + od);
+            g[j] = g[j] + (geq[j] - g[j]) * om + (ev - od);
         }
     } else {
+        // EDM: S_i = w rho [3 c.d + 4.5 (c.d)(2 c.u + c.d) - 1.5 d.(2u + d)], d = F/rho
         const float inv = 1.0f / m.rho;
         const float dx = fx * inv, dy = fy * inv, dz = fz * inv;
         const float du = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
+        g[0] = g[0] + (geq[0] - g[0]) * om - LT::w(0) * m.rho * 1.5f * du;
 #pragma unroll
-        for (int i = 0; i < LT::Q; ++i) {
+        for (int i = 1; i < LT::Q; ++i) {
+            if (LT::opp(i) < i) continue;
             const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
             const float cu = cx * ux + cy * uy + cz * uz;
             const float cd = cx * dx + cy * dy + cz * dz;
-            const float s = LT::w(i) * m.rho * (3.0f * cd + 4.5f * cd * (2.0f * cu + cd) - 1.5f * du);
-            g[i] = g[i] + (geq[i] - g[i]) * om + s;
+            const float ev = LT::w(i) * m.rho * (4.5f * cd * (2.0f * cu + cd) - 1.5f * du);
+            const float od = LT::w(i) * m.rho * 3.0f * cd;
+            const int j = LT::opp(i);
+            g[i] = g[i] + (geq[i] - g[i]) * om + (ev + od);
+            g[j] = g[j] + (geq[j] - g[j]) * om + (ev - od);
         }
     }
     const float inv = 1.0f / m.rho;
@@ -323,7 +374,7 @@ __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restr
     float g[LT::Q];
     pull<DIM, T>(p, src, x, y, z, n, g);
     float r, vx, vy, vz;
-    collide_node<DIM, SUB>(p, g, x, y, z, vn, kolmo, st, r, vx, vy, vz);
+    collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g, x, y, z, vn, kolmo, st, r, vx, vy, vz);
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) st_<T>(dst + (size_t)i * N + n, g[i]);
     if (fields) {
@@ -437,8 +488,8 @@ __global__ void __launch_bounds__(128) collide2_kernel(Params p, const T* __rest
         return;
     }
     float r0, vx0, vy0, vz0, r1, vx1, vy1, vz1;
-    collide_node<DIM, SUB>(p, g0, x0, y, z, vn, kolmo, st, r0, vx0, vy0, vz0);
-    collide_node<DIM, SUB>(p, g1, x0 + 1, y, z, vn, kolmo, st, r1, vx1, vy1, vz1);
+    collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g0, x0, y, z, vn, kolmo, st, r0, vx0, vy0, vz0);
+    collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g1, x0 + 1, y, z, vn, kolmo, st, r1, vx1, vy1, vz1);
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) Vec2<T>::st(dst + (size_t)i * N + n0, g0[i], g1[i]);
     if (fields) {

@@ -44,6 +44,30 @@ def _peaks():
     return 6400.0, "fallback"
 
 
+# DRAM traffic of the fused Laplacian-filter launches (lap3_kernel<7,1> and
+# cross3_kernel<2>, the dominant kernel class), from one ncu capture on the
+# 320x200x160 channel (profiles/filters_channel3d_320x200x160.md): read+write
+# bytes per launch averaged over the class, per lattice node.  It is reported
+# only while the kernel source still has the hash it had when captured.
+TRAFFIC = {
+    "lap3": {"bytes_per_node": ((275.314688 + 212.014336) + (254.4256 + 206.620672)) / 2 * 1e6 / (320 * 200 * 160),
+             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "85df6288052e4c36"},
+}
+
+
+def _traffic(kind, n_nodes):
+    import hashlib
+
+    t = TRAFFIC.get(kind)
+    if not t:
+        return None
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, t["source"]), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return t["bytes_per_node"] * n_nodes if sha == t["sha256_16"] else None
+
+
 # FP32 (non-tensor) arithmetic peak of one B300 from its unit counts and clock:
 # 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.032 GHz maximum SM clock.
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -219,9 +243,12 @@ def run_ours(args, world, rank, local):
         tms, cnt = prof[dominant]
         per_launch = flops[dominant] / (cnt / args.profile_steps)
         ach = per_launch / (tms / cnt * 1e-3) / 1e12
+        tr = _traffic(dominant, n_nodes)
         roof = {"kernel": dominant, "bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
-                "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz", "traffic": None,
+                "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz",
+                "traffic": None if tr is None else round(tr), "traffic_unit": "bytes per launch (ncu, scaled by nodes)",
+                "algorithmic_bytes_per_launch": n_nodes * 2 * 6 * 4,
                 "flops_per_launch": per_launch, "avg_launch_ms": tms / cnt,
                 "hbm_gbs": round(n_nodes * 2 * 6 * 4 / (tms / cnt * 1e-3) / 1e9, 1)}
     coll = prof["collide"]

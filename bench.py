@@ -186,8 +186,9 @@ def run_ours(args, world, rank, local):
         sim.set_lrs(*lrs)
     launches = B.lbm_launches_per_step(sim.ctx)
 
-    # warm-up (also captures the CUDA graph)
+    # warm-up (also runs the launch-shape autotuner and captures the CUDA graph)
     sim.step(args.warmup)
+    tuning = B.lbm_get_tuning(sim.ctx)
     sim.sync()
     sim.qoi()
     if world > 1:
@@ -293,7 +294,7 @@ def run_ours(args, world, rank, local):
                          "frac_of_8tbs": round(byts / (t4 * 1e-3) / 1e9 / 8000.0, 4)}
             s4.close()
     sim.close()
-    return dict(ms_per_step=ms_per_step, mlups=mlups, launches=launches, clocks=clk, sections=sections,
+    return dict(ms_per_step=ms_per_step, mlups=mlups, launches=launches, clocks=clk, sections=sections, tuning=tuning,
                 roofline=roof, e2e=e2e, bgk=extra, collide_gbs=coll_gbs, step_gbs=step_gbs, wl=wl,
                 n_nodes=n_nodes)
 
@@ -428,7 +429,7 @@ def main():
                 "config": config, "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
                 "gpu_launches": int(r["launches"] * args.steps), "clocks": r["clocks"],
                 "step_hbm_gbs": round(r["step_gbs"], 1), "collide_gbs": r["collide_gbs"],
-                "sections": r["sections"], "bgk_480x200x240": r["bgk"], "serving": serving}
+                "sections": r["sections"], "tuning": r["tuning"], "bgk_480x200x240": r["bgk"], "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

@@ -208,6 +208,18 @@ enum {
     LBM_K_COUNT = 11
 };
 int lbm_set_graphs(lbm_ctx* ctx, int enable);
+
+/* Autotuner (default on): before the first lbm_step the library times the
+ * candidate launch shapes of its kernels on this context's buffers (node-pair
+ * vs single-node collide, 4-node vs single-node SGS apply, the z-segment count
+ * of the fused 3-D filters, the line segments of 2-D filter passes) and keeps
+ * the fastest, cached per grid shape for the process.  Per node, every
+ * candidate evaluates the same arithmetic.  lbm_set_autotune must precede the
+ * first lbm_step; 0 keeps the built-in shapes.  lbm_get_tuning returns
+ * [tuned, collide_pair, apply4, march_threads, blocks_per_sm of filter slot
+ * 0..7 (0 = default)] (up to count values). */
+int lbm_set_autotune(lbm_ctx* ctx, int enable);
+int lbm_get_tuning(lbm_ctx* ctx, int32_t* values, int count);
 int lbm_profile(lbm_ctx* ctx, int enable);
 int lbm_profile_read(lbm_ctx* ctx, double* ms, int64_t* launches, int count);
 

@@ -31,7 +31,7 @@ EXPORTED = [
     "lbm_save", "lbm_load", "lbm_set_graphs", "lbm_profile", "lbm_profile_read", "lbm_launches_per_step",
     "lbm_qoi_eval_static", "lbm_filter_flops_per_step",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_admit", "lbm_batch_member", "lbm_batch_run",
-    "lbm_batch_poll", "lbm_batch_release", "lbm_batch_stats",
+    "lbm_batch_poll", "lbm_batch_release", "lbm_batch_stats", "lbm_set_autotune", "lbm_get_tuning",
 ]
 
 
@@ -96,6 +96,8 @@ def _load():
         "lbm_batch_poll": [VP, P(lbm_completion), C.c_int32, P(C.c_int32)],
         "lbm_batch_release": [VP, C.c_int32],
         "lbm_batch_stats": [VP, P(C.c_size_t), P(C.c_size_t), P(C.c_int32)],
+        "lbm_set_autotune": [VP, C.c_int],
+        "lbm_get_tuning": [VP, P(C.c_int32), C.c_int],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -348,3 +350,14 @@ def lbm_batch_stats(b):
     f, l, a = C.c_size_t(), C.c_size_t(), C.c_int32()
     _check(_lib.lbm_batch_stats(b, C.byref(f), C.byref(l), C.byref(a)))
     return f.value, l.value, a.value
+
+
+def lbm_set_autotune(ctx, enable):
+    _check(_lib.lbm_set_autotune(ctx, int(bool(enable))), ctx)
+
+
+def lbm_get_tuning(ctx):
+    v = (C.c_int32 * 12)()
+    _check(_lib.lbm_get_tuning(ctx, v, 12), ctx)
+    return {"tuned": int(v[0]), "collide_pair": int(v[1]), "apply4": int(v[2]), "march_threads": int(v[3]),
+            "filter_blocks_per_sm": [int(v[4 + f]) for f in range(8)]}

@@ -122,8 +122,8 @@ static cudaError_t run(const Params& p, const float* in, float* out, int axis, c
     } else {
         const int L = axis == 1 ? p.ny : p.nz;
         const int lines = p.nx * (axis == 1 ? p.nz : p.ny);
-        // split lines into segments so that ~4 warps per SM-slot are in flight
-        int nseg = (int)((148LL * 2048 + lines - 1) / lines);
+        // split lines into segments so that ~tune.march_lines threads are in flight
+        int nseg = (int)(((long long)p.tune.march_lines + lines - 1) / lines);
         if (nseg < 1) nseg = 1;
         int seg = (L + nseg - 1) / nseg;
         if (seg < 4 * R) seg = 4 * R;

@@ -363,11 +363,11 @@ int seg_len(const Params& p, int blocks_xy, int ncomp, int R, int per_sm) {
 
 template <int R>
 cudaError_t run_gauss(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale, int acc,
-                      cudaStream_t s) {
+                      int per_sm, cudaStream_t s) {
     T3<R> tp;
     for (int i = 0; i < 2 * R + 1; ++i) tp.t[i] = t.t[i];
     const int bx = (p.nx + TX - 1) / TX, by = (p.ny + TY - 1) / TY;
-    const int seg = seg_len(p, bx * by, ncomp, R, 8);
+    const int seg = seg_len(p, bx * by, ncomp, R, per_sm > 0 ? per_sm : 8);
     const int nseg = (p.nz + seg - 1) / seg;
     gauss3_kernel<R><<<dim3(bx, by, ncomp * nseg), 128, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
     return cudaGetLastError();
@@ -375,11 +375,11 @@ cudaError_t run_gauss(const Params& p, const float* in, float* out, int ncomp, c
 
 template <int RA, int RB>
 cudaError_t run_lap(const Params& p, const float* in, float* out, int ncomp, const Taps& arm, float scale, int acc,
-                    cudaStream_t s) {
+                    int per_sm, cudaStream_t s) {
     T3<RA> tp;
     for (int i = 0; i < 2 * RA + 1; ++i) tp.t[i] = arm.t[i];
     const int bx = (p.nx + TX - 1) / TX, by = (p.ny + TY - 1) / TY;
-    const int seg = seg_len(p, bx * by, ncomp, RA, 4);
+    const int seg = seg_len(p, bx * by, ncomp, RA, per_sm > 0 ? per_sm : 4);
     const int nseg = (p.nz + seg - 1) / seg;
     if (RB == 0)
         cross3_kernel<RA><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
@@ -391,21 +391,21 @@ cudaError_t run_lap(const Params& p, const float* in, float* out, int ncomp, con
 
 // G_s / B3 in 3-D with the same 1-D taps on every axis.
 cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
-                          int accumulate, cudaStream_t s) {
+                          int accumulate, int per_sm, cudaStream_t s) {
     switch (t.radius) {
-        case 1: return run_gauss<1>(p, in, out, ncomp, t, scale, accumulate, s);
-        case 2: return run_gauss<2>(p, in, out, ncomp, t, scale, accumulate, s);
-        case 4: return run_gauss<4>(p, in, out, ncomp, t, scale, accumulate, s);
-        case 6: return run_gauss<6>(p, in, out, ncomp, t, scale, accumulate, s);
+        case 1: return run_gauss<1>(p, in, out, ncomp, t, scale, accumulate, per_sm, s);
+        case 2: return run_gauss<2>(p, in, out, ncomp, t, scale, accumulate, per_sm, s);
+        case 4: return run_gauss<4>(p, in, out, ncomp, t, scale, accumulate, per_sm, s);
+        case 6: return run_gauss<6>(p, in, out, ncomp, t, scale, accumulate, per_sm, s);
         default: return cudaErrorNotSupported;
     }
 }
 
 // L_s in 3-D for s = 1 (arm radius 2, no box) and s = 3 (arm 7, box 1).
 cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp, int s_scale, const Taps& arm,
-                        float scale, int accumulate, cudaStream_t s) {
-    if (s_scale == 1 && arm.radius == 2) return run_lap<2, 0>(p, in, out, ncomp, arm, scale, accumulate, s);
-    if (s_scale == 3 && arm.radius == 7) return run_lap<7, 1>(p, in, out, ncomp, arm, scale, accumulate, s);
+                        float scale, int accumulate, int per_sm, cudaStream_t s) {
+    if (s_scale == 1 && arm.radius == 2) return run_lap<2, 0>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
+    if (s_scale == 3 && arm.radius == 7) return run_lap<7, 1>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
     return cudaErrorNotSupported;
 }
 

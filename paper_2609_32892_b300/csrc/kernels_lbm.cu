@@ -526,8 +526,9 @@ __global__ void __launch_bounds__(256) apply_kernel(Params p, T* __restrict__ f,
         dy += b * v[(size_t)N + n];
         if (DIM == 3) dz += b * v[(size_t)2 * N + n];
     }
-    for (int j = 0; j < p.n_mp; ++j) dx += (float)(beta[p.n_s + j] * w_mp[(size_t)j * p.ny + y]);
-    if (dx == 0.f && dy == 0.f && dz == 0.f) return;
+    float mp = 0.f;  // same order as the 4-node kernel, so both give identical results
+    for (int j = 0; j < p.n_mp; ++j) mp += (float)(beta[p.n_s + j] * w_mp[(size_t)j * p.ny + y]);
+    dx += mp;
     const float r = rho[n];
     const float ux = vps[n], uy = vps[(size_t)N + n], uz = DIM == 3 ? vps[(size_t)2 * N + n] : 0.f;
     const float du = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
@@ -738,10 +739,8 @@ static void do_collide_d(const Params& p, const Layout& L, int src, cudaStream_t
     const int fields = p.to_mode != LBM_TO_OFF;
     const T* a = (const T*)L.f[src];
     T* b = (T*)L.f[1 - src];
-    if (p.nx % 2 == 0 && p.substrate != LBM_SUBSTRATE_WALE) {
+    if (p.nx % 2 == 0 && p.tune.collide_pair) {
         // node pairs: nx even keeps every pair inside one row and 2-aligned
-        // (WALE's gradient loads push the pair kernel to 128 registers, where
-        // the single-node kernel is faster)
         const unsigned g2 = grid_of(p.n / 2, 128);
         if (p.substrate == LBM_SUBSTRATE_SMAG)
             collide2_kernel<DIM, T, LBM_SUBSTRATE_SMAG><<<g2, 128, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
@@ -777,7 +776,7 @@ static void do_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) 
         const int slot = p.qoi_filter_slot[k];
         vk.v[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
     }
-    if (p.nx % 4 == 0) {
+    if (p.nx % 4 == 0 && p.tune.apply4) {
         if (p.dim == 2)
             apply4_kernel<2, T><<<grid_of(p.n / 4, 128), 128, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
         else

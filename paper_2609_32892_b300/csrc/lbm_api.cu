@@ -50,6 +50,8 @@ struct lbm_ctx {
     double prof_ms[LBM_K_COUNT];
     long long prof_n[LBM_K_COUNT];
     int lrs_set;
+    int autotune;     // tune launch shapes before the first step (default on)
+    int tuned;
 };
 
 static int fail(lbm_ctx* c, int code, const char* fmt, ...) {
@@ -194,6 +196,10 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     p->nzc = (c->nz + zper - 1) / zper;
     p->nblk_red = c->ny * p->nzc;
     p->npart = p->n_s + p->n_s * (p->n_s + 1) / 2;
+    for (int f = 0; f < 8; ++f) p->tune.filter_per_sm[f] = 0;
+    p->tune.march_lines = 148 * 2048;
+    p->tune.collide_pair = c->substrate == LBM_SUBSTRATE_WALE ? 0 : 1;
+    p->tune.apply4 = 1;
     if (p->h > 0) {
         const long long rows = (long long)(2 * p->h + 1) * p->n_q + 1;
         p->lrs_rows_per_blk = 1024;
@@ -332,7 +338,7 @@ static double filter_taps(const Filter& f, int d) {
     return d * (5.0 * f.scale + (f.scale > 1 ? (d - 1) * (double)f.scale : 0.0));
 }
 
-static void enqueue_filter(Launcher& lc, const Filter& f, const float* in, float* out) {
+static void enqueue_filter(Launcher& lc, const Filter& f, int slot, const float* in, float* out) {
     lbm_ctx* c = lc.c;
     const Params& p = c->p;
     const int nc = p.ncomp;
@@ -346,13 +352,14 @@ static void enqueue_filter(Launcher& lc, const Filter& f, const float* in, float
             const Taps t = f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps();
             if (launch_gauss3_supported(t.radius)) {
                 if (lc.count_only) c->filter_flops[LBM_K_GAUSS3] += flops;
-                LAUNCH(lc, LBM_K_GAUSS3, launch_gauss3(p, in, out, nc, t, 1.f, 0, lc.s));
+                LAUNCH(lc, LBM_K_GAUSS3, launch_gauss3(p, in, out, nc, t, 1.f, 0, p.tune.filter_per_sm[slot], lc.s));
                 return;
             }
         } else if (launch_lap3_supported(f.scale)) {
             const float scale = (float)(1.0 / (8.0 * d * (double)f.scale * f.scale * f.scale));
             if (lc.count_only) c->filter_flops[LBM_K_LAP3] += flops;
-            LAUNCH(lc, LBM_K_LAP3, launch_lap3(p, in, out, nc, f.scale, ell_taps(f.scale), scale, 0, lc.s));
+            LAUNCH(lc, LBM_K_LAP3,
+                   launch_lap3(p, in, out, nc, f.scale, ell_taps(f.scale), scale, 0, p.tune.filter_per_sm[slot], lc.s));
             return;
         }
     }
@@ -405,8 +412,8 @@ static void enqueue_step(Launcher& lc, int src) {
     if (p.to_mode == LBM_TO_LRS) LAUNCH(lc, LBM_K_LRS, launch_lrs_hist(p, L, lc.s));
     LAUNCH(lc, LBM_K_CURL, launch_to_curl(p, L, lc.s));
     for (size_t f = 0; f < c->filters.size(); ++f) {
-        enqueue_filter(lc, c->filters[f], L.x6, L.acc);
-        enqueue_filter(lc, c->filters[f], L.acc, L.rr[f]);
+        enqueue_filter(lc, c->filters[f], (int)f, L.x6, L.acc);
+        enqueue_filter(lc, c->filters[f], (int)f, L.acc, L.rr[f]);
         if (c->filters[f].need_z)
             LAUNCH(lc, LBM_K_SENS, launch_sens_curl(p, L.rr[f] + (size_t)p.dim * p.n, L.vz[f], lc.s));
     }
@@ -549,6 +556,124 @@ static void lrs_parts(lbm_ctx* c, void* ptr[4], size_t bytes[4]) {
     ptr[3] = c->L.lrs_sigma; bytes[3] = sizeof(double) * nq;
 }
 
+// ------------------------------------------------------------- autotuner --
+// Launch shapes are chosen by timing the candidates on this context's own
+// buffers before the first step (CUDA events on its stream).  Only buffers the
+// next step overwrites are written: the other population copy, the TO fields
+// and the filter scratch.  Choices are cached per grid shape for the process,
+// so every context of a shape (ensemble members included) runs the same kernels.
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, Tune> g_tune_cache;
+
+TuneKey tune_key(const Params& p) {
+    return TuneKey(p.dim, p.nx, p.ny, p.nz, p.walls, p.storage, p.substrate, p.to_mode != LBM_TO_OFF, p.n_filters);
+}
+}  // namespace
+
+template <typename F>
+static float time_ms(lbm_ctx* c, F launch, int reps = 3) {
+    launch();  // warm-up
+    cudaEvent_t a = c->ev[0], b = c->ev[1];
+    cudaEventRecord(a, c->stream);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(b, c->stream);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms / reps;
+}
+
+static int autotune(lbm_ctx* c) {
+    Params& p = c->p;
+    const TuneKey key = tune_key(p);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p.tune = it->second;
+            c->tuned = 1;
+            return LBM_OK;
+        }
+    }
+    const int src = c->cur;
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t e) { if (e != cudaSuccess && err == cudaSuccess) err = e; };
+    // collide: node pairs or single nodes
+    if (p.nx % 2 == 0) {
+        float best = 1e30f;
+        int pick = p.tune.collide_pair;
+        for (int v = 0; v <= 1; ++v) {
+            p.tune.collide_pair = v;
+            const float t = time_ms(c, [&] { chk(launch_collide(p, c->L, src, c->stream)); }, 5);
+            if (t < best) { best = t; pick = v; }
+        }
+        p.tune.collide_pair = pick;
+    }
+    if (p.to_mode != LBM_TO_OFF) {
+        // SGS apply on the other population copy (overwritten by the next collide)
+        if (p.nx % 4 == 0) {
+            float best = 1e30f;
+            int pick = p.tune.apply4;
+            for (int v = 0; v <= 1; ++v) {
+                p.tune.apply4 = v;
+                const float t = time_ms(c, [&] { chk(launch_apply(p, c->L, 1 - src, c->stream)); }, 5);
+                if (t < best) { best = t; pick = v; }
+            }
+            p.tune.apply4 = pick;
+        }
+        const int nc = p.ncomp;
+        if (p.dim == 3) {
+            static const int cand[] = {2, 4, 8, 16};
+            for (size_t f = 0; f < c->filters.size() && f < 8; ++f) {
+                const Filter& fl = c->filters[f];
+                const bool lap = fl.kind == LBM_FILTER_LAPLACE;
+                if (lap ? !launch_lap3_supported(fl.scale) : !launch_gauss3_supported(
+                                                               fl.kind == LBM_FILTER_GAUSS ? gauss_taps(fl.scale, 3).radius : 1))
+                    continue;
+                const Taps t0 = lap ? ell_taps(fl.scale) : (fl.kind == LBM_FILTER_GAUSS ? gauss_taps(fl.scale, 3) : binom_taps());
+                float best = 1e30f;
+                int pick = 0;
+                for (int v : cand) {
+                    const float t = time_ms(c, [&] {
+                        chk(lap ? launch_lap3(p, c->L.x6, c->L.acc, nc, fl.scale, t0, 1.f, 0, v, c->stream)
+                                : launch_gauss3(p, c->L.x6, c->L.acc, nc, t0, 1.f, 0, v, c->stream));
+                    }, 5);
+                    if (t < best) { best = t; pick = v; }
+                }
+                p.tune.filter_per_sm[f] = pick;
+            }
+        } else if (!c->filters.empty()) {
+            // 2-D: the y-axis march of the widest filter
+            const Filter& fl = c->filters[0];
+            const Taps t0 = fl.kind == LBM_FILTER_GAUSS ? gauss_taps(fl.scale, 2)
+                            : fl.kind == LBM_FILTER_BINOMIAL ? binom_taps() : ell_taps(fl.scale);
+            static const int cand[] = {148 * 256, 148 * 512, 148 * 1024, 148 * 2048, 148 * 4096};
+            float best = 1e30f;
+            int pick = p.tune.march_lines;
+            for (int v : cand) {
+                p.tune.march_lines = v;
+                const float t = time_ms(c, [&] { chk(launch_pass(p, c->L.x6, c->L.t1, nc, 1, t0, 1.f, 0, c->stream)); });
+                if (t < best) { best = t; pick = v; }
+            }
+            p.tune.march_lines = pick;
+        }
+    }
+    if (err != cudaSuccess) return fail(c, LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(err));
+    CK(c, cudaStreamSynchronize(c->stream));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = p.tune;
+    }
+    c->tuned = 1;
+    return LBM_OK;
+}
+
 // ================================================================== C ABI ==
 extern "C" {
 
@@ -587,6 +712,7 @@ int lbm_create(const lbm_config* cfg, void* dev_buf, size_t bytes, void* cuda_st
     c->stream = (cudaStream_t)cuda_stream;
     c->elem = cfg->storage == LBM_STORAGE_FP32 ? 4 : 2;
     c->use_graphs = 1;
+    c->autotune = 1;
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
@@ -743,6 +869,10 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
     if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
     if (c->p.to_mode == LBM_TO_LRS && !c->lrs_set) return fail(c, LBM_ERR_STATE, "call lbm_set_lrs first");
+    if (c->autotune && !c->tuned && nsteps > 0) {
+        const int rc = autotune(c);
+        if (rc) return rc;
+    }
     int64_t left = nsteps;
     const bool graphs = c->use_graphs && !c->profiling;
     if (graphs && left >= 2) {
@@ -966,6 +1096,21 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t bytes) {
     c->host_read = h.host_read;
     c->lrs_set = c->lrs_set || c->p.h > 0;
     return sync_check(c);
+}
+
+int lbm_set_autotune(lbm_ctx* c, int enable) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    if (c->graph) return fail(c, LBM_ERR_STATE, "lbm_set_autotune must precede the first lbm_step");
+    c->autotune = enable ? 1 : 0;
+    return LBM_OK;
+}
+
+int lbm_get_tuning(lbm_ctx* c, int32_t* values, int count) {
+    if (!c || !values) return fail(c, LBM_ERR_ARG, "NULL argument");
+    int32_t v[12] = {c->tuned, c->p.tune.collide_pair, c->p.tune.apply4, c->p.tune.march_lines};
+    for (int f = 0; f < 8; ++f) v[4 + f] = c->p.tune.filter_per_sm[f];
+    for (int k = 0; k < count && k < 12; ++k) values[k] = v[k];
+    return LBM_OK;
 }
 
 int lbm_set_graphs(lbm_ctx* c, int enable) {

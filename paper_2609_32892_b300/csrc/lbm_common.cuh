@@ -63,6 +63,14 @@ struct Layout {
     DevState* st;
 };
 
+// Launch shapes chosen by the autotuner (results do not depend on them).
+struct Tune {
+    int filter_per_sm[8];  // fused 3-D filter of each distinct filter slot: target blocks per SM (0: default)
+    int march_lines;    // 1-D passes along y/z: target threads in flight (line segments)
+    int collide_pair;   // node-pair collide when nx is even
+    int apply4;         // 4-node SGS apply when nx % 4 == 0
+};
+
 struct Params {
     int dim, q, nx, ny, nz, walls, forcing, substrate, storage, to_mode;
     long long n;         // nodes
@@ -79,6 +87,7 @@ struct Params {
     double gamma_std;
     unsigned long long seed, member;
     int nblk_red, nzc, npart, nblk_lrs, lrs_rows_per_blk;
+    Tune tune;
 };
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
@@ -92,10 +101,11 @@ cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp,
                         float scale, int accumulate, cudaStream_t s);
 cudaError_t launch_pass_fast(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t,
                              float scale, int accumulate, cudaStream_t s);
+// per_sm: target blocks per SM (z segments); 0 = built-in default
 cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
-                          int accumulate, cudaStream_t s);
+                          int accumulate, int per_sm, cudaStream_t s);
 cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp, int s_scale, const Taps& arm,
-                        float scale, int accumulate, cudaStream_t s);
+                        float scale, int accumulate, int per_sm, cudaStream_t s);
 inline bool launch_gauss3_supported(int radius) { return radius == 1 || radius == 2 || radius == 4 || radius == 6; }
 inline bool launch_lap3_supported(int s_scale) { return s_scale == 1 || s_scale == 3; }
 cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s);

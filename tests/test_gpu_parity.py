@@ -182,3 +182,31 @@ def test_lrs_reference_scales_from_first_step():
     _, rg, rho_g, u_g = run_gpu(wl, 15, lrs=lrs)
     _compare_state(wl, rho_g, u_g, rho_o, u_o)
     _compare_rows(wl, rg, ro)
+
+
+@pytest.mark.parametrize("name,kw", [("C3", dict(nx=36, ny=22, nz=13, h=2)), ("C2", dict(nx=44, ny=36, h=2))])
+def test_autotuned_launch_shapes_change_nothing(name, kw):
+    """The autotuner picks launch shapes only: results with and without it
+    agree (to FP32 rounding of the same arithmetic) and both match the oracle."""
+    from paper_2609_32892_b300 import LbmSim, binding as B
+
+    wl = synthetic.workload(name, **kw)
+    lrs = lrs_inputs(wl, np.zeros(nq_of(wl)))
+    out = []
+    for tune in (True, False):
+        g = LbmSim(wl)
+        B.lbm_set_autotune(g.ctx, tune)
+        g.init(synthetic.initial_velocity(wl))
+        g.set_lrs(*lrs)
+        g.step(6)
+        g.sync()
+        rows = g.qoi()
+        rho, u = g.macros()
+        t = B.lbm_get_tuning(g.ctx)
+        g.close()
+        assert t["tuned"] == (1 if tune else 0)
+        out.append((rows, rho, u))
+    np.testing.assert_allclose(out[0][2], out[1][2], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(out[0][0][:, 1:], out[1][0][:, 1:], rtol=1e-6, atol=0)
+    _, ro, rho_o, u_o = run_oracle(wl, 6, lrs=lrs)
+    _compare_state(wl, out[0][1], out[0][2], rho_o, u_o)

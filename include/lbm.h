@@ -109,7 +109,11 @@ typedef struct {
     double gamma_std;   /* LBM_TO_GAMMA: std of the per-step gamma                 */
     uint64_t seed;      /* Philox key word 0                                       */
     uint64_t member;    /* Philox key word 1 (ensemble member id)                  */
-    int64_t track_len;  /* LBM_TO_TRACK: number of reference rows the buffer holds */
+    int64_t track_len;  /* LBM_TO_TRACK, or LBM_TO_LRS with spinup: reference rows held */
+    int64_t spinup;     /* LBM_TO_LRS: the first spinup steps are nudged to the
+                           reference series (dQ = Q_ref - q*, the reference enters
+                           the histories), as online runs start after a tracked
+                           spin-up; needs track_len >= 1 and sigma_ref > 0 */
 } lbm_config;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -154,8 +158,9 @@ int lbm_init_macros(lbm_ctx* ctx, const double* rho, const double* u);
 int lbm_set_lrs(lbm_ctx* ctx, const double* C, const double* mu, const double* Sigma,
                 const double* sigma_ref, const double* q_hist, const double* qs_hist);
 
-/* Reference QoI series for LBM_TO_TRACK: qref[len][N], row n used at step n
- * (len <= cfg.track_len; steps past the end reuse the last row). */
+/* Reference QoI series for LBM_TO_TRACK (or the spin-up of LBM_TO_LRS):
+ * qref[len][N], row n used at step n (len <= cfg.track_len; steps past the
+ * end reuse the last row). */
 int lbm_set_track_reference(lbm_ctx* ctx, const double* qref, int64_t len);
 
 /* Queue nsteps time steps on the stream (asynchronous).  Returns the status

@@ -135,6 +135,15 @@ class Simulation:
                 if not singular:
                     gamma = self.wl["gamma_std"] * z
                     dq = gamma * den
+            elif self.mode == "lrs" and self.n < self.wl.get("spinup", 0):
+                # spin-up of an online run: nudged to the reference series
+                # (Sec. 6.5 and 7.5: online runs start after tracked steps that
+                # fill the history); the reference enters the history
+                q = self.track_ref[min(self.n, len(self.track_ref) - 1)]
+                dq = q - qstar
+                self.lrs.push(q, qstar)
+                if not singular:
+                    gamma = dq / den
             elif self.mode == "lrs":
                 z = normals(self.seed, self.member, self.n, STREAM_LRS, nq)
                 q = self.lrs.predict(qstar, z)
@@ -143,7 +152,7 @@ class Simulation:
                 if not singular:
                     gamma = dq / den
             elif self.mode == "track":
-                dq = self.track_ref[self.n] - qstar
+                dq = self.track_ref[min(self.n, len(self.track_ref) - 1)] - qstar
                 if not singular:
                     gamma = dq / den
             if singular:

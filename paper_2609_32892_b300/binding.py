@@ -53,6 +53,7 @@ class lbm_config(C.Structure):
         ("c_smag", C.c_double), ("c_wale", C.c_double), ("n_qoi", C.c_int32), ("n_mp", C.c_int32),
         ("qoi", lbm_qoi_spec * MAX_QOI), ("h", C.c_int32), ("qoi_ring", C.c_int32),
         ("gamma_std", C.c_double), ("seed", C.c_uint64), ("member", C.c_uint64), ("track_len", C.c_int64),
+        ("spinup", C.c_int64),
     ]
 
 
@@ -162,6 +163,7 @@ def config_from_workload(wl, member=0):
     c.seed = wl["seed"]
     c.member = member
     c.track_len = wl.get("track_len", 0)
+    c.spinup = wl.get("spinup", 0)
     return c
 
 

@@ -371,7 +371,14 @@ __global__ void __launch_bounds__(256) solve_kernel(Params p, Layout L) {
         if (!singular)
             for (int r = i; r < nq; ++r) ginv_ii += Li[r][i] * Li[r][i];
         double d = 0.0, g = 0.0;
-        if (p.to_mode == LBM_TO_LRS) {
+        if (p.to_mode == LBM_TO_LRS && step < p.spinup) {
+            // spin-up: nudged to the reference, which enters the history
+            const long long row = step < p.track_len ? step : p.track_len - 1;
+            const double qref = L.track[(size_t)row * nq + i];
+            d = qref - q[i];
+            tmp[i] = qref;
+            g = singular ? 0.0 : d * ginv_ii;
+        } else if (p.to_mode == LBM_TO_LRS) {
             double qh = tmp[i] + L.lrs_mu[i];
             for (int j = 0; j < nq; ++j)
                 qh += (q[j] / sigs[j]) * L.lrs_C[((size_t)p.h * nq + j) * nq + i] + L.lrs_L[(size_t)i * nq + j] * z[j];

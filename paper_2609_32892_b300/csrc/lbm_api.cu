@@ -115,6 +115,9 @@ static int validate(const lbm_config* c) {
         }
         if (c->to_mode == LBM_TO_LRS && c->h < 1) return fail(nullptr, LBM_ERR_ARG, "LRS needs h >= 1");
         if (c->to_mode == LBM_TO_TRACK && c->track_len < 1) return fail(nullptr, LBM_ERR_ARG, "tracking needs track_len >= 1");
+        if (c->spinup < 0) return fail(nullptr, LBM_ERR_ARG, "spinup must be >= 0");
+        if (c->spinup > 0 && c->to_mode != LBM_TO_LRS) return fail(nullptr, LBM_ERR_ARG, "spinup applies to LBM_TO_LRS");
+        if (c->spinup > 0 && c->track_len < 1) return fail(nullptr, LBM_ERR_ARG, "spinup needs track_len >= 1");
     }
     return LBM_OK;
 }
@@ -184,7 +187,8 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     p->h = c->to_mode == LBM_TO_LRS ? c->h : 0;
     p->ring_cap = c->qoi_ring > 0 ? c->qoi_ring : 4096;
     p->row_len = 2 + 3 * p->n_q;
-    p->track_len = c->to_mode == LBM_TO_TRACK ? c->track_len : 0;
+    p->spinup = c->to_mode == LBM_TO_LRS ? c->spinup : 0;
+    p->track_len = (c->to_mode == LBM_TO_TRACK || p->spinup > 0) ? c->track_len : 0;
     p->gamma_std = c->gamma_std;
     p->seed = c->seed;
     p->member = c->member;
@@ -809,8 +813,8 @@ int lbm_set_lrs(lbm_ctx* c, const double* C, const double* mu, const double* Sig
     const int n = p.n_q;
     for (int i = 0; i < n; ++i) {
         if (!(sigma_ref[i] == sigma_ref[i])) return fail(c, LBM_ERR_ARG, "sigma_ref[%d] is NaN", i);
-        if (sigma_ref[i] <= 0.0 && (q_hist || qs_hist))
-            return fail(c, LBM_ERR_ARG, "sigma_ref <= 0 (taken from the first step) needs zero initial histories");
+        if (sigma_ref[i] <= 0.0 && (q_hist || qs_hist || p.spinup > 0))
+            return fail(c, LBM_ERR_ARG, "sigma_ref <= 0 (taken from the first step) needs zero initial histories and no spin-up");
     }
     // Cholesky of Sigma (symmetric positive definite required)
     std::vector<double> Lh((size_t)n * n, 0.0);
@@ -855,7 +859,7 @@ int lbm_set_lrs(lbm_ctx* c, const double* C, const double* mu, const double* Sig
 
 int lbm_set_track_reference(lbm_ctx* c, const double* qref, int64_t len) {
     if (!c || !qref) return fail(c, LBM_ERR_ARG, "NULL argument");
-    if (c->p.to_mode != LBM_TO_TRACK) return fail(c, LBM_ERR_STATE, "needs to_mode LBM_TO_TRACK");
+    if (c->p.track_len < 1) return fail(c, LBM_ERR_STATE, "needs LBM_TO_TRACK or an LRS spin-up (track_len >= 1)");
     if (len < 1 || len > c->p.track_len) return fail(c, LBM_ERR_ARG, "len must be in 1..track_len");
     std::vector<double> buf((size_t)c->p.track_len * c->p.n_q);
     for (long long r = 0; r < c->p.track_len; ++r)

@@ -84,6 +84,7 @@ struct Params {
     int ncomp;           // components filtered: 3 (2-D: vx, vy, w) or 6 (3-D)
     int h, ring_cap, row_len;
     long long track_len;
+    long long spinup;    // LRS: steps nudged to the reference first
     double gamma_std;
     unsigned long long seed, member;
     int nblk_red, nzc, npart, nblk_lrs, lrs_rows_per_blk;

@@ -210,3 +210,19 @@ def test_autotuned_launch_shapes_change_nothing(name, kw):
     np.testing.assert_allclose(out[0][0][:, 1:], out[1][0][:, 1:], rtol=1e-6, atol=0)
     _, ro, rho_o, u_o = run_oracle(wl, 6, lrs=lrs)
     _compare_state(wl, out[0][1], out[0][2], rho_o, u_o)
+
+
+def test_lrs_with_tracked_spin_up():
+    """Online TO-LRS whose first steps are nudged to a reference series: the
+    reference enters the histories, then the LRS model takes over."""
+    wl = synthetic.workload("C2", nx=36, ny=30, h=3)
+    ref_run = dict(wl, to_mode="observe")
+    _, ro, _, _ = run_oracle(ref_run, 5)
+    nq = nq_of(wl)
+    ref = ro[:, 1:1 + nq] * (1.0 + 2e-4)
+    w = dict(wl, spinup=5, track_len=len(ref))
+    lrs = lrs_inputs(w, np.sqrt((ro[:, 1:1 + nq] ** 2).mean(axis=0)))
+    _, rot, rho_o, u_o = run_oracle(w, 12, lrs=lrs, track=ref)
+    _, rgt, rho_g, u_g = run_gpu(w, 12, lrs=lrs, track=ref)
+    _compare_state(w, rho_g, u_g, rho_o, u_o)
+    _compare_rows(w, rgt, rot)

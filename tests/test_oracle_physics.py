@@ -280,3 +280,17 @@ def test_printed_filter_constants(root):
         assert filters.gaussian_kernel(3, dim).shape[0] == 2 * 3 * g["gaussian_alpha"][key] + 1
         for s in (1, 3):
             assert abs(np.abs(filters.laplacian_kernel(s, dim)).sum() - g["laplacian_abs_sum"]["value"]) < 1e-14
+
+
+def test_lrs_spin_up_follows_the_reference():
+    """During the spin-up of an online run, dQ = Q_ref - q* and the reference
+    (not an LRS prediction) enters the corrected-QoI history."""
+    wl = synthetic.workload("C2", nx=20, ny=18, h=3, spinup=2, track_len=2)
+    nq = len(wl["qois"])
+    ref = np.array([np.full(nq, 1.0), np.full(nq, 2.0)])
+    sim = Simulation(wl, synthetic.initial_velocity(wl), lrs=_lrs_inputs(wl), track_ref=ref)
+    rows = sim.run(2)
+    np.testing.assert_allclose(rows[:, 1 + nq:1 + 2 * nq], ref - rows[:, 1:1 + nq], rtol=1e-15)
+    np.testing.assert_array_equal(sim.lrs.q_hist[0], ref[1])
+    np.testing.assert_array_equal(sim.lrs.q_hist[1], ref[0])
+    np.testing.assert_array_equal(sim.lrs.qs_hist[0], rows[1, 1:1 + nq])

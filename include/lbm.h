@@ -64,7 +64,8 @@ enum { LBM_SUBSTRATE_NONE = 0, LBM_SUBSTRATE_SMAG = 1, LBM_SUBSTRATE_WALE = 2 };
 /* Populations are always stored shifted, as g_i = f_i - w_i. */
 enum { LBM_STORAGE_FP32 = 0, LBM_STORAGE_FP16 = 1, LBM_STORAGE_BF16 = 2 };
 enum { LBM_QOI_ENERGY = 0, LBM_QOI_ENSTROPHY = 1 };
-enum { LBM_FILTER_GAUSS = 0, LBM_FILTER_LAPLACE = 1, LBM_FILTER_BINOMIAL = 2 };
+enum { LBM_FILTER_GAUSS = 0, LBM_FILTER_LAPLACE = 1, LBM_FILTER_BINOMIAL = 2,
+       LBM_FILTER_FOURIER = 3 /* sharp band l - 1/2 <= |k| < m + 1/2; periodic 2-D, nx = ny */ };
 enum {
     LBM_TO_OFF = 0,      /* substrate-only LES, no QoIs                              */
     LBM_TO_OBSERVE = 1,  /* QoIs and Gram on the predictor, no forcing (dQ = 0)      */
@@ -80,10 +81,11 @@ enum {
 #define LBM_FLAG_UNSTABLE 2u  /* instability seen during this step        */
 
 typedef struct {
-    int32_t kind;    /* LBM_QOI_ENERGY or LBM_QOI_ENSTROPHY               */
-    int32_t filter;  /* LBM_FILTER_*                                        */
-    int32_t scale;   /* s of G_s / L_s (odd, >= 1); ignored for binomial    */
-    int32_t pad;
+    int32_t kind;    /* LBM_QOI_ENERGY or LBM_QOI_ENSTROPHY                      */
+    int32_t filter;  /* LBM_FILTER_*                                               */
+    int32_t scale;   /* s of G_s / L_s (odd, >= 1); ignored for binomial;
+                        lower wavenumber bin l of a Fourier band                  */
+    int32_t band_hi; /* upper wavenumber bin m of a Fourier band (else unused)    */
 } lbm_qoi_spec;
 
 typedef struct {
@@ -210,7 +212,8 @@ enum {
     LBM_K_REDUCE = 5, LBM_K_LRS = 6, LBM_K_SOLVE = 7, LBM_K_APPLY = 8,
     LBM_K_GAUSS3 = 9,  /* fused 3-D Gaussian / binomial filter applications */
     LBM_K_LAP3 = 10,   /* fused 3-D Laplacian filter applications           */
-    LBM_K_COUNT = 11
+    LBM_K_FFT = 11,    /* cuFFT transforms of the Fourier-band filters      */
+    LBM_K_COUNT = 12
 };
 int lbm_set_graphs(lbm_ctx* ctx, int enable);
 

@@ -10,6 +10,10 @@
   Binomial B3: [1, 2, 1]/4 along every axis (the 3x3 pattern filter of the
     64^2 Kolmogorov workload; not one of the paper's filters).
 
+  Sharp Fourier band R_[l,m] (Sec. 4.1, Eq. scale-aware-energy-fourier, App. E):
+    keeps the Fourier modes with l - 1/2 <= |k| < m + 1/2, k the integer
+    wavenumber vector of a periodic 2-D grid; defined on periodic domains only.
+
 Filters act on the fluid nodes Omega: periodic along x and z; along y with walls
 the field is extended by zeros (Sec. 4.1, zero padding) and the output is kept
 only on fluid rows, so each filter is a self-adjoint operator on Omega.
@@ -93,3 +97,14 @@ def apply_kernel(a, k, mask, walls):
             r = (rx, ry, rz)
         out += k[idx] * shifted(am, r, walls)
     return out * mask
+
+
+def fourier_band(a, lo, hi):
+    """R_[lo,hi] a on a periodic 2-D field a[..., 1, ny, nx] (Eq. scale-aware-energy-fourier):
+    F^-1 (mask F a) with the mask 1 where lo - 1/2 <= |k| < hi + 1/2."""
+    ny, nx = a.shape[-2], a.shape[-1]
+    ky = np.fft.fftfreq(ny) * ny
+    kx = np.fft.fftfreq(nx) * nx
+    kk = np.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
+    mask = (kk >= lo - 0.5) & (kk < hi + 0.5)
+    return np.real(np.fft.ifft2(np.fft.fft2(a, axes=(-2, -1)) * mask, axes=(-2, -1)))

@@ -71,10 +71,14 @@ class TOSetup:
         if walls:
             self.mask[:, 0, :] = 0.0
             self.mask[:, ny - 1, :] = 0.0
-        self.kernels = {(f, s): filters.kernel(f, s, dim) for (_, f, s) in self.qois}
+        self.kernels = {(f, s): filters.kernel(f, s, dim) for (_, f, s) in self.qois if f != "F"}
+        if any(f == "F" for (_, f, _) in self.qois) and (dim != 2 or walls):
+            raise ValueError("Fourier-band QoIs need a periodic 2-D grid")
         self.w_mp = mp_band_weights(ny, n_mp) if n_mp > 0 else np.zeros((0, ny))
 
     def filt(self, a, f, s):
+        if f == "F":
+            return filters.fourier_band(a, s[0], s[1])
         return filters.apply_kernel(a, self.kernels[(f, s)], self.mask, self.walls)
 
     def qoi_values(self, v):

@@ -19,11 +19,11 @@ FORCING = {"edm": 0, "guo": 1}
 SUBSTRATE = {"none": 0, "smag": 1, "wale": 2}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 QOI_KIND = {"E": 0, "Z": 1}
-FILTER = {"G": 0, "L": 1, "B": 2}
+FILTER = {"G": 0, "L": 1, "B": 2, "F": 3}
 TO_MODE = {"off": 0, "observe": 1, "gamma": 2, "lrs": 3, "track": 4}
 MAX_QOI = 16
 FLAG_SINGULAR, FLAG_UNSTABLE = 1, 2
-K_NAMES = ["moments", "collide", "curl", "filter", "sens", "reduce", "lrs", "solve", "apply", "gauss3", "lap3"]
+K_NAMES = ["moments", "collide", "curl", "filter", "sens", "reduce", "lrs", "solve", "apply", "gauss3", "lap3", "fft"]
 EXPORTED = [
     "lbm_qoi_row_len", "lbm_required_bytes", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_macros",
     "lbm_set_lrs", "lbm_set_track_reference", "lbm_step", "lbm_sync", "lbm_qoi", "lbm_get_macros",
@@ -41,7 +41,7 @@ class lbm_completion(C.Structure):
 
 
 class lbm_qoi_spec(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("filter", C.c_int32), ("scale", C.c_int32), ("pad", C.c_int32)]
+    _fields_ = [("kind", C.c_int32), ("filter", C.c_int32), ("scale", C.c_int32), ("band_hi", C.c_int32)]
 
 
 class lbm_config(C.Structure):
@@ -156,7 +156,11 @@ def config_from_workload(wl, member=0):
     c.n_qoi = len(qois)
     c.n_mp = wl["n_mp"] if wl["to_mode"] != "off" else 0
     for i, (kind, filt, scale) in enumerate(qois):
-        c.qoi[i].kind, c.qoi[i].filter, c.qoi[i].scale = QOI_KIND[kind], FILTER[filt], scale
+        c.qoi[i].kind, c.qoi[i].filter = QOI_KIND[kind], FILTER[filt]
+        if filt == "F":
+            c.qoi[i].scale, c.qoi[i].band_hi = scale
+        else:
+            c.qoi[i].scale = scale
     c.h = wl["h"]
     c.qoi_ring = wl.get("qoi_ring", 0)
     c.gamma_std = wl["gamma_std"]

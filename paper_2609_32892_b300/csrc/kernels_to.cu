@@ -99,6 +99,29 @@ __global__ void __launch_bounds__(256) pass_kernel(Params p, const float* __rest
     }
 }
 
+// ------------------------------------------------------- Fourier bands --
+// out = in * (1/(nx ny) if lo - 1/2 <= |k| < hi + 1/2 else 0) on the R2C half
+// spectrum [c][ky][kx] (kx = 0..nx/2, ky folded to -ny/2..ny/2-1): the sharp
+// filter R_[lo,hi] of Sec. 4.1 with the inverse transform's normalisation.
+// The band edges sit at half-integers, so the test on the integer |k|^2 is exact.
+__global__ void __launch_bounds__(256) band_mask_kernel(Params p, const float2* __restrict__ in,
+                                                        float2* __restrict__ out, int ncomp, int lo, int hi) {
+    const int nxh = p.nx / 2 + 1;
+    const long long per = (long long)p.ny * nxh;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= per * ncomp) return;
+    const long long e = i % per;
+    const int kx = (int)(e % nxh);
+    const int jy = (int)(e / nxh);
+    const int ky = jy <= p.ny / 2 ? jy : jy - p.ny;
+    const long long k2 = (long long)kx * kx + (long long)ky * ky;
+    // lo - 1/2 <= |k|  <=>  k2 >= lo^2 - lo + 1 (lo >= 1);  |k| < hi + 1/2  <=>  k2 <= hi^2 + hi
+    const bool keep = (lo == 0 || k2 >= (long long)lo * lo - lo + 1) && k2 <= (long long)hi * hi + hi;
+    const float sc = keep ? 1.0f / ((float)p.nx * (float)p.ny) : 0.f;
+    const float2 v = in[i];
+    out[i] = make_float2(v.x * sc, v.y * sc);
+}
+
 // ---------------------------------------------- enstrophy sensitivities --
 // V_Z = curl*(W), W = R R omega (App. A): 2-D (d_y W, -d_x W); 3-D curl W.
 __global__ void __launch_bounds__(256) sens_curl_kernel(Params p, const float* __restrict__ w, float* __restrict__ out) {
@@ -466,6 +489,12 @@ cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp,
     const cudaError_t e = launch_pass_fast(p, in, out, ncomp, axis, t, scale, accumulate, s);
     if (e != cudaErrorNotSupported) return e;
     pass_kernel<<<gridn(p.n, 256), 256, 0, s>>>(p, in, out, ncomp, axis, t, scale, accumulate);
+    return cudaGetLastError();
+}
+cudaError_t launch_band_mask(const Params& p, const float2* in, float2* out, int ncomp, int lo, int hi,
+                             cudaStream_t s) {
+    const long long n = (long long)p.ny * (p.nx / 2 + 1) * ncomp;
+    band_mask_kernel<<<gridn(n, 256), 256, 0, s>>>(p, in, out, ncomp, lo, hi);
     return cudaGetLastError();
 }
 cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s) {

@@ -9,6 +9,8 @@
 
 #include <vector>
 
+#include <cufft.h>
+
 #include "lbm_common.cuh"
 
 using namespace lbm;
@@ -19,7 +21,8 @@ thread_local char g_err[256] = "";
 
 struct Filter {
     int kind;   // LBM_FILTER_*
-    int scale;
+    int scale;  // s, or the lower wavenumber bin of a Fourier band
+    int hi;     // upper wavenumber bin of a Fourier band
     bool need_z;
 };
 
@@ -52,6 +55,8 @@ struct lbm_ctx {
     int lrs_set;
     int autotune;     // tune launch shapes before the first step (default on)
     int tuned;
+    cufftHandle fft_r2c, fft_c2r;  // Fourier-band filters (3 components batched)
+    bool has_fft;
 };
 
 static int fail(lbm_ctx* c, int code, const char* fmt, ...) {
@@ -104,7 +109,13 @@ static int validate(const lbm_config* c) {
         for (int i = 0; i < c->n_qoi; ++i) {
             const lbm_qoi_spec& s = c->qoi[i];
             if (s.kind != LBM_QOI_ENERGY && s.kind != LBM_QOI_ENSTROPHY) return fail(nullptr, LBM_ERR_ARG, "bad QoI kind");
-            if (s.filter < 0 || s.filter > 2) return fail(nullptr, LBM_ERR_ARG, "bad QoI filter");
+            if (s.filter < 0 || s.filter > 3) return fail(nullptr, LBM_ERR_ARG, "bad QoI filter");
+            if (s.filter == LBM_FILTER_FOURIER) {
+                if (c->dim != 2 || c->walls || c->nx != c->ny || c->nx % 2)
+                    return fail(nullptr, LBM_ERR_ARG, "Fourier-band QoIs need a periodic 2-D grid with nx = ny even");
+                if (s.scale < 0 || s.band_hi < s.scale) return fail(nullptr, LBM_ERR_ARG, "bad Fourier band");
+                continue;
+            }
             if (s.filter != LBM_FILTER_BINOMIAL && (s.scale < 1 || s.scale % 2 == 0))
                 return fail(nullptr, LBM_ERR_ARG, "filter scale must be odd and >= 1");
             const int alpha = c->dim == 2 ? 4 : 2;
@@ -128,11 +139,12 @@ static std::vector<Filter> distinct_filters(const lbm_config* c, int* slot) {
     for (int i = 0; i < c->n_qoi; ++i) {
         const int kind = c->qoi[i].filter;
         const int s = kind == LBM_FILTER_BINOMIAL ? 1 : c->qoi[i].scale;
+        const int hi = kind == LBM_FILTER_FOURIER ? c->qoi[i].band_hi : 0;
         int found = -1;
         for (size_t j = 0; j < out.size(); ++j)
-            if (out[j].kind == kind && out[j].scale == s) found = (int)j;
+            if (out[j].kind == kind && out[j].scale == s && out[j].hi == hi) found = (int)j;
         if (found < 0) {
-            out.push_back({kind, s, false});
+            out.push_back({kind, s, hi, false});
             found = (int)out.size() - 1;
         }
         if (c->qoi[i].kind == LBM_QOI_ENSTROPHY) out[found].need_z = true;
@@ -211,6 +223,25 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     }
 }
 
+// cuFFT 2-D transforms of the three filtered components (v_x, v_y, omega),
+// batched with component stride N, real <-> half spectrum
+static void fft_dims(const Params& p, int n[2], int rin[2], int cout_[2]) {
+    n[0] = p.ny; n[1] = p.nx;
+    rin[0] = p.ny; rin[1] = p.nx;
+    cout_[0] = p.ny; cout_[1] = p.nx / 2 + 1;
+}
+
+static size_t fft_work_bytes(const Params& p) {
+    int n[2], rin[2], co[2];
+    fft_dims(p, n, rin, co);
+    const int idist = p.ny * p.nx, odist = p.ny * (p.nx / 2 + 1);
+    size_t a = 0, b = 0;
+    cufftEstimateMany(2, n, rin, 1, idist, co, 1, odist, CUFFT_R2C, 3, &a);
+    cufftEstimateMany(2, n, co, 1, odist, rin, 1, idist, CUFFT_C2R, 3, &b);
+    const size_t w = a > b ? a : b;
+    return (w + (1 << 20)) & ~(size_t)255;  // estimate plus margin
+}
+
 static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filter>& filt, char* base, Layout* L,
                     float** aux) {
     Carver cv;
@@ -251,6 +282,14 @@ static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filt
         if (p.track_len > 0) l.track = cv.take<double>((size_t)p.track_len * p.n_q);
         l.w_mp = cv.take<double>((size_t)(p.n_mp > 0 ? p.n_mp : 1) * p.ny);
         l.g_mpmp = cv.take<double>((size_t)(p.n_mp > 0 ? p.n_mp * p.n_mp : 1));
+        bool fourier = false;
+        for (const Filter& f : filt) fourier = fourier || f.kind == LBM_FILTER_FOURIER;
+        if (fourier) {
+            const size_t nspec = (size_t)3 * p.ny * (p.nx / 2 + 1);
+            l.spec = cv.take<float2>(nspec);
+            l.spec_band = cv.take<float2>(nspec);
+            l.fft_work = cv.take<char>(fft_work_bytes(p));
+        }
         l.beta = cv.take<double>(kMaxQoi);
         l.ring = cv.take<double>((size_t)p.ring_cap * p.row_len);
         l.profile = cv.take<double>(p.ny);
@@ -328,6 +367,17 @@ struct Launcher {
     }
 };
 
+// a library call (cuFFT): timed like a kernel, not counted as one of ours
+#define LIBCALL(lc, cls, expr)                                       \
+    do {                                                             \
+        if (!(lc).count_only) {                                      \
+            const int n_ = (int)(lc).n;                              \
+            (lc).before(cls);                                        \
+            (lc).n = n_;                                             \
+            (lc).after((expr) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown); \
+        }                                                            \
+    } while (0)
+
 #define LAUNCH(lc, cls, expr)              \
     do {                                   \
         (lc).before(cls);                  \
@@ -337,6 +387,7 @@ struct Launcher {
 // taps of one application of a separable filter per output: G/B d(2R+1);
 // L_s d x (5 s arm + (d-1) s box taps, the box omitted when s = 1)
 static double filter_taps(const Filter& f, int d) {
+    if (f.kind == LBM_FILTER_FOURIER) return 0.0;  // transforms, counted separately
     if (f.kind == LBM_FILTER_GAUSS) return d * (2.0 * (d == 2 ? 4 : 2) * f.scale + 1.0);
     if (f.kind == LBM_FILTER_BINOMIAL) return d * 3.0;
     return d * (5.0 * f.scale + (f.scale > 1 ? (d - 1) * (double)f.scale : 0.0));
@@ -415,11 +466,22 @@ static void enqueue_step(Launcher& lc, int src) {
     if (p.to_mode == LBM_TO_OFF) return;
     if (p.to_mode == LBM_TO_LRS) LAUNCH(lc, LBM_K_LRS, launch_lrs_hist(p, L, lc.s));
     LAUNCH(lc, LBM_K_CURL, launch_to_curl(p, L, lc.s));
+    if (c->has_fft) {
+        // one forward transform of (v_x, v_y, omega) serves every Fourier band
+        LIBCALL(lc, LBM_K_FFT, (cufftSetStream(c->fft_r2c, lc.s), cufftExecR2C(c->fft_r2c, (cufftReal*)L.x6, (cufftComplex*)L.spec)));
+    }
     for (size_t f = 0; f < c->filters.size(); ++f) {
-        enqueue_filter(lc, c->filters[f], (int)f, L.x6, L.acc);
-        enqueue_filter(lc, c->filters[f], (int)f, L.acc, L.rr[f]);
-        if (c->filters[f].need_z)
-            LAUNCH(lc, LBM_K_SENS, launch_sens_curl(p, L.rr[f] + (size_t)p.dim * p.n, L.vz[f], lc.s));
+        const Filter& fl = c->filters[f];
+        if (fl.kind == LBM_FILTER_FOURIER) {
+            // a sharp band is a projection, R R = R: one masked inverse transform
+            LAUNCH(lc, LBM_K_FILTER, launch_band_mask(p, L.spec, L.spec_band, 3, fl.scale, fl.hi, lc.s));
+            LIBCALL(lc, LBM_K_FFT, (cufftSetStream(c->fft_c2r, lc.s),
+                                    cufftExecC2R(c->fft_c2r, (cufftComplex*)L.spec_band, (cufftReal*)L.rr[f])));
+        } else {
+            enqueue_filter(lc, fl, (int)f, L.x6, L.acc);
+            enqueue_filter(lc, fl, (int)f, L.acc, L.rr[f]);
+        }
+        if (fl.need_z) LAUNCH(lc, LBM_K_SENS, launch_sens_curl(p, L.rr[f] + (size_t)p.dim * p.n, L.vz[f], lc.s));
     }
     const float* vk[kMaxQoi];
     for (int k = 0; k < p.n_s; ++k) {
@@ -652,9 +714,13 @@ static int autotune(lbm_ctx* c) {
                 }
                 p.tune.filter_per_sm[f] = pick;
             }
-        } else if (!c->filters.empty()) {
-            // 2-D: the y-axis march of the widest filter
-            const Filter& fl = c->filters[0];
+        } else {
+            // 2-D: the y-axis march of the first compact filter
+            const Filter* fp = nullptr;
+            for (const Filter& f : c->filters)
+                if (!fp && f.kind != LBM_FILTER_FOURIER) fp = &f;
+            if (!fp) goto tuned;
+            const Filter& fl = *fp;
             const Taps t0 = fl.kind == LBM_FILTER_GAUSS ? gauss_taps(fl.scale, 2)
                             : fl.kind == LBM_FILTER_BINOMIAL ? binom_taps() : ell_taps(fl.scale);
             static const int cand[] = {148 * 256, 148 * 512, 148 * 1024, 148 * 2048, 148 * 4096};
@@ -668,6 +734,7 @@ static int autotune(lbm_ctx* c) {
             p.tune.march_lines = pick;
         }
     }
+tuned:
     if (err != cudaSuccess) return fail(c, LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(err));
     CK(c, cudaStreamSynchronize(c->stream));
     {
@@ -717,6 +784,25 @@ int lbm_create(const lbm_config* cfg, void* dev_buf, size_t bytes, void* cuda_st
     c->elem = cfg->storage == LBM_STORAGE_FP32 ? 4 : 2;
     c->use_graphs = 1;
     c->autotune = 1;
+    c->has_fft = c->L.spec != nullptr;
+    if (c->has_fft) {
+        int n[2], rin[2], co[2];
+        fft_dims(c->p, n, rin, co);
+        const int idist = c->p.ny * c->p.nx, odist = c->p.ny * (c->p.nx / 2 + 1);
+        size_t w1 = 0, w2 = 0;
+        const size_t avail = fft_work_bytes(c->p);
+        bool ok = cufftCreate(&c->fft_r2c) == CUFFT_SUCCESS && cufftCreate(&c->fft_c2r) == CUFFT_SUCCESS &&
+                  cufftSetAutoAllocation(c->fft_r2c, 0) == CUFFT_SUCCESS &&
+                  cufftSetAutoAllocation(c->fft_c2r, 0) == CUFFT_SUCCESS &&
+                  cufftMakePlanMany(c->fft_r2c, 2, n, rin, 1, idist, co, 1, odist, CUFFT_R2C, 3, &w1) == CUFFT_SUCCESS &&
+                  cufftMakePlanMany(c->fft_c2r, 2, n, co, 1, odist, rin, 1, idist, CUFFT_C2R, 3, &w2) == CUFFT_SUCCESS;
+        ok = ok && w1 <= avail && w2 <= avail && cufftSetWorkArea(c->fft_r2c, c->L.fft_work) == CUFFT_SUCCESS &&
+             cufftSetWorkArea(c->fft_c2r, c->L.fft_work) == CUFFT_SUCCESS;
+        if (!ok) {
+            delete c;
+            return fail(nullptr, LBM_ERR_CUDA, "cuFFT plan set-up failed (work area %zu/%zu of %zu bytes)", w1, w2, avail);
+        }
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
@@ -761,6 +847,10 @@ int lbm_destroy(lbm_ctx* c) {
     for (int i = 0; i < 2 * 96; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->has_fft) {
+        cufftDestroy(c->fft_r2c);
+        cufftDestroy(c->fft_c2r);
+    }
     delete c;
     return LBM_OK;
 }

@@ -60,6 +60,9 @@ struct Layout {
     double* beta;        // [N_Q] SGS coefficients of the current step (beta = G^-1 dQ)
     double* ring;        // [ring_cap][row_len]
     double* profile;     // [ny]
+    float2* spec;        // [3][ny][nx/2+1] spectrum of (v_x, v_y, omega) (Fourier bands)
+    float2* spec_band;   // [3][ny][nx/2+1] one band of it
+    void* fft_work;      // cuFFT work area
     DevState* st;
 };
 
@@ -109,6 +112,8 @@ cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp,
                         float scale, int accumulate, int per_sm, cudaStream_t s);
 inline bool launch_gauss3_supported(int radius) { return radius == 1 || radius == 2 || radius == 4 || radius == 6; }
 inline bool launch_lap3_supported(int s_scale) { return s_scale == 1 || s_scale == 3; }
+cudaError_t launch_band_mask(const Params& p, const float2* in, float2* out, int ncomp, int lo, int hi,
+                             cudaStream_t s);
 cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s);
 cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* vk, cudaStream_t s);
 cudaError_t launch_lrs_hist(const Params& p, const Layout& L, cudaStream_t s);

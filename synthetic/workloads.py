@@ -11,7 +11,8 @@ A workload is a plain dict of parameters.  Keys:
   kolmo_drag          linear drag rate alpha: force density -alpha * rho v
   substrate           'none' | 'smag' | 'wale', with c_smag / c_wale
   qois                list of (kind, filter, scale): kind 'E' or 'Z',
-                      filter 'G' (Gaussian), 'L' (Laplacian) or 'B' (3x3 binomial)
+                      filter 'G' (Gaussian), 'L' (Laplacian), 'B' (3x3 binomial)
+                      or 'F' (sharp Fourier band, scale = (l, m) wavenumber bins)
   n_mp                number of mean-profile QoIs (channel only)
   to_mode             'off' | 'gamma' | 'lrs' | 'track'
   gamma_std           std of the per-step random gamma ('gamma' mode)
@@ -91,6 +92,17 @@ def _c4_to_mid():
     return w
 
 
+def _c2f():
+    """The Kolmogorov LES with sharp Fourier-band QoIs (App. E bins on 128^2)."""
+    p = kolmogorov_lattice(128)
+    w = _c2()
+    w.update(name="kolmogorov2d_128_smag_tolrs_fourier", nx=128, ny=128, tau=p["tau"], kolmo_amp=p["kolmo_amp"],
+             kolmo_drag=p["kolmo_drag"],
+             qois=[("E", "F", (0, 12)), ("Z", "F", (0, 12)), ("E", "F", (13, 32)), ("Z", "F", (13, 32)),
+                   ("E", "F", (33, 128)), ("Z", "F", (33, 128))], seed=20260907)
+    return w
+
+
 WORKLOADS = {
     "C1": _c1,
     "C2": _c2,
@@ -98,6 +110,7 @@ WORKLOADS = {
     "C4": _c4,
     "C4_TO": _c4_to,
     "C4_TO_MID": _c4_to_mid,
+    "C2F": _c2f,
 }
 
 

@@ -226,3 +226,17 @@ def test_lrs_with_tracked_spin_up():
     _, rgt, rho_g, u_g = run_gpu(w, 12, lrs=lrs, track=ref)
     _compare_state(w, rho_g, u_g, rho_o, u_o)
     _compare_rows(w, rgt, rot)
+
+
+@pytest.mark.parametrize("mode", ["gamma", "lrs"])
+def test_fourier_band_qois_2d(mode):
+    """Sharp Fourier-band QoIs (App. E) through batched cuFFT transforms and a
+    band mask, against the oracle's numpy FFT on a 32^2 Kolmogorov grid."""
+    bands = [(0, 2), (3, 5), (6, 32)]
+    qois = [(k, "F", b) for b in bands for k in ("E", "Z")]
+    wl = synthetic.workload("C2", nx=32, ny=32, h=2, qois=qois, to_mode=mode, gamma_std=1e-2)
+    lrs = lrs_inputs(wl, np.zeros(nq_of(wl))) if mode == "lrs" else None
+    _, ro, rho_o, u_o = run_oracle(wl, 20, lrs=lrs)
+    _, rg, rho_g, u_g = run_gpu(wl, 20, lrs=lrs)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)

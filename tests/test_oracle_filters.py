@@ -139,3 +139,25 @@ def test_curl_adjoint(dim, walls):
     ca = to.curl(a, dim, walls) * mask
     cb = to.curl_adjoint(b, dim, walls) * mask
     assert abs((ca * b).sum() - (a * cb).sum()) < 1e-12
+
+
+def test_fourier_bands_are_orthogonal_projections():
+    """R_[l,m] is idempotent and self-adjoint, bands covering the spectrum sum
+    to the identity, and band energies add up to the total (Parseval)."""
+    rng = np.random.default_rng(9)
+    a = rng.normal(size=(2, 1, 32, 32))
+    bands = [(0, 3), (4, 9), (10, 40)]
+    parts = [filters.fourier_band(a, lo, hi) for lo, hi in bands]
+    np.testing.assert_allclose(sum(parts), a, atol=1e-12)
+    for (lo, hi), r in zip(bands, parts):
+        np.testing.assert_allclose(filters.fourier_band(r, lo, hi), r, atol=1e-12)
+    b = rng.normal(size=a.shape)
+    rb = filters.fourier_band(b, 4, 9)
+    assert abs((parts[1] * b).sum() - (a * rb).sum()) < 1e-10
+    e_tot = 0.5 * (a * a).sum()
+    assert abs(sum(0.5 * (r * r).sum() for r in parts) - e_tot) < 1e-10 * e_tot
+    # a single mode lands in the band of its wavenumber |k| = 5
+    y, x = np.meshgrid(np.arange(32), np.arange(32), indexing="ij")
+    mode = np.cos(2 * np.pi * (3 * x + 4 * y) / 32)[None, None]
+    np.testing.assert_allclose(filters.fourier_band(mode, 4, 9), mode, atol=1e-12)
+    np.testing.assert_allclose(filters.fourier_band(mode, 0, 3), 0, atol=1e-12)

@@ -8,6 +8,7 @@ from oracle import to
 CASES = [
     (2, False, (1, 12, 10), [("E", "G", 3), ("Z", "G", 3), ("E", "L", 1), ("Z", "L", 1)], 0),
     (2, False, (1, 8, 8), [("E", "B", 1), ("Z", "B", 1)], 0),
+    (2, False, (1, 16, 16), [("E", "F", (0, 2)), ("Z", "F", (0, 2)), ("E", "F", (3, 5)), ("Z", "F", (3, 5))], 0),
     (3, True, (4, 16, 6), [("E", "G", 3), ("Z", "G", 3), ("E", "L", 3), ("Z", "L", 3), ("E", "L", 1), ("Z", "L", 1)], 6),
 ]
 

@@ -28,6 +28,11 @@ import time
 
 import numpy as np
 
+# The serving leg runs many members, each on its own stream; more hardware
+# work queues than the default 8 keep their streams from aliasing onto shared
+# queues.  Read when the CUDA context is created, so set before any CUDA call.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 

@@ -217,6 +217,15 @@ enum {
 };
 int lbm_set_graphs(lbm_ctx* ctx, int enable);
 
+/* Step branching (default on): the LRS history product (Eq. LRS, the terms
+ * known before the current QoIs) and the step's normals need only the previous
+ * step, so lbm_step runs them on a second stream of the context beside the
+ * field kernels and joins before the solve.  0 runs them in line on the
+ * context's stream (members of an lbm_batch do: they already overlap one
+ * another).  Results are identical either way.  Must precede the first
+ * lbm_step (LBM_ERR_STATE after it). */
+int lbm_set_branching(lbm_ctx* ctx, int enable);
+
 /* Autotuner (default on): before the first lbm_step the library times the
  * candidate launch shapes of its kernels on this context's buffers (node-pair
  * vs single-node collide, 4-node vs single-node SGS apply, the z-segment count

@@ -31,7 +31,7 @@ EXPORTED = [
     "lbm_save", "lbm_load", "lbm_set_graphs", "lbm_profile", "lbm_profile_read", "lbm_launches_per_step",
     "lbm_qoi_eval_static", "lbm_filter_flops_per_step",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_admit", "lbm_batch_member", "lbm_batch_run",
-    "lbm_batch_poll", "lbm_batch_release", "lbm_batch_stats", "lbm_set_autotune", "lbm_get_tuning",
+    "lbm_batch_poll", "lbm_batch_release", "lbm_batch_stats", "lbm_set_autotune", "lbm_get_tuning", "lbm_set_branching",
 ]
 
 
@@ -98,6 +98,7 @@ def _load():
         "lbm_batch_release": [VP, C.c_int32],
         "lbm_batch_stats": [VP, P(C.c_size_t), P(C.c_size_t), P(C.c_int32)],
         "lbm_set_autotune": [VP, C.c_int],
+        "lbm_set_branching": [VP, C.c_int],
         "lbm_get_tuning": [VP, P(C.c_int32), C.c_int],
     }
     for name, args in sig.items():
@@ -360,6 +361,10 @@ def lbm_batch_stats(b):
 
 def lbm_set_autotune(ctx, enable):
     _check(_lib.lbm_set_autotune(ctx, int(bool(enable))), ctx)
+
+
+def lbm_set_branching(ctx, enable):
+    _check(_lib.lbm_set_branching(ctx, int(bool(enable))), ctx)
 
 
 def lbm_get_tuning(ctx):

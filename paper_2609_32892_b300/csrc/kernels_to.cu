@@ -7,6 +7,7 @@
 // central differences use beyond the walls (Sec. 4.1).
 #include "lbm_common.cuh"
 #include "rng.cuh"
+#include "dfloat.cuh"
 
 namespace lbm {
 
@@ -159,14 +160,17 @@ __global__ void __launch_bounds__(256) sens_curl_kernel(Params p, const float* _
 // ------------------------------------------------------ block reduction --
 // Per block (one y row, a chunk of z planes): <v*, V_k> and <V_i, V_j> (i <= j)
 // over its fluid nodes, and the row sums of v*_x and V_k,x (the mean-profile
-// couplings).  FP32 per thread over a few nodes, FP64 across threads/blocks.
+// couplings).  FP32 throughout the block (per thread over a few nodes, then a
+// warp tree); the partials are summed with compensation in the solve.  No
+// double-precision arithmetic here: on this GPU an FP64 warp tree over the
+// NV values of every block costs more than the whole field traversal.
 struct RedPtrs {
     const float* v[kMaxQoi];
 };
 
 template <int NS>
 __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __restrict__ vps, RedPtrs vk,
-                                                     double* __restrict__ part, double* __restrict__ plane_part) {
+                                                     float* __restrict__ part, float* __restrict__ plane_part) {
     constexpr int NG = NS * (NS + 1) / 2;
     constexpr int NV = NS + NG + 1 + NS;  // <v,V_k>, Gram, row sums (v_x, V_k,x)
     const int y = blockIdx.x;
@@ -204,11 +208,11 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
 #pragma unroll
         for (int k = 0; k < NS; ++k) acc[idx++] += w[k][0];
     }
-    __shared__ double sh[4][NV];
+    __shared__ float sh[4][NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        double a = (double)acc[v];
+        float a = acc[v];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if (lane == 0) sh[wid][v] = a;
@@ -216,259 +220,269 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
     __syncthreads();
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
     for (int v = threadIdx.x; v < NV; v += blockDim.x) {
-        const double s = (sh[0][v] + sh[1][v]) + (sh[2][v] + sh[3][v]);
+        const float s = (sh[0][v] + sh[1][v]) + (sh[2][v] + sh[3][v]);
         if (v < NS + NG) part[(size_t)blk * (NS + NG) + v] = s;
         else plane_part[((size_t)zc * p.ny + y) * (1 + NS) + (v - NS - NG)] = s;
     }
 }
 
-// ------------------------------------------------ LRS history matvec --
-// Partial sums over the rows of C whose inputs are already known before the
-// current QoIs: the histories q^{n-1..n-h}, q^{n-1*..n-h*} (scaled by
-// sigma_ref) and the bias 1 (Eq. LRS).  The q^{n*} block is added in the solve.
-__global__ void __launch_bounds__(256) lrs_hist_kernel(Params p, Layout L) {
-    const int nq = p.n_q, h = p.h;
-    const long long rows = (long long)(2 * h + 1) * nq + 1;
-    const long long r0 = (long long)blockIdx.x * p.lrs_rows_per_blk;
-    const long long r1 = min(rows, r0 + p.lrs_rows_per_blk);
-    const long long pos = L.st->hist_pos;
-    double acc[kMaxQoi];
-    for (int k = 0; k < nq; ++k) acc[k] = 0.0;
-    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double xr;
-        if (r < (long long)h * nq) {
-            const int kk = (int)(r / nq) + 1, i = (int)(r % nq);
-            const long long slot = ((pos - kk) % h + h) % h;
-            const double sg = L.lrs_sigma[i];
-            xr = sg > 0.0 ? L.qh[slot * nq + i] / sg : 0.0;  // sigma <= 0: not yet set, histories are zero
-        } else if (r < (long long)(h + 1) * nq) {
-            continue;
-        } else if (r < rows - 1) {
-            const long long rr = r - (long long)(h + 1) * nq;
-            const int kk = (int)(rr / nq) + 1, i = (int)(rr % nq);
-            const long long slot = ((pos - kk) % h + h) % h;
-            const double sg = L.lrs_sigma[i];
-            xr = sg > 0.0 ? L.qsh[slot * nq + i] / sg : 0.0;
-        } else {
-            xr = 1.0;
-        }
-        const double* c = L.lrs_C + r * nq;
-        for (int k = 0; k < nq; ++k) acc[k] = fma(xr, c[k], acc[k]);
+// ------------------------------------------- LRS history matvec, normals --
+// Runs on a side branch of the step (it needs only the previous step's
+// histories and the step counter), so its latency hides behind the field
+// kernels.  Blocks 0..nblk_lrs-1: partial sums of x_r C[r][:] over the rows of
+// C whose inputs are known before the current QoIs: the histories
+// q^{n-1..n-h} and q^{n-1*..n-h*} (scaled by sigma_ref) and the bias 1
+// (Eq. LRS); the q^{n*} block is added in the solve.  A block first forms its
+// rows' inputs x_r in shared memory (one division each, as in the model),
+// then thread (j, k) accumulates rows j, j + per, ... of column k, so a warp
+// reads consecutive elements of C.  The last block draws the step's normals
+// (the LRS noise or the gamma draws).
+__global__ void __launch_bounds__(256) lrs_pre_kernel(Params p, Layout L, int nb) {
+    const int nq = p.n_q;
+    const long long step = L.st->step;
+    if (blockIdx.x == (unsigned)nb) {
+        const int stream = p.to_mode == LBM_TO_GAMMA ? kStreamGamma : kStreamLrs;
+        if (threadIdx.x < (unsigned)nq) L.znorm[threadIdx.x] = philox_normal(p.seed, p.member, step, stream, threadIdx.x);
+        return;
     }
-    __shared__ double sh[8][kMaxQoi];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = 0; k < nq; ++k) {
-        double a = acc[k];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) sh[wid][k] = a;
+    const int h = p.h;
+    const int rows = (2 * h + 1) * nq + 1;
+    const int r0 = blockIdx.x * p.lrs_rows_per_blk;
+    const int r1 = min(rows, r0 + p.lrs_rows_per_blk);
+    const int posm = (int)(L.st->hist_pos % h);
+    __shared__ double xs[kLrsRowsPerBlk];
+    __shared__ double sh[256];
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double xr = 0.0;
+        if (r < h * nq || (r >= (h + 1) * nq && r < rows - 1)) {
+            const bool corrected = r < h * nq;
+            const int rr = corrected ? r : r - (h + 1) * nq;
+            const int kk = rr / nq + 1, i = rr - (kk - 1) * nq;
+            int slot = posm - kk;
+            if (slot < 0) slot += h;
+            const double sg = L.lrs_sigma[i];
+            const double qv = corrected ? L.qh[(size_t)slot * nq + i] : L.qsh[(size_t)slot * nq + i];
+            xr = sg > 0.0 ? qv / sg : 0.0;  // sigma <= 0: not yet set, the histories are zero
+        } else if (r == rows - 1) {
+            xr = 1.0;
+        }  // rows of the q^{n*} block: added in the solve
+        xs[r - r0] = xr;
     }
     __syncthreads();
-    if (threadIdx.x < nq) {
+    const int per = blockDim.x / nq;
+    const int j = threadIdx.x / nq, k = threadIdx.x - j * nq;
+    double acc = 0.0;
+    if (j < per)
+        for (int r = r0 + j; r < r1; r += per) acc = fma(xs[r - r0], L.lrs_C[(size_t)r * nq + k], acc);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < (unsigned)nq) {
         double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][threadIdx.x];
+        for (int jj = 0; jj < per; ++jj) s += sh[jj * nq + threadIdx.x];
         L.lrs_part[(size_t)blockIdx.x * nq + threadIdx.x] = s;
     }
 }
 
 // ------------------------------------------------------------- solve --
-// One block: sum the partials, assemble q^{n*} and the Gram matrix, draw the
-// normals, evaluate the coefficient source, Cholesky-factor G (FP64), and
-// produce beta = G^-1 dQ (dv_SGS = sum_k beta_k V_k equals sum_i gamma_i O_i
-// with c_ij and gamma_i of Sec. 4.2-4.3), gamma_i = dQ_i (G^-1)_ii.  Then
-// write the QoI block row, push the LRS histories, add the mean profile and
-// advance the step counter.
+// One block: sum the partials, assemble q^{n*} and the Gram matrix, evaluate
+// the coefficient source, factor G = X^-1 D X^-T (LDL^T, FP64), and produce
+// beta = G^-1 dQ (dv_SGS = sum_k beta_k V_k equals sum_i gamma_i O_i with c_ij
+// and gamma_i of Sec. 4.2-4.3), gamma_i = dQ_i (G^-1)_ii.  Then write the QoI
+// block row, push the LRS histories, add the mean profile and advance the step
+// counter.
+//
+// Double-precision operations issue slowly on this GPU and this kernel is on
+// the critical path of every step, so its FP64 work is arranged as short
+// parallel chains: sums of FP32 partials are compensated single-precision
+// sums widened once, the factorisation is right-looking with one reciprocal
+// per pivot, and the triangular products run one row/column per lane.
 __global__ void __launch_bounds__(256) solve_kernel(Params p, Layout L) {
     const int ns = p.n_s, nmp = p.n_mp, nq = p.n_q;
     const int ng = ns * (ns + 1) / 2;
     const int npart = ns + ng;
     __shared__ double red[kMaxQoi + kMaxQoi * (kMaxQoi + 1) / 2];
-    __shared__ double G[kMaxQoi][kMaxQoi];
-    __shared__ double Lc[kMaxQoi][kMaxQoi];
-    __shared__ double Li[kMaxQoi][kMaxQoi];
-    __shared__ double q[kMaxQoi], dq[kMaxQoi], gam[kMaxQoi], beta[kMaxQoi], z[kMaxQoi], tmp[kMaxQoi], sigs[kMaxQoi];
+    __shared__ double A[kMaxQoi][kMaxQoi + 1];   // G, overwritten by the factorisation
+    __shared__ double Lc[kMaxQoi][kMaxQoi + 1];  // unit lower factor
+    __shared__ double X[kMaxQoi][kMaxQoi + 1];   // its inverse
+    __shared__ double invD[kMaxQoi];
+    __shared__ double q[kMaxQoi], dq[kMaxQoi], beta[kMaxQoi], z[kMaxQoi], hpart[kMaxQoi], qnew[kMaxQoi];
+    __shared__ double xq[kMaxQoi], yv[kMaxQoi];
     __shared__ double wP[kMaxQoi][kMaxQoi + 1];  // sum_y w_j(y) P_k(y), k = 0 (v_x), 1..ns (V_k,x)
-    __shared__ int singular;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const long long step = L.st->step;
+    const bool lrs = p.to_mode == LBM_TO_LRS;
 
-    // 1. block partials -> totals (fixed order: strided lanes, then tree)
+    // 1. totals of the block partials (one warp per value) and the LRS
+    //    history partials; plane sums P_k(y) over the z chunks (one per thread)
     for (int v = wid; v < npart; v += nw) {
-        double a = 0.0;
-        for (int b = lane; b < p.nblk_red; b += 32) a += L.part[(size_t)b * npart + v];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        const double a = df_warp_sum(L.part + v, p.nblk_red, (size_t)npart, lane);
         if (lane == 0) red[v] = a;
     }
-    // 2. plane sums P_k(y) over the z chunks
+    if (lrs)
+        for (int k = wid; k < nq; k += nw) {
+            double a = 0.0;
+            for (int b = lane; b < p.nblk_lrs; b += 32) a += L.lrs_part[(size_t)b * nq + k];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) hpart[k] = a;
+        }
     const int np1 = 1 + ns;
     for (int e = tid; e < p.ny * np1; e += blockDim.x) {
-        const int y = e / np1, k = e % np1;
-        double a = 0.0;
-        for (int zc = 0; zc < p.nzc; ++zc) a += L.plane_part[((size_t)zc * p.ny + y) * np1 + k];
-        L.plane_sum[e] = a;
+        DF a = {0.f, 0.f};
+        for (int zc = 0; zc < p.nzc; ++zc) a = df_add(a, L.plane_part[((size_t)zc * p.ny) * np1 + e]);
+        L.plane_sum[e] = (double)a.hi + (double)a.lo;
     }
     __syncthreads();
-    // 3. mean-profile couplings sum_y w_j(y) P_k(y)
-    for (int e = tid; e < nmp * np1; e += blockDim.x) {
-        const int j = e / np1, k = e % np1;
+    // 2. mean-profile couplings sum_y w_j(y) P_k(y): one warp per (j, k), lanes over y
+    for (int e = wid; e < nmp * np1; e += nw) {
+        const int j = e / np1, k = e - j * np1;
         double a = 0.0;
-        for (int y = 0; y < p.ny; ++y) a += L.w_mp[(size_t)j * p.ny + y] * L.plane_sum[(size_t)y * np1 + k];
-        wP[j][k] = a;
-    }
-    // LRS: sum the history partials
-    if (p.to_mode == LBM_TO_LRS && tid < nq) {
-        double a = 0.0;
-        for (int b = 0; b < p.nblk_lrs; ++b) a += L.lrs_part[(size_t)b * nq + tid];
-        tmp[tid] = a;
+        for (int y = lane; y < p.ny; y += 32) a = fma(L.w_mp[(size_t)j * p.ny + y], L.plane_sum[(size_t)y * np1 + k], a);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) wP[j][k] = a;
     }
     __syncthreads();
-    // 4. q^{n*} and G
-    if (tid < nq) {
-        const int i = tid;
-        q[i] = i < ns ? 0.5 * red[i] : wP[i - ns][0];
-        for (int j = 0; j < nq; ++j) {
-            double gij;
-            if (i < ns && j < ns) {
-                const int a = min(i, j), b = max(i, j);
-                gij = red[ns + a * ns - a * (a - 1) / 2 + (b - a)];
-            } else if (i >= ns && j >= ns) {
-                gij = L.g_mpmp[(size_t)(i - ns) * nmp + (j - ns)];
-            } else if (i >= ns) {
-                gij = wP[i - ns][1 + j];
-            } else {
-                gij = wP[j - ns][1 + i];
-            }
-            G[i][j] = gij;
-        }
-        z[i] = 0.0;
-        if (p.to_mode == LBM_TO_LRS) z[i] = philox_normal(p.seed, p.member, step, kStreamLrs, i);
-        if (p.to_mode == LBM_TO_GAMMA) z[i] = philox_normal(p.seed, p.member, step, kStreamGamma, i);
-    }
-    __syncthreads();
-    // 5. Cholesky of G with the pivot test (warp 0)
+    // 3. q^{n*}, G, the normals, reference scales (warp 0, lane i = QoI i)
     if (wid == 0) {
-        double dmax = 0.0;
-        for (int i = 0; i < nq; ++i) dmax = fmax(dmax, G[i][i]);
-        int sing = !(dmax > 0.0);
-        for (int k = 0; k < nq && !sing; ++k) {
-            double dk = G[k][k];
-            for (int m = 0; m < k; ++m) dk -= Lc[k][m] * Lc[k][m];
-            if (!(dk > 1e-14 * dmax)) { sing = 1; break; }
-            const double lkk = sqrt(dk);
-            const int i = k + 1 + lane;
-            if (i < nq) {
-                double a = G[i][k];
-                for (int m = 0; m < k; ++m) a -= Lc[i][m] * Lc[k][m];
-                Lc[i][k] = a / lkk;
+        const int i = lane;
+        double gdiag = 0.0;
+        if (i < nq) {
+            q[i] = i < ns ? 0.5 * red[i] : wP[i - ns][0];
+            for (int j = 0; j < nq; ++j) {
+                double gij;
+                if (i < ns && j < ns) {
+                    const int a = min(i, j), b = max(i, j);
+                    gij = red[ns + a * ns - a * (a - 1) / 2 + (b - a)];
+                } else if (i >= ns && j >= ns) {
+                    gij = L.g_mpmp[(size_t)(i - ns) * nmp + (j - ns)];
+                } else if (i >= ns) {
+                    gij = wP[i - ns][1 + j];
+                } else {
+                    gij = wP[j - ns][1 + i];
+                }
+                A[i][j] = gij;
+                if (j == i) gdiag = gij;
             }
-            if (lane == 0) Lc[k][k] = lkk;
+            z[i] = (lrs || p.to_mode == LBM_TO_GAMMA) ? L.znorm[i] : 0.0;
+            if (lrs) {
+                // a reference scale <= 0 is taken from this step's predictor QoI
+                double sg = L.lrs_sigma[i];
+                if (!(sg > 0.0)) {
+                    sg = fabs(q[i]) > 0.0 ? fabs(q[i]) : 1.0;
+                    L.lrs_sigma[i] = sg;
+                }
+                xq[i] = q[i] / sg;
+            }
+        }
+        // 4. LDL^T with the pivot test d_k > 1e-14 max_i G_ii (the Schur
+        //    complements are the Cholesky pivots of Sec. 4.3's singular test)
+        double dmax = gdiag;
+        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        int sing = !(dmax > 0.0);
+        __syncwarp();
+        for (int k = 0; k < nq && !sing; ++k) {
+            const double dk = A[k][k];
+            if (!(dk > 1e-14 * dmax)) { sing = 1; break; }
+            const double inv = 1.0 / dk;
+            if (i == k) { invD[k] = inv; Lc[k][k] = 1.0; }
+            if (i > k && i < nq) Lc[i][k] = A[i][k] * inv;
+            __syncwarp();
+            // trailing update A_ij -= L_ik A_jk (k < j <= i), lanes over i
+            if (i > k && i < nq) {
+                const double lik = Lc[i][k];
+                for (int j = k + 1; j <= i; ++j) A[i][j] = fma(-lik, A[j][k], A[i][j]);
+            }
             __syncwarp();
         }
-        if (lane == 0) singular = sing;
-        __syncwarp();
-        // inverse of the factor, column `lane`: L X = e_lane
-        if (!sing && lane < nq) {
-            const int c = lane;
+        // X = Lc^-1 (unit lower): lane c owns column c, rows in order
+        if (!sing && i < nq) {
             for (int r = 0; r < nq; ++r) {
-                double a = (r == c) ? 1.0 : 0.0;
-                for (int m = c; m < r; ++m) a -= Lc[r][m] * Li[m][c];
-                Li[r][c] = r < c ? 0.0 : a / Lc[r][r];
+                double a = r == i ? 1.0 : 0.0;
+                if (r > i)
+                    for (int m = i; m < r; ++m) a = fma(-Lc[r][m], X[m][i], a);
+                X[r][i] = a;
             }
         }
-    }
-    __syncthreads();
-    // 6. coefficient source -> dQ, gamma, beta
-    if (tid < nq && p.to_mode == LBM_TO_LRS) {
-        // a reference scale <= 0 is taken from this step's predictor QoI
-        const int i = tid;
-        double sg = L.lrs_sigma[i];
-        if (!(sg > 0.0)) {
-            sg = fabs(q[i]) > 0.0 ? fabs(q[i]) : 1.0;
-            L.lrs_sigma[i] = sg;
-        }
-        sigs[i] = sg;
-    }
-    __syncthreads();
-    if (tid < nq) {
-        const int i = tid;
-        double ginv_ii = 0.0;
-        if (!singular)
-            for (int r = i; r < nq; ++r) ginv_ii += Li[r][i] * Li[r][i];
+        __syncwarp();
+        // 5. coefficient source -> dQ, gamma; G^-1 = X^T D^-1 X
         double d = 0.0, g = 0.0;
-        if (p.to_mode == LBM_TO_LRS && step < p.spinup) {
-            // spin-up: nudged to the reference, which enters the history
-            const long long row = step < p.track_len ? step : p.track_len - 1;
-            const double qref = L.track[(size_t)row * nq + i];
-            d = qref - q[i];
-            tmp[i] = qref;
-            g = singular ? 0.0 : d * ginv_ii;
-        } else if (p.to_mode == LBM_TO_LRS) {
-            double qh = tmp[i] + L.lrs_mu[i];
-            for (int j = 0; j < nq; ++j)
-                qh += (q[j] / sigs[j]) * L.lrs_C[((size_t)p.h * nq + j) * nq + i] + L.lrs_L[(size_t)i * nq + j] * z[j];
-            const double qn = sigs[i] * qh;
-            d = qn - q[i];
-            tmp[i] = qn;  // corrected QoI for the history
-            g = singular ? 0.0 : d * ginv_ii;
-        } else if (p.to_mode == LBM_TO_GAMMA) {
-            if (!singular) {
-                g = p.gamma_std * z[i];
-                d = g / ginv_ii;
+        if (i < nq) {
+            double ginv_ii = 0.0;
+            if (!sing)
+                for (int r = i; r < nq; ++r) ginv_ii = fma(X[r][i] * X[r][i], invD[r], ginv_ii);
+            if (lrs && step < p.spinup) {
+                // spin-up: nudged to the reference, which enters the history
+                const long long row = step < p.track_len ? step : p.track_len - 1;
+                const double qref = L.track[(size_t)row * nq + i];
+                d = qref - q[i];
+                qnew[i] = qref;
+                g = sing ? 0.0 : d * ginv_ii;
+            } else if (lrs) {
+                double qh = hpart[i] + L.lrs_mu[i];
+                for (int j = 0; j < nq; ++j)
+                    qh += xq[j] * L.lrs_C[((size_t)p.h * nq + j) * nq + i] + L.lrs_L[(size_t)i * nq + j] * z[j];
+                const double qn = L.lrs_sigma[i] * qh;
+                d = qn - q[i];
+                qnew[i] = qn;  // corrected QoI for the history
+                g = sing ? 0.0 : d * ginv_ii;
+            } else if (p.to_mode == LBM_TO_GAMMA) {
+                if (!sing) {
+                    g = p.gamma_std * z[i];
+                    d = g / ginv_ii;
+                }
+            } else if (p.to_mode == LBM_TO_TRACK) {
+                const long long row = step < p.track_len ? step : p.track_len - 1;
+                d = L.track[(size_t)row * nq + i] - q[i];
+                g = sing ? 0.0 : d * ginv_ii;
             }
-        } else if (p.to_mode == LBM_TO_TRACK) {
-            long long row = step < p.track_len ? step : p.track_len - 1;
-            d = L.track[(size_t)row * nq + i] - q[i];
-            g = singular ? 0.0 : d * ginv_ii;
+            dq[i] = d;
         }
-        dq[i] = d;
-        gam[i] = g;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        // beta = G^-1 dQ = L^-T L^-1 dQ
-        const bool skip = singular || p.to_mode == LBM_TO_OBSERVE;
-        double yv[kMaxQoi];
-        for (int r = 0; r < nq; ++r) {
+        __syncwarp();
+        // beta = X^T D^-1 X dQ: lane r forms (X dQ)_r / D_r, then lane c sums column c
+        const bool skip = sing || p.to_mode == LBM_TO_OBSERVE;
+        if (i < nq) {
             double a = 0.0;
             if (!skip)
-                for (int m = 0; m <= r; ++m) a += Li[r][m] * dq[m];
-            yv[r] = a;
+                for (int m = 0; m <= i; ++m) a = fma(X[i][m], dq[m], a);
+            yv[i] = skip ? 0.0 : a * invD[i];
         }
-        for (int c = 0; c < nq; ++c) {
+        __syncwarp();
+        if (i < nq) {
             double a = 0.0;
             if (!skip)
-                for (int r = c; r < nq; ++r) a += Li[r][c] * yv[r];
-            beta[c] = a;
-            L.beta[c] = a;
-        }
-        // QoI block row
-        const long long rc = L.st->ring_count;
-        double* row = L.ring + (size_t)(rc % p.ring_cap) * p.row_len;
-        row[0] = (double)step;
-        for (int i = 0; i < nq; ++i) {
+                for (int r = i; r < nq; ++r) a = fma(X[r][i], yv[r], a);
+            beta[i] = a;
+            L.beta[i] = a;
+            // QoI block row
+            const long long rc = L.st->ring_count;
+            double* row = L.ring + (size_t)(rc % p.ring_cap) * p.row_len;
+            if (i == 0) row[0] = (double)step;
             row[1 + i] = q[i];
-            row[1 + nq + i] = dq[i];
-            row[1 + 2 * nq + i] = gam[i];
-        }
-        unsigned fl = singular ? LBM_FLAG_SINGULAR : 0u;
-        if (L.st->status & 1u) fl |= LBM_FLAG_UNSTABLE;
-        row[1 + 3 * nq] = (double)fl;
-        L.st->ring_count = rc + 1;
-        if (p.to_mode == LBM_TO_LRS && p.h > 0) {
-            const long long slot = L.st->hist_pos % p.h;
-            for (int i = 0; i < nq; ++i) {
-                L.qh[slot * nq + i] = tmp[i];
+            row[1 + nq + i] = d;
+            row[1 + 2 * nq + i] = g;
+            if (i == 0) {
+                unsigned fl = sing ? LBM_FLAG_SINGULAR : 0u;
+                if (L.st->status & 1u) fl |= LBM_FLAG_UNSTABLE;
+                row[1 + 3 * nq] = (double)fl;
+            }
+            if (lrs && p.h > 0) {
+                const long long slot = L.st->hist_pos % p.h;
+                L.qh[slot * nq + i] = qnew[i];
                 L.qsh[slot * nq + i] = q[i];
             }
-            L.st->hist_pos += 1;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            L.st->ring_count += 1;
+            if (lrs && p.h > 0) L.st->hist_pos += 1;
         }
     }
     __syncthreads();
-    // 7. mean profile of the corrected velocity: P_v + sum_k beta_k P_k + nx nz sum_j beta_mp_j w_j
+    // 6. mean profile of the corrected velocity: P_v + sum_k beta_k P_k + nx nz sum_j beta_mp_j w_j
     const double area = (double)p.nx * (double)p.nz;
     for (int y = tid; y < p.ny; y += blockDim.x) {
         double a = L.plane_sum[(size_t)y * np1];
-        for (int k = 0; k < ns; ++k) a += beta[k] * L.plane_sum[(size_t)y * np1 + 1 + k];
-        for (int j = 0; j < nmp; ++j) a += area * beta[ns + j] * L.w_mp[(size_t)j * p.ny + y];
+        for (int k = 0; k < ns; ++k) a = fma(beta[k], L.plane_sum[(size_t)y * np1 + 1 + k], a);
+        for (int j = 0; j < nmp; ++j) a = fma(area * beta[ns + j], L.w_mp[(size_t)j * p.ny + y], a);
         L.profile[y] += a / area;
     }
     if (tid == 0) {
@@ -518,8 +532,9 @@ cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* 
     }
     return cudaGetLastError();
 }
-cudaError_t launch_lrs_hist(const Params& p, const Layout& L, cudaStream_t s) {
-    lrs_hist_kernel<<<p.nblk_lrs, 256, 0, s>>>(p, L);
+cudaError_t launch_lrs_pre(const Params& p, const Layout& L, cudaStream_t s) {
+    const int nb = p.to_mode == LBM_TO_LRS ? p.nblk_lrs : 0;
+    lrs_pre_kernel<<<nb + 1, 256, 0, s>>>(p, L, nb);
     return cudaGetLastError();
 }
 cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s) {

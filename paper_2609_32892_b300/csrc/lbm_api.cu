@@ -34,6 +34,8 @@ struct lbm_ctx {
     Layout L;
     cudaStream_t stream;       // caller's stream
     cudaStream_t cap_stream;   // private stream used only to capture the step graph
+    cudaStream_t side;         // branch of the step that runs beside the field kernels
+    cudaEvent_t ev_fork, ev_join;
     std::vector<Filter> filters;
     std::vector<Taps> taps1d;  // scratch for building passes
     int cur;                   // which population buffer holds the current state
@@ -54,6 +56,7 @@ struct lbm_ctx {
     long long prof_n[LBM_K_COUNT];
     int lrs_set;
     int autotune;     // tune launch shapes before the first step (default on)
+    int branch;       // LRS history / normals on a parallel branch of the step (default on)
     int tuned;
     cufftHandle fft_r2c, fft_c2r;  // Fourier-band filters (3 components batched)
     bool has_fft;
@@ -124,7 +127,7 @@ static int validate(const lbm_config* c) {
             if (s.filter == LBM_FILTER_LAPLACE && 5 * s.scale > kMaxTaps)
                 return fail(nullptr, LBM_ERR_ARG, "Laplacian scale too large");
         }
-        if (c->to_mode == LBM_TO_LRS && c->h < 1) return fail(nullptr, LBM_ERR_ARG, "LRS needs h >= 1");
+        if (c->to_mode == LBM_TO_LRS && (c->h < 1 || c->h > (1 << 20))) return fail(nullptr, LBM_ERR_ARG, "LRS needs 1 <= h <= 2^20");
         if (c->to_mode == LBM_TO_TRACK && c->track_len < 1) return fail(nullptr, LBM_ERR_ARG, "tracking needs track_len >= 1");
         if (c->spinup < 0) return fail(nullptr, LBM_ERR_ARG, "spinup must be >= 0");
         if (c->spinup > 0 && c->to_mode != LBM_TO_LRS) return fail(nullptr, LBM_ERR_ARG, "spinup applies to LBM_TO_LRS");
@@ -218,8 +221,12 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     p->tune.apply4 = 1;
     if (p->h > 0) {
         const long long rows = (long long)(2 * p->h + 1) * p->n_q + 1;
-        p->lrs_rows_per_blk = 1024;
-        p->nblk_lrs = (int)((rows + 1023) / 1024);
+        // about 64 blocks (the solve sums their partials two per lane)
+        long long rpb = (rows + 63) / 64;
+        if (rpb < 256) rpb = 256;
+        if (rpb > kLrsRowsPerBlk) rpb = kLrsRowsPerBlk;
+        p->lrs_rows_per_blk = (int)rpb;
+        p->nblk_lrs = (int)((rows + rpb - 1) / rpb);
     }
 }
 
@@ -266,8 +273,9 @@ static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filt
             l.rr[f] = cv.take<float>(p.ncomp * N);
             l.vz[f] = filt[f].need_z ? cv.take<float>(p.dim * N) : nullptr;
         }
-        l.part = cv.take<double>((size_t)p.nblk_red * (p.npart > 0 ? p.npart : 1));
-        l.plane_part = cv.take<double>((size_t)p.nzc * p.ny * (1 + p.n_s));
+        l.part = cv.take<float>((size_t)p.nblk_red * (p.npart > 0 ? p.npart : 1));
+        l.plane_part = cv.take<float>((size_t)p.nzc * p.ny * (1 + p.n_s));
+        l.znorm = cv.take<double>(kMaxQoi);
         l.plane_sum = cv.take<double>((size_t)p.ny * (1 + p.n_s));
         if (p.h > 0) {
             const size_t rows = (size_t)(2 * p.h + 1) * p.n_q + 1;
@@ -358,8 +366,11 @@ struct Launcher {
             cudaEventRecord(c->ev[2 * c->ev_used], s);
         }
     }
-    void after(cudaError_t e) {
+    void check(cudaError_t e) {
         if (e != cudaSuccess && err == cudaSuccess) err = e;
+    }
+    void after(cudaError_t e) {
+        check(e);
         if (timed && c->ev_used < 96) {
             cudaEventRecord(c->ev[2 * c->ev_used + 1], s);
             ++c->ev_used;
@@ -461,10 +472,21 @@ static void enqueue_step(Launcher& lc, int src) {
     lbm_ctx* c = lc.c;
     const Params& p = c->p;
     const Layout& L = c->L;
+    // LRS history matvec and the step's normals: inputs from the previous
+    // step only, so they run on a branch beside the field kernels and join
+    // before the solve (in line when the kernels are timed one by one)
+    const bool pre = p.to_mode == LBM_TO_LRS || p.to_mode == LBM_TO_GAMMA;
+    const bool fork = pre && c->branch && !lc.timed && !lc.count_only;
+    if (fork) {
+        lc.check(cudaEventRecord(c->ev_fork, lc.s));
+        lc.check(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, c->side));
+        lc.check(cudaEventRecord(c->ev_join, c->side));
+    }
     if (p.substrate == LBM_SUBSTRATE_WALE) LAUNCH(lc, LBM_K_MOMENTS, launch_moments(p, L, src, lc.s));
     LAUNCH(lc, LBM_K_COLLIDE, launch_collide(p, L, src, lc.s));
     if (p.to_mode == LBM_TO_OFF) return;
-    if (p.to_mode == LBM_TO_LRS) LAUNCH(lc, LBM_K_LRS, launch_lrs_hist(p, L, lc.s));
+    if (pre && !fork) LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, lc.s));
     LAUNCH(lc, LBM_K_CURL, launch_to_curl(p, L, lc.s));
     if (c->has_fft) {
         // one forward transform of (v_x, v_y, omega) serves every Fourier band
@@ -489,6 +511,7 @@ static void enqueue_step(Launcher& lc, int src) {
         vk[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
     }
     LAUNCH(lc, LBM_K_REDUCE, launch_reduce(p, L, vk, lc.s));
+    if (fork) lc.check(cudaStreamWaitEvent(lc.s, c->ev_join, 0));
     LAUNCH(lc, LBM_K_SOLVE, launch_solve(p, L, lc.s));
     if (p.to_mode != LBM_TO_OBSERVE) LAUNCH(lc, LBM_K_APPLY, launch_apply(p, L, 1 - src, lc.s));
 }
@@ -783,6 +806,7 @@ int lbm_create(const lbm_config* cfg, void* dev_buf, size_t bytes, void* cuda_st
     c->stream = (cudaStream_t)cuda_stream;
     c->elem = cfg->storage == LBM_STORAGE_FP32 ? 4 : 2;
     c->use_graphs = 1;
+    c->branch = 1;
     c->autotune = 1;
     c->has_fft = c->L.spec != nullptr;
     if (c->has_fft) {
@@ -807,6 +831,13 @@ int lbm_create(const lbm_config* cfg, void* dev_buf, size_t bytes, void* cuda_st
     if (e != cudaSuccess) {
         delete c;
         return fail(nullptr, LBM_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ERR_CUDA, "stream/event create: %s", cudaGetErrorString(e));
     }
     for (int i = 0; i < 2 * 96; ++i) cudaEventCreate(&c->ev[i]);
     // zero everything (rest state: shifted populations g = 0), then tables
@@ -847,6 +878,12 @@ int lbm_destroy(lbm_ctx* c) {
     for (int i = 0; i < 2 * 96; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->has_fft) {
         cufftDestroy(c->fft_r2c);
         cufftDestroy(c->fft_c2r);
@@ -1204,6 +1241,13 @@ int lbm_get_tuning(lbm_ctx* c, int32_t* values, int count) {
     int32_t v[12] = {c->tuned, c->p.tune.collide_pair, c->p.tune.apply4, c->p.tune.march_lines};
     for (int f = 0; f < 8; ++f) v[4 + f] = c->p.tune.filter_per_sm[f];
     for (int k = 0; k < count && k < 12; ++k) values[k] = v[k];
+    return LBM_OK;
+}
+
+int lbm_set_branching(lbm_ctx* c, int enable) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    if (c->graph) return fail(c, LBM_ERR_STATE, "lbm_set_branching must precede the first lbm_step");
+    c->branch = enable ? 1 : 0;
     return LBM_OK;
 }
 

@@ -146,6 +146,8 @@ int lbm_batch_admit(lbm_batch* b, const lbm_config* cfg, const double* u0, int64
         return berr(LBM_ERR_CUDA, "lbm_batch_admit: %s", cudaGetErrorString(e));
     }
     rc = lbm_create(cfg, b->pool + off, need, mm.stream, &mm.ctx);
+    // members overlap one another; a per-member branch only adds queue traffic
+    if (rc == LBM_OK) rc = lbm_set_branching(mm.ctx, 0);
     if (rc == LBM_OK) rc = lbm_init_macros(mm.ctx, nullptr, u0);
     if (rc != LBM_OK) {
         if (mm.ctx) lbm_destroy(mm.ctx);

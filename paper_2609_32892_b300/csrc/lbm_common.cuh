@@ -11,6 +11,7 @@
 namespace lbm {
 
 constexpr int kMaxQoi = LBM_MAX_QOI;
+constexpr int kLrsRowsPerBlk = 1024;  // most rows of C one history-matvec block takes
 constexpr int kMaxTaps = 64;     // longest 1-D filter pass (L_s arm: 5 s taps)
 constexpr int kMaxFilters = 8;   // distinct (filter, scale) pairs per run
 
@@ -43,11 +44,12 @@ struct Layout {
     float* acc;          // [6][N]  R applied once
     float* rr[kMaxFilters];  // [6][N] R R (v, omega) per filter
     float* vz[kMaxFilters];  // [3][N] curl*(R R omega) per filter
-    double* part;        // [nblk_red][npart] reduction partials
-    double* plane_part;  // [nzc][ny][1 + n_s] plane-sum partials
+    float* part;         // [nblk_red][npart] reduction partials (FP32 block sums)
+    float* plane_part;   // [nzc][ny][1 + n_s] plane-sum partials
     double* plane_sum;   // [ny][1 + n_s] plane sums of v_x and V_k,x
     double* red_out;     // [npart] reduced partials (diagnostics)
     double* lrs_part;    // [nblk_lrs][N_Q] LRS history matvec partials
+    double* znorm;       // [N_Q] normals of the current step (LRS noise / gamma draws)
     double* lrs_C;       // [(2h+1)N + 1][N]
     double* lrs_mu;      // [N]
     double* lrs_L;       // [N][N] Cholesky factor of Sigma
@@ -116,7 +118,8 @@ cudaError_t launch_band_mask(const Params& p, const float2* in, float2* out, int
                              cudaStream_t s);
 cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s);
 cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* vk, cudaStream_t s);
-cudaError_t launch_lrs_hist(const Params& p, const Layout& L, cudaStream_t s);
+// LRS history partials and the step's normals (LRS and gamma modes)
+cudaError_t launch_lrs_pre(const Params& p, const Layout& L, cudaStream_t s);
 cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s);
 cudaError_t launch_macros(const Params& p, const Layout& L, int which, float* drho_out, float* u_out,
                           cudaStream_t s);

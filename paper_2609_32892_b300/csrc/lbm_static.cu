@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "lbm_common.cuh"
+#include "dfloat.cuh"
 
 using namespace lbm;
 
@@ -42,12 +43,10 @@ __global__ void masked_copy_kernel(Params p, const float* __restrict__ u, float*
 
 // q_k = (1/2) sum over blocks of <v, V_k> (self-adjointness: E_R = <v, RRv>/2,
 // Z_R = <v, curl*(RR omega)>/2), one warp per QoI in a fixed order
-__global__ void finish_kernel(Params p, const double* __restrict__ part, double* __restrict__ q) {
+__global__ void finish_kernel(Params p, const float* __restrict__ part, double* __restrict__ q) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = wid; k < p.n_s; k += blockDim.x >> 5) {
-        double a = 0.0;
-        for (int b = lane; b < p.nblk_red; b += 32) a += part[(size_t)b * p.npart + k];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        const double a = df_warp_sum(part + k, p.nblk_red, (size_t)p.npart, lane);
         if (lane == 0) q[k] = 0.5 * a;
     }
 }
@@ -197,9 +196,9 @@ extern "C" int lbm_qoi_eval_static(const lbm_config* cfg, const float* u, double
         if (filt[f].need_z) need += align256(sizeof(float) * p.dim * N);
     }
     const size_t off_part = need;
-    need += align256(sizeof(double) * (size_t)p.nblk_red * p.npart);
+    need += align256(sizeof(float) * (size_t)p.nblk_red * p.npart);
     const size_t off_plane = need;
-    need += align256(sizeof(double) * (size_t)p.nzc * p.ny * (1 + p.n_s));
+    need += align256(sizeof(float) * (size_t)p.nzc * p.ny * (1 + p.n_s));
     if (need > LBM_STATIC_SCRATCH_BYTES)
         return err(LBM_ERR_BUDGET, "lbm_qoi_eval_static: needs %zu scratch bytes, the static array holds %u", need,
                    (unsigned)LBM_STATIC_SCRATCH_BYTES);
@@ -233,8 +232,8 @@ extern "C" int lbm_qoi_eval_static(const lbm_config* cfg, const float* u, double
         L.rr[f] = (float*)(base + off_rr[f]);
         L.vz[f] = filt[f].need_z ? (float*)(base + off_vz[f]) : nullptr;
     }
-    L.part = (double*)(base + off_part);
-    L.plane_part = (double*)(base + off_plane);
+    L.part = (float*)(base + off_part);
+    L.plane_part = (float*)(base + off_plane);
 
     // every scratch region below is fully written before it is read:
     // the velocity copy zeroes solid rows, curl/passes/sens write every node,

@@ -13,12 +13,20 @@ Scheduling and marshalling only: every step runs in liblbm.so.
 
 import collections
 import math
+import os
 import time
 
 import numpy as np
 
 import synthetic
 from . import binding as B
+
+# Each member steps on its own stream.  With the default 8 hardware work
+# queues, dozens of member streams alias onto shared queues and serialise one
+# another; 32 lets them run side by side (several times the member-steps/s for
+# small members).  The variable is read when the CUDA context is created, so
+# it takes effect when this module is imported before the first CUDA call.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 
 def steps_per_tu(wl):

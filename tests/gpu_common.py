@@ -32,7 +32,7 @@ def run_oracle(wl, steps, lrs=None, track=None):
     return sim, rows, rho, u
 
 
-def run_gpu(wl, steps, lrs=None, graphs=True, track=None, chunks=None):
+def run_gpu(wl, steps, lrs=None, graphs=True, track=None, chunks=None, branching=True):
     from paper_2609_32892_b300 import LbmSim, binding as B
 
     g = LbmSim(wl)
@@ -42,6 +42,7 @@ def run_gpu(wl, steps, lrs=None, graphs=True, track=None, chunks=None):
     if track is not None:
         B.lbm_set_track_reference(g.ctx, track)
     B.lbm_set_graphs(g.ctx, graphs)
+    B.lbm_set_branching(g.ctx, branching)
     for n in (chunks or [steps]):
         g.step(n)
     g.sync()

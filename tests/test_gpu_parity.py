@@ -174,6 +174,22 @@ def test_graph_replay_equals_eager_launches():
     np.testing.assert_array_equal(rho_a, rho_b)
 
 
+@pytest.mark.parametrize("name,kw", [("C2", dict(nx=40, ny=34, h=3)), ("C3", dict(nx=36, ny=22, nz=13, h=2)),
+                                     ("C1", dict(nx=40, ny=36))])
+def test_branched_step_equals_in_line_step(name, kw):
+    """The LRS history product and the normals on a parallel branch of the
+    step (graph and eager) give bit-identical results to running them in line."""
+    wl = synthetic.workload(name, **kw)
+    lrs = lrs_inputs(wl, np.zeros(nq_of(wl))) if wl["to_mode"] == "lrs" else None
+    _, ra, rho_a, u_a = run_gpu(wl, 9, lrs=lrs, graphs=True, chunks=[4, 5], branching=True)
+    _, rb, rho_b, u_b = run_gpu(wl, 9, lrs=lrs, graphs=True, chunks=[4, 5], branching=False)
+    _, rc, rho_c, u_c = run_gpu(wl, 9, lrs=lrs, graphs=False, branching=True)
+    for r, rho, u in ((rb, rho_b, u_b), (rc, rho_c, u_c)):
+        np.testing.assert_array_equal(ra, r)
+        np.testing.assert_array_equal(u_a, u)
+        np.testing.assert_array_equal(rho_a, rho)
+
+
 def test_lrs_reference_scales_from_first_step():
     """sigma_ref <= 0 is taken from the first predictor QoIs, on both sides."""
     wl = synthetic.workload("C2", nx=36, ny=30, h=2)

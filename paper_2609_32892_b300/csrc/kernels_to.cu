@@ -159,18 +159,20 @@ __global__ void __launch_bounds__(256) sens_curl_kernel(Params p, const float* _
 
 // ------------------------------------------------------ block reduction --
 // Per block (one y row, a chunk of z planes): <v*, V_k> and <V_i, V_j> (i <= j)
-// over its fluid nodes, and the row sums of v*_x and V_k,x (the mean-profile
-// couplings).  FP32 throughout the block (per thread over a few nodes, then a
-// warp tree); the partials are summed with compensation in the solve.  No
-// double-precision arithmetic here: on this GPU an FP64 warp tree over the
-// NV values of every block costs more than the whole field traversal.
+// over its fluid nodes, the row sums P_k of v*_x and V_k,x, and the
+// mean-profile couplings w_j(y) P_k.  FP32 throughout the block (per thread
+// over a few nodes, then a warp tree); the totals kernel sums the partials
+// with compensation.  No double-precision arithmetic here: on this GPU an
+// FP64 warp tree over the values of every block costs more than the whole
+// field traversal.
 struct RedPtrs {
     const float* v[kMaxQoi];
 };
 
 template <int NS>
 __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __restrict__ vps, RedPtrs vk,
-                                                     float* __restrict__ part, float* __restrict__ plane_part) {
+                                                     const float2* __restrict__ w_mp2, float* __restrict__ part,
+                                                     float* __restrict__ plane_part) {
     constexpr int NG = NS * (NS + 1) / 2;
     constexpr int NV = NS + NG + 1 + NS;  // <v,V_k>, Gram, row sums (v_x, V_k,x)
     const int y = blockIdx.x;
@@ -209,6 +211,7 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
         for (int k = 0; k < NS; ++k) acc[idx++] += w[k][0];
     }
     __shared__ float sh[4][NV];
+    __shared__ float tot[NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -219,11 +222,114 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
     }
     __syncthreads();
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t row = (size_t)blk * p.npart_all;
     for (int v = threadIdx.x; v < NV; v += blockDim.x) {
         const float s = (sh[0][v] + sh[1][v]) + (sh[2][v] + sh[3][v]);
-        if (v < NS + NG) part[(size_t)blk * (NS + NG) + v] = s;
+        tot[v] = s;
+        if (v < NS + NG) part[row + v] = s;
         else plane_part[((size_t)zc * p.ny + y) * (1 + NS) + (v - NS - NG)] = s;
     }
+    __syncthreads();
+    // couplings w_j(y) P_k of this block's row sums, j < n_mp, k = 0..NS, as
+    // unevaluated float pairs: with w = w_hi + w_lo (the FP64 weight split in
+    // two floats) the products are exact up to w_lo P_k's rounding, so the
+    // couplings keep FP64 accuracy (the mean-profile QoIs are large and the
+    // LRS corrects them by small differences)
+    for (int t = threadIdx.x; t < p.n_mp * (1 + NS); t += blockDim.x) {
+        const int j = t / (1 + NS), k = t - j * (1 + NS);
+        const float2 w = w_mp2[(size_t)j * p.ny + y];
+        const float r = tot[NS + NG + k];
+        const float hi = w.x * r;
+        const float lo = fmaf(w.y, r, fmaf(w.x, r, -hi));
+        part[row + NS + NG + 2 * t] = hi;
+        part[row + NS + NG + 2 * t + 1] = lo;
+    }
+}
+
+// ------------------------------------------------------------ totals --
+// Sums the reduction partials across blocks, one block per value (the solve
+// is a single block: reading every partial there would serialise a few
+// hundred KB of L2 reads on one SM).  Compensated FP32 (TwoSum) per thread and
+// across the block, widened to double once.  Further blocks: the plane sums
+// P_k(y) over the z chunks (one warp per (y, k)) and, in LRS mode, the known
+// part of the LRS prediction (history partials + mu + L z, Eq. LRS).
+__device__ __forceinline__ DF df_block_sum(DF a, DF* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_down(a, o));
+    if (lane == 0) sh[wid] = a;
+    __syncthreads();
+    DF t = {0.f, 0.f};
+    if (wid == 0) {
+        if (lane < (int)(blockDim.x >> 5)) t = sh[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = df_add(t, df_shfl_down(t, o));
+    }
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) totals_kernel(Params p, Layout L, int nplane_blk) {
+    __shared__ DF sh[8];
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (b < p.npart) {
+        DF a = {0.f, 0.f};
+        int i = threadIdx.x;
+        // four loads in flight per thread
+        for (; i + 3 * 256 < p.nblk_red; i += 4 * 256) {
+            const float x0 = L.part[(size_t)i * p.npart_all + b];
+            const float x1 = L.part[(size_t)(i + 256) * p.npart_all + b];
+            const float x2 = L.part[(size_t)(i + 512) * p.npart_all + b];
+            const float x3 = L.part[(size_t)(i + 768) * p.npart_all + b];
+            a = df_add(df_add(a, x0), df_add(df_two_sum(x1, x2), x3));
+        }
+        for (; i < p.nblk_red; i += 256) a = df_add(a, L.part[(size_t)i * p.npart_all + b]);
+        const DF t = df_block_sum(a, sh);
+        if (threadIdx.x == 0) L.tot[b] = (double)t.hi + (double)t.lo;
+        return;
+    }
+    if (b < p.ntot) {
+        // a coupling: float pairs (hi, lo) per block
+        const size_t off = (size_t)p.npart + 2 * (size_t)(b - p.npart);
+        DF a = {0.f, 0.f};
+        int i = threadIdx.x;
+        // (hi, lo) need not be 8-byte aligned: two scalar loads each
+        for (; i + 256 < p.nblk_red; i += 2 * 256) {
+            const float* r0 = L.part + (size_t)i * p.npart_all + off;
+            const float* r1 = L.part + (size_t)(i + 256) * p.npart_all + off;
+            const DF x0 = {r0[0], r0[1]}, x1 = {r1[0], r1[1]};
+            a = df_add(df_add(a, x0), x1);
+        }
+        for (; i < p.nblk_red; i += 256) {
+            const float* r0 = L.part + (size_t)i * p.npart_all + off;
+            a = df_add(a, DF{r0[0], r0[1]});
+        }
+        const DF t = df_block_sum(a, sh);
+        if (threadIdx.x == 0) L.tot[b] = (double)t.hi + (double)t.lo;
+        return;
+    }
+    const int np1 = 1 + p.n_s;
+    if (b < p.ntot + nplane_blk) {
+        const int e = (b - p.ntot) * 8 + wid;
+        if (e >= p.ny * np1) return;
+        DF a = {0.f, 0.f};
+        for (int zc = lane; zc < p.nzc; zc += 32) a = df_add(a, L.plane_part[(size_t)zc * p.ny * np1 + e]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_down(a, o));
+        if (lane == 0) L.plane_sum[e] = (double)a.hi + (double)a.lo;
+        return;
+    }
+    // LRS: hsum_k = sum of the history partials + mu_k + (L z)_k, one block
+    // (one warp: FP64 instructions are slow, spread them over SMs) per k
+    const int nq = p.n_q;
+    const int k = b - p.ntot - nplane_blk;
+    if (wid != 0 || k >= nq) return;
+    double a = lane < nq ? L.lrs_L[(size_t)k * nq + lane] * L.znorm[lane] : 0.0;
+    if (lane == 0) a += L.lrs_mu[k];
+    for (int bb = lane; bb < p.nblk_lrs; bb += 32) a += L.lrs_part[(size_t)bb * nq + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) L.hsum[k] = a;
 }
 
 // ------------------------------------------- LRS history matvec, normals --
@@ -284,208 +390,279 @@ __global__ void __launch_bounds__(256) lrs_pre_kernel(Params p, Layout L, int nb
 }
 
 // ------------------------------------------------------------- solve --
-// One block: sum the partials, assemble q^{n*} and the Gram matrix, evaluate
-// the coefficient source, factor G = X^-1 D X^-T (LDL^T, FP64), and produce
-// beta = G^-1 dQ (dv_SGS = sum_k beta_k V_k equals sum_i gamma_i O_i with c_ij
-// and gamma_i of Sec. 4.2-4.3), gamma_i = dQ_i (G^-1)_ii.  Then write the QoI
-// block row, push the LRS histories, add the mean profile and advance the step
-// counter.
+// One block: assemble q^{n*} and the Gram matrix G from the totals, evaluate
+// the coefficient source, invert G and form beta = G^-1 dQ (dv_SGS = sum_k
+// beta_k V_k equals sum_i gamma_i O_i with c_ij and gamma_i of Sec. 4.2-4.3)
+// and gamma_i = dQ_i (G^-1)_ii.  Then write the QoI block row, push the LRS
+// histories, add the mean profile and advance the step counter.
 //
-// Double-precision operations issue slowly on this GPU and this kernel is on
-// the critical path of every step, so its FP64 work is arranged as short
-// parallel chains: sums of FP32 partials are compensated single-precision
-// sums widened once, the factorisation is right-looking with one reciprocal
-// per pivot, and the triangular products run one row/column per lane.
-__global__ void __launch_bounds__(256) solve_kernel(Params p, Layout L) {
+// Cost model (measured on this GPU): a double-precision warp instruction
+// occupies the FP64 unit of its SM sub-partition for about 64 cycles and is
+// not pipelined, whatever the number of active lanes; four sub-partitions per
+// SM; a division costs about ten such instructions.  This kernel is on the
+// critical path of every step, so it counts FP64 warp instructions per
+// sub-partition rather than flops:
+//  * G is equilibrated by exact powers of two, G~ = S G S, S = diag(s_i) with
+//    s_i^2 G_ii in [1, 4) (integer operations on the exponent field);
+//  * G~ is inverted by Gauss-Jordan elimination on [G~ | I] without pivoting
+//    (G is symmetric positive definite when not singular) in fraction-free
+//    form: row i <- a'_k R_i - (a_ik 2^-e_k) R_k with a_kk = a'_k 2^e_k,
+//    a'_k in [1, 2): two FP64 instructions per element and step, no
+//    division, one element per thread on the active columns only.  The left
+//    block ends diagonal, d_i, and G~^-1 = diag(d)^-1 B;
+//  * Sec. 4.3's singular test (Cholesky pivot D_k > 1e-14 max_i G_ii) is
+//    taken after the elimination on the same pivots: the fraction-free pivot
+//    is a_kk = m_k s_k^2 D_k, m_k = a'_0 ... a'_(k-1) the factor of row k;
+//  * dot products over the QoIs run on groups of 8 lanes (3 warps for 12
+//    QoIs), and the two divisions on different warps.
+__device__ __forceinline__ int exp2_of(double a) {  // floor(log2 |a|) for a normal a
+    return (int)((__double_as_longlong(a) >> 52) & 0x7ff) - 1023;
+}
+__device__ __forceinline__ double pow2(int e) {  // 2^e, -1022 <= e <= 1023
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+// x 2^e on the exponent field (integer operations only): exact for normal x
+// and a normal result; zero and subnormal x give a signed zero, a result
+// outside the normal range a signed zero or infinity
+__device__ __forceinline__ double scale2(double x, int e) {
+    const long long b = __double_as_longlong(x);
+    const long long sign = b & (long long)0x8000000000000000ULL;
+    const int ex = (int)((b >> 52) & 0x7ff);
+    const int en = ex + e;
+    if (ex == 0 || en <= 0) return __longlong_as_double(sign);
+    if (en >= 2047 || ex == 2047) return __longlong_as_double(sign | 0x7ff0000000000000LL);
+    return __longlong_as_double(b + ((long long)e << 52));
+}
+// the mantissa of a as a value in [1, 2) (a normal)
+__device__ __forceinline__ double mant(double a) {
+    return __longlong_as_double((__double_as_longlong(a) & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+}
+// sum over groups of 8 consecutive lanes (every lane gets its group's sum)
+__device__ __forceinline__ double group8_sum(double a) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+// G_ij from the totals (scale block, couplings) and the fixed band block
+__device__ __forceinline__ double gram_entry(const Params& p, const Layout& L, int i, int j) {
+    const int ns = p.n_s, np1 = 1 + ns, cpl = ns + ns * (ns + 1) / 2;
+    if (i < ns && j < ns) {
+        const int a = min(i, j), b = max(i, j);
+        return L.tot[ns + a * ns - a * (a - 1) / 2 + (b - a)];
+    }
+    if (i >= ns && j >= ns) return L.g_mpmp[(size_t)(i - ns) * p.n_mp + (j - ns)];
+    if (i >= ns) return L.tot[cpl + (i - ns) * np1 + 1 + j];
+    return L.tot[cpl + (j - ns) * np1 + 1 + i];
+}
+// half the binary exponent of a diagonal entry (its scale is 2^-half)
+__device__ __forceinline__ int half_exp(double gii) {
+    const int e = gii > 1e-300 && gii < 1e300 ? exp2_of(gii) : 0;
+    return e >> 1;  // floor(e / 2)
+}
+
+constexpr int kSolveThreads = 320;  // >= 16 x 17 + 15 active elements, plus a spare warp
+
+__global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L) {
+    constexpr int MQ = kMaxQoi;
+    constexpr int MW = 2 * MQ + 1;
     const int ns = p.n_s, nmp = p.n_mp, nq = p.n_q;
-    const int ng = ns * (ns + 1) / 2;
-    const int npart = ns + ng;
-    __shared__ double red[kMaxQoi + kMaxQoi * (kMaxQoi + 1) / 2];
-    __shared__ double A[kMaxQoi][kMaxQoi + 1];   // G, overwritten by the factorisation
-    __shared__ double Lc[kMaxQoi][kMaxQoi + 1];  // unit lower factor
-    __shared__ double X[kMaxQoi][kMaxQoi + 1];   // its inverse
-    __shared__ double invD[kMaxQoi];
-    __shared__ double q[kMaxQoi], dq[kMaxQoi], beta[kMaxQoi], z[kMaxQoi], hpart[kMaxQoi], qnew[kMaxQoi];
-    __shared__ double xq[kMaxQoi], yv[kMaxQoi];
-    __shared__ double wP[kMaxQoi][kMaxQoi + 1];  // sum_y w_j(y) P_k(y), k = 0 (v_x), 1..ns (V_k,x)
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int np1 = 1 + ns;
+    const int cpl = ns + ns * (ns + 1) / 2;  // offset of the couplings in the totals
+    __shared__ double M[2][MQ][MW];  // [G~ | I], ping-pong
+    __shared__ double q[MQ], xq[MQ], dq[MQ], gam[MQ], ginv[MQ], wv[MQ], beta[MQ], qnew[MQ], rs[MQ];
+    __shared__ double piv[MQ], mkv[MQ + 1];
+    __shared__ long long diagbits[MQ];
+    __shared__ int hexp[MQ];
+    __shared__ int singular;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int gi = tid >> 3, gl = tid & 7;  // group of 8 lanes gi (output), lane gl
     const long long step = L.st->step;
     const bool lrs = p.to_mode == LBM_TO_LRS;
+    const bool lrs_pred = lrs && step >= p.spinup;
+    // loads needed late, issued now: the q^{n*} block of C (terms j = gl, gl + 8)
+    double c_q0 = 0.0, c_q1 = 0.0;
+    if (lrs_pred && gi < nq) {
+        const size_t base = (size_t)p.h * nq;
+        if (gl < nq) c_q0 = L.lrs_C[(base + gl) * nq + gi];
+        if (gl + 8 < nq) c_q1 = L.lrs_C[(base + gl + 8) * nq + gi];
+    }
 
-    // 1. totals of the block partials (one warp per value) and the LRS
-    //    history partials; plane sums P_k(y) over the z chunks (one per thread)
-    for (int v = wid; v < npart; v += nw) {
-        const double a = df_warp_sum(L.part + v, p.nblk_red, (size_t)npart, lane);
-        if (lane == 0) red[v] = a;
-    }
-    if (lrs)
-        for (int k = wid; k < nq; k += nw) {
-            double a = 0.0;
-            for (int b = lane; b < p.nblk_lrs; b += 32) a += L.lrs_part[(size_t)b * nq + k];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) hpart[k] = a;
+    // 1. q^{n*} and G~ = S G S (one element per thread)
+    for (int e = tid; e < nq * nq; e += blockDim.x) {
+        const int i = e / nq, j = e - i * nq;
+        const double gij = gram_entry(p, L, i, j);
+        const double gii = i == j ? gij : gram_entry(p, L, i, i);
+        const double gjj = i == j ? gij : gram_entry(p, L, j, j);
+        M[0][i][j] = scale2(gij, -half_exp(gii) - half_exp(gjj));
+        if (i == j) {
+            diagbits[i] = __double_as_longlong(gij);
+            hexp[i] = half_exp(gij);
         }
-    const int np1 = 1 + ns;
-    for (int e = tid; e < p.ny * np1; e += blockDim.x) {
-        DF a = {0.f, 0.f};
-        for (int zc = 0; zc < p.nzc; ++zc) a = df_add(a, L.plane_part[((size_t)zc * p.ny) * np1 + e]);
-        L.plane_sum[e] = (double)a.hi + (double)a.lo;
+    }
+    if (tid == 0) mkv[0] = 1.0;
+    double sig = 0.0;
+    if (tid < nq) {
+        const int i = tid;
+        q[i] = i < ns ? scale2(L.tot[i], -1) : L.tot[cpl + (i - ns) * np1];
+        if (lrs) {
+            // a reference scale <= 0 is taken from this step's predictor QoI
+            sig = L.lrs_sigma[i];
+            if (!(sig > 0.0)) {
+                sig = fabs(q[i]) > 0.0 ? fabs(q[i]) : 1.0;
+                L.lrs_sigma[i] = sig;
+            }
+        }
     }
     __syncthreads();
-    // 2. mean-profile couplings sum_y w_j(y) P_k(y): one warp per (j, k), lanes over y
-    for (int e = wid; e < nmp * np1; e += nw) {
-        const int j = e / np1, k = e - j * np1;
-        double a = 0.0;
-        for (int y = lane; y < p.ny; y += 32) a = fma(L.w_mp[(size_t)j * p.ny + y], L.plane_sum[(size_t)y * np1 + k], a);
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) wP[j][k] = a;
+
+    // 2. fraction-free Gauss-Jordan on [G~ | I].  At step k only the active
+    //    part is touched: the left columns k.., the right columns ..k and the
+    //    left diagonal entries (i, i), i < k (their columns are eliminated,
+    //    so they are only scaled).  Right column k enters as e_k times the
+    //    factor m_k of row k.  The last warp carries m_k and the pivots.
+    int cur = 0;
+    for (int k = 0; k < nq; ++k) {
+        const double akk = M[cur][k][k];
+        const int ek = exp2_of(akk);
+        const double ap = mant(akk);  // akk 2^-ek, in [1, 2)
+        const int act = nq * (nq + 1);
+        if (tid < act + k) {
+            int i, j;
+            if (tid < act) {
+                i = tid / (nq + 1);
+                const int c = tid - i * (nq + 1);
+                j = c < nq - k ? k + c : nq + (c - (nq - k));
+            } else {
+                i = j = tid - act;
+            }
+            const bool fresh = j == nq + k;  // right column entering the active set
+            const double mk = mkv[k];
+            const double mij = fresh ? (i == k ? mk : 0.0) : M[cur][i][j];
+            double r = mij;
+            if (tid >= act) {
+                r = ap * mij;  // eliminated column: row k holds 0 there
+            } else if (i != k) {
+                const double mkj = fresh ? mk : M[cur][k][j];
+                r = fma(-scale2(M[cur][i][k], -ek), mkj, ap * mij);
+            }
+            M[cur ^ 1][i][j] = r;
+        }
+        if (tid == kSolveThreads - 32) {
+            piv[k] = akk;
+            mkv[k + 1] = mkv[k] * ap;
+        }
+        cur ^= 1;
+        __syncthreads();
     }
-    __syncthreads();
-    // 3. q^{n*}, G, the normals, reference scales (warp 0, lane i = QoI i)
+
+    // 3. the singular test on the pivots (warp 0); the two divisions
+    //    1 / d_i (warp 0) and q_i / sigma_i (warp 1) on different warps
     if (wid == 0) {
-        const int i = lane;
-        double gdiag = 0.0;
-        if (i < nq) {
-            q[i] = i < ns ? 0.5 * red[i] : wP[i - ns][0];
-            for (int j = 0; j < nq; ++j) {
-                double gij;
-                if (i < ns && j < ns) {
-                    const int a = min(i, j), b = max(i, j);
-                    gij = red[ns + a * ns - a * (a - 1) / 2 + (b - a)];
-                } else if (i >= ns && j >= ns) {
-                    gij = L.g_mpmp[(size_t)(i - ns) * nmp + (j - ns)];
-                } else if (i >= ns) {
-                    gij = wP[i - ns][1 + j];
-                } else {
-                    gij = wP[j - ns][1 + i];
-                }
-                A[i][j] = gij;
-                if (j == i) gdiag = gij;
-            }
-            z[i] = (lrs || p.to_mode == LBM_TO_GAMMA) ? L.znorm[i] : 0.0;
-            if (lrs) {
-                // a reference scale <= 0 is taken from this step's predictor QoI
-                double sg = L.lrs_sigma[i];
-                if (!(sg > 0.0)) {
-                    sg = fabs(q[i]) > 0.0 ? fabs(q[i]) : 1.0;
-                    L.lrs_sigma[i] = sg;
-                }
-                xq[i] = q[i] / sg;
-            }
+        long long dmb = 0;  // max_i G_ii on the bit patterns: non-negative doubles
+        for (int i = 0; i < nq; ++i) dmb = max(dmb, diagbits[i]);  // order as integers; NaN propagates
+        const double dmax = __longlong_as_double(dmb);
+        bool bad = false;
+        if (lane < nq) {
+            const double a = piv[lane];
+            bad = !(a > scale2(1e-14 * dmax, -2 * hexp[lane]) * mkv[lane]) || !(a < 1e300);
         }
-        // 4. LDL^T with the pivot test d_k > 1e-14 max_i G_ii (the Schur
-        //    complements are the Cholesky pivots of Sec. 4.3's singular test)
-        double dmax = gdiag;
-        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        int sing = !(dmax > 0.0);
-        __syncwarp();
-        for (int k = 0; k < nq && !sing; ++k) {
-            const double dk = A[k][k];
-            if (!(dk > 1e-14 * dmax)) { sing = 1; break; }
-            const double inv = 1.0 / dk;
-            if (i == k) { invD[k] = inv; Lc[k][k] = 1.0; }
-            if (i > k && i < nq) Lc[i][k] = A[i][k] * inv;
-            __syncwarp();
-            // trailing update A_ij -= L_ik A_jk (k < j <= i), lanes over i
-            if (i > k && i < nq) {
-                const double lik = Lc[i][k];
-                for (int j = k + 1; j <= i; ++j) A[i][j] = fma(-lik, A[j][k], A[i][j]);
-            }
-            __syncwarp();
+        const bool sing = __any_sync(0xffffffffu, bad) || !(dmax > 0.0) || isinf(dmax);
+        if (lane == 0) singular = sing;
+        if (lane < nq && !sing) {
+            const int i = lane;
+            const double invd = 1.0 / M[cur][i][i];
+            rs[i] = scale2(invd, -hexp[i]);
+            ginv[i] = scale2(M[cur][i][nq + i] * invd, -2 * hexp[i]);
         }
-        // X = Lc^-1 (unit lower): lane c owns column c, rows in order
-        if (!sing && i < nq) {
-            for (int r = 0; r < nq; ++r) {
-                double a = r == i ? 1.0 : 0.0;
-                if (r > i)
-                    for (int m = i; m < r; ++m) a = fma(-Lc[r][m], X[m][i], a);
-                X[r][i] = a;
-            }
-        }
-        __syncwarp();
-        // 5. coefficient source -> dQ, gamma; G^-1 = X^T D^-1 X
-        double d = 0.0, g = 0.0;
-        if (i < nq) {
-            double ginv_ii = 0.0;
-            if (!sing)
-                for (int r = i; r < nq; ++r) ginv_ii = fma(X[r][i] * X[r][i], invD[r], ginv_ii);
-            if (lrs && step < p.spinup) {
-                // spin-up: nudged to the reference, which enters the history
-                const long long row = step < p.track_len ? step : p.track_len - 1;
-                const double qref = L.track[(size_t)row * nq + i];
-                d = qref - q[i];
-                qnew[i] = qref;
-                g = sing ? 0.0 : d * ginv_ii;
-            } else if (lrs) {
-                double qh = hpart[i] + L.lrs_mu[i];
-                for (int j = 0; j < nq; ++j)
-                    qh += xq[j] * L.lrs_C[((size_t)p.h * nq + j) * nq + i] + L.lrs_L[(size_t)i * nq + j] * z[j];
-                const double qn = L.lrs_sigma[i] * qh;
-                d = qn - q[i];
-                qnew[i] = qn;  // corrected QoI for the history
-                g = sing ? 0.0 : d * ginv_ii;
-            } else if (p.to_mode == LBM_TO_GAMMA) {
-                if (!sing) {
-                    g = p.gamma_std * z[i];
-                    d = g / ginv_ii;
-                }
-            } else if (p.to_mode == LBM_TO_TRACK) {
-                const long long row = step < p.track_len ? step : p.track_len - 1;
-                d = L.track[(size_t)row * nq + i] - q[i];
-                g = sing ? 0.0 : d * ginv_ii;
-            }
-            dq[i] = d;
-        }
-        __syncwarp();
-        // beta = X^T D^-1 X dQ: lane r forms (X dQ)_r / D_r, then lane c sums column c
-        const bool skip = sing || p.to_mode == LBM_TO_OBSERVE;
-        if (i < nq) {
-            double a = 0.0;
-            if (!skip)
-                for (int m = 0; m <= i; ++m) a = fma(X[i][m], dq[m], a);
-            yv[i] = skip ? 0.0 : a * invD[i];
-        }
-        __syncwarp();
-        if (i < nq) {
-            double a = 0.0;
-            if (!skip)
-                for (int r = i; r < nq; ++r) a = fma(X[r][i], yv[r], a);
-            beta[i] = a;
-            L.beta[i] = a;
-            // QoI block row
-            const long long rc = L.st->ring_count;
-            double* row = L.ring + (size_t)(rc % p.ring_cap) * p.row_len;
-            if (i == 0) row[0] = (double)step;
-            row[1 + i] = q[i];
-            row[1 + nq + i] = d;
-            row[1 + 2 * nq + i] = g;
-            if (i == 0) {
-                unsigned fl = sing ? LBM_FLAG_SINGULAR : 0u;
-                if (L.st->status & 1u) fl |= LBM_FLAG_UNSTABLE;
-                row[1 + 3 * nq] = (double)fl;
-            }
-            if (lrs && p.h > 0) {
-                const long long slot = L.st->hist_pos % p.h;
-                L.qh[slot * nq + i] = qnew[i];
-                L.qsh[slot * nq + i] = q[i];
-            }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            L.st->ring_count += 1;
-            if (lrs && p.h > 0) L.st->hist_pos += 1;
-        }
+    } else if (wid == 1 && lrs_pred && lane < nq) {
+        xq[lane] = q[lane] / L.lrs_sigma[lane];
     }
     __syncthreads();
-    // 6. mean profile of the corrected velocity: P_v + sum_k beta_k P_k + nx nz sum_j beta_mp_j w_j
-    const double area = (double)p.nx * (double)p.nz;
-    for (int y = tid; y < p.ny; y += blockDim.x) {
-        double a = L.plane_sum[(size_t)y * np1];
-        for (int k = 0; k < ns; ++k) a = fma(beta[k], L.plane_sum[(size_t)y * np1 + 1 + k], a);
-        for (int j = 0; j < nmp; ++j) a = fma(area * beta[ns + j], L.w_mp[(size_t)j * p.ny + y], a);
-        L.profile[y] += a / area;
+    const bool sing = singular;
+    // 4. coefficient source -> dQ, gamma (group gi forms the LRS product of QoI gi)
+    if (lrs_pred) {
+        double t = 0.0;
+        if (gi < nq) t = xq[gl] * c_q0 + (gl + 8 < nq ? xq[gl + 8] * c_q1 : 0.0);
+        t = group8_sum(t);
+        if (gl == 0 && gi < nq) qnew[gi] = L.lrs_sigma[gi] * (L.hsum[gi] + t);  // corrected QoI for the history
     }
+    __syncthreads();
+    if (tid < nq) {
+        const int i = tid;
+        const double gii = sing ? 0.0 : ginv[i];
+        double d = 0.0, g = 0.0;
+        if (lrs && step < p.spinup) {
+            // spin-up: nudged to the reference, which enters the history
+            const long long row = step < p.track_len ? step : p.track_len - 1;
+            const double qref = L.track[(size_t)row * nq + i];
+            d = qref - q[i];
+            qnew[i] = qref;
+            g = d * gii;
+        } else if (lrs) {
+            d = qnew[i] - q[i];
+            g = d * gii;
+        } else if (p.to_mode == LBM_TO_GAMMA) {
+            if (!sing) {
+                g = p.gamma_std * L.znorm[i];
+                d = g / gii;
+            }
+        } else if (p.to_mode == LBM_TO_TRACK) {
+            const long long row = step < p.track_len ? step : p.track_len - 1;
+            d = L.track[(size_t)row * nq + i] - q[i];
+            g = d * gii;
+        }
+        dq[i] = d;
+        gam[i] = g;
+        wv[i] = sing ? 0.0 : scale2(d, -hexp[i]);
+    }
+    __syncthreads();
+    // 5. beta = G^-1 dQ = (s_i / d_i) sum_j B_ij s_j dQ_j (group gi forms beta_gi)
+    const bool skip = sing || p.to_mode == LBM_TO_OBSERVE;
+    if (!skip) {
+        double t = 0.0;
+        if (gi < nq) {
+            t = M[cur][gi][nq + gl] * wv[gl];
+            if (gl + 8 < nq) t = fma(M[cur][gi][nq + gl + 8], wv[gl + 8], t);
+        }
+        t = group8_sum(t);
+        if (gl == 0 && gi < nq) beta[gi] = rs[gi] * t;
+    } else if (tid < nq) {
+        beta[tid] = 0.0;
+    }
+    __syncthreads();
+    // 6. QoI block row and histories (thread i = QoI i)
+    const long long rc = L.st->ring_count;
+    double* row = L.ring + (size_t)(rc % p.ring_cap) * p.row_len;
+    if (tid < nq) {
+        const int i = tid;
+        L.beta[i] = beta[i];
+        row[1 + i] = q[i];
+        row[1 + nq + i] = dq[i];
+        row[1 + 2 * nq + i] = gam[i];
+        if (lrs) {
+            const long long slot = L.st->hist_pos % p.h;
+            L.qh[slot * nq + i] = qnew[i];
+            L.qsh[slot * nq + i] = q[i];
+        }
+    }
+    if (tid == 32) {
+        row[0] = (double)step;
+        unsigned fl = sing ? LBM_FLAG_SINGULAR : 0u;
+        if (L.st->status & 1u) fl |= LBM_FLAG_UNSTABLE;
+        row[1 + 3 * nq] = (double)fl;
+    }
+    // 7. mean profile of the corrected velocity: P_v + sum_k beta_k P_k + nx nz sum_j beta_mp_j w_j
+    for (int y = tid; y < p.ny; y += blockDim.x) {
+        const double* ps = L.plane_sum + (size_t)y * np1;
+        double a = ps[0], b = 0.0;
+        for (int k = 0; k < ns; ++k) a = fma(beta[k], ps[1 + k], a);
+        for (int j = 0; j < nmp; ++j) b = fma(beta[ns + j], L.w_mp[(size_t)j * p.ny + y], b);
+        L.profile[y] += fma(a, p.inv_area, b);
+    }
+    __syncthreads();
     if (tid == 0) {
+        L.st->ring_count = rc + 1;
+        if (lrs) L.st->hist_pos += 1;
         L.st->prof_steps += 1;
         L.st->step = step + 1;
     }
@@ -520,14 +697,14 @@ cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* 
     for (int k = 0; k < kMaxQoi; ++k) r.v[k] = k < p.n_s ? vk[k] : nullptr;
     dim3 grid(p.ny, p.nzc);
     switch (p.n_s) {
-        case 1: reduce_kernel<1><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
-        case 2: reduce_kernel<2><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
-        case 3: reduce_kernel<3><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
-        case 4: reduce_kernel<4><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
-        case 5: reduce_kernel<5><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
-        case 6: reduce_kernel<6><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
-        case 7: reduce_kernel<7><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
-        case 8: reduce_kernel<8><<<grid, 128, 0, s>>>(p, L.vps, r, L.part, L.plane_part); break;
+        case 1: reduce_kernel<1><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
+        case 2: reduce_kernel<2><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
+        case 3: reduce_kernel<3><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
+        case 4: reduce_kernel<4><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
+        case 5: reduce_kernel<5><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
+        case 6: reduce_kernel<6><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
+        case 7: reduce_kernel<7><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
+        case 8: reduce_kernel<8><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -537,8 +714,14 @@ cudaError_t launch_lrs_pre(const Params& p, const Layout& L, cudaStream_t s) {
     lrs_pre_kernel<<<nb + 1, 256, 0, s>>>(p, L, nb);
     return cudaGetLastError();
 }
+cudaError_t launch_totals(const Params& p, const Layout& L, cudaStream_t s) {
+    const int nplane_blk = (p.ny * (1 + p.n_s) + 7) / 8;
+    const int nb = p.ntot + nplane_blk + (p.to_mode == LBM_TO_LRS ? p.n_q : 0);
+    totals_kernel<<<nb, 256, 0, s>>>(p, L, nplane_blk);
+    return cudaGetLastError();
+}
 cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s) {
-    solve_kernel<<<1, 256, 0, s>>>(p, L);
+    solve_kernel<<<1, kSolveThreads, 0, s>>>(p, L);
     return cudaGetLastError();
 }
 

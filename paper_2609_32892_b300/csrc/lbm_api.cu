@@ -205,6 +205,7 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     p->spinup = c->to_mode == LBM_TO_LRS ? c->spinup : 0;
     p->track_len = (c->to_mode == LBM_TO_TRACK || p->spinup > 0) ? c->track_len : 0;
     p->gamma_std = c->gamma_std;
+    p->inv_area = 1.0 / ((double)c->nx * (double)c->nz);
     p->seed = c->seed;
     p->member = c->member;
     // reduction geometry: one block per (row y, chunk of z planes), ~1200 blocks
@@ -215,6 +216,8 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     p->nzc = (c->nz + zper - 1) / zper;
     p->nblk_red = c->ny * p->nzc;
     p->npart = p->n_s + p->n_s * (p->n_s + 1) / 2;
+    p->ntot = p->npart + p->n_mp * (1 + p->n_s);
+    p->npart_all = p->npart + 2 * p->n_mp * (1 + p->n_s);
     for (int f = 0; f < 8; ++f) p->tune.filter_per_sm[f] = 0;
     p->tune.march_lines = 148 * 2048;
     p->tune.collide_pair = c->substrate == LBM_SUBSTRATE_WALE ? 0 : 1;
@@ -273,7 +276,9 @@ static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filt
             l.rr[f] = cv.take<float>(p.ncomp * N);
             l.vz[f] = filt[f].need_z ? cv.take<float>(p.dim * N) : nullptr;
         }
-        l.part = cv.take<float>((size_t)p.nblk_red * (p.npart > 0 ? p.npart : 1));
+        l.part = cv.take<float>((size_t)p.nblk_red * (p.npart_all > 0 ? p.npart_all : 1));
+        l.tot = cv.take<double>(p.ntot > 0 ? p.ntot : 1);
+        l.hsum = cv.take<double>(kMaxQoi);
         l.plane_part = cv.take<float>((size_t)p.nzc * p.ny * (1 + p.n_s));
         l.znorm = cv.take<double>(kMaxQoi);
         l.plane_sum = cv.take<double>((size_t)p.ny * (1 + p.n_s));
@@ -289,6 +294,7 @@ static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filt
         }
         if (p.track_len > 0) l.track = cv.take<double>((size_t)p.track_len * p.n_q);
         l.w_mp = cv.take<double>((size_t)(p.n_mp > 0 ? p.n_mp : 1) * p.ny);
+        l.w_mp2 = cv.take<float2>((size_t)(p.n_mp > 0 ? p.n_mp : 1) * p.ny);
         l.g_mpmp = cv.take<double>((size_t)(p.n_mp > 0 ? p.n_mp * p.n_mp : 1));
         bool fourier = false;
         for (const Filter& f : filt) fourier = fourier || f.kind == LBM_FILTER_FOURIER;
@@ -512,6 +518,7 @@ static void enqueue_step(Launcher& lc, int src) {
     }
     LAUNCH(lc, LBM_K_REDUCE, launch_reduce(p, L, vk, lc.s));
     if (fork) lc.check(cudaStreamWaitEvent(lc.s, c->ev_join, 0));
+    LAUNCH(lc, LBM_K_REDUCE, launch_totals(p, L, lc.s));
     LAUNCH(lc, LBM_K_SOLVE, launch_solve(p, L, lc.s));
     if (p.to_mode != LBM_TO_OBSERVE) LAUNCH(lc, LBM_K_APPLY, launch_apply(p, L, 1 - src, lc.s));
 }
@@ -858,6 +865,13 @@ int lbm_create(const lbm_config* cfg, void* dev_buf, size_t bytes, void* cuda_st
                 g[(size_t)i * c->p.n_mp + j] = area * a;
             }
         e = cudaMemcpyAsync(c->L.w_mp, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, c->stream);
+        std::vector<float2> w2(w.size());
+        for (size_t i = 0; i < w.size(); ++i) {
+            w2[i].x = (float)w[i];
+            w2[i].y = (float)(w[i] - (double)w2[i].x);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->L.w_mp2, w2.data(), sizeof(float2) * w2.size(), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(c->L.g_mpmp, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, c->stream);
     }

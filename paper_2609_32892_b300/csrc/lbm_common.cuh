@@ -44,10 +44,12 @@ struct Layout {
     float* acc;          // [6][N]  R applied once
     float* rr[kMaxFilters];  // [6][N] R R (v, omega) per filter
     float* vz[kMaxFilters];  // [3][N] curl*(R R omega) per filter
-    float* part;         // [nblk_red][npart] reduction partials (FP32 block sums)
+    float* part;         // [nblk_red][npart_all] reduction partials (FP32 block sums, coupling pairs)
     float* plane_part;   // [nzc][ny][1 + n_s] plane-sum partials
     double* plane_sum;   // [ny][1 + n_s] plane sums of v_x and V_k,x
-    double* red_out;     // [npart] reduced partials (diagnostics)
+    double* tot;         // [ntot] totals of the reduction partials
+    double* hsum;        // [N_Q] known part of the LRS prediction (histories, mu, L z)
+    float2* w_mp2;       // [n_mp][ny] band weights as float pairs hi + lo (block couplings)
     double* lrs_part;    // [nblk_lrs][N_Q] LRS history matvec partials
     double* znorm;       // [N_Q] normals of the current step (LRS noise / gamma draws)
     double* lrs_C;       // [(2h+1)N + 1][N]
@@ -91,8 +93,11 @@ struct Params {
     long long track_len;
     long long spinup;    // LRS: steps nudged to the reference first
     double gamma_std;
+    double inv_area;     // 1 / (nx nz), rounded once on the host
     unsigned long long seed, member;
     int nblk_red, nzc, npart, nblk_lrs, lrs_rows_per_blk;
+    int ntot;            // npart + n_mp (1 + n_s) mean-profile couplings
+    int npart_all;       // floats per block partial row: npart + 2 n_mp (1 + n_s) (couplings as float pairs)
     Tune tune;
 };
 
@@ -120,6 +125,7 @@ cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaSt
 cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* vk, cudaStream_t s);
 // LRS history partials and the step's normals (LRS and gamma modes)
 cudaError_t launch_lrs_pre(const Params& p, const Layout& L, cudaStream_t s);
+cudaError_t launch_totals(const Params& p, const Layout& L, cudaStream_t s);
 cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s);
 cudaError_t launch_macros(const Params& p, const Layout& L, int which, float* drho_out, float* u_out,
                           cudaStream_t s);

@@ -46,7 +46,7 @@ __global__ void masked_copy_kernel(Params p, const float* __restrict__ u, float*
 __global__ void finish_kernel(Params p, const float* __restrict__ part, double* __restrict__ q) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = wid; k < p.n_s; k += blockDim.x >> 5) {
-        const double a = df_warp_sum(part + k, p.nblk_red, (size_t)p.npart, lane);
+        const double a = df_warp_sum(part + k, p.nblk_red, (size_t)p.npart_all, lane);
         if (lane == 0) q[k] = 0.5 * a;
     }
 }
@@ -183,6 +183,8 @@ extern "C" int lbm_qoi_eval_static(const lbm_config* cfg, const float* u, double
     p.nzc = (p.nz + zper - 1) / zper;
     p.nblk_red = p.ny * p.nzc;
     p.npart = p.n_s + p.n_s * (p.n_s + 1) / 2;
+    p.ntot = p.npart;  // no mean-profile bands
+    p.npart_all = p.npart;
 
     // scratch layout (offsets into the static array)
     const size_t N = (size_t)p.n;
@@ -196,7 +198,7 @@ extern "C" int lbm_qoi_eval_static(const lbm_config* cfg, const float* u, double
         if (filt[f].need_z) need += align256(sizeof(float) * p.dim * N);
     }
     const size_t off_part = need;
-    need += align256(sizeof(float) * (size_t)p.nblk_red * p.npart);
+    need += align256(sizeof(float) * (size_t)p.nblk_red * p.npart_all);
     const size_t off_plane = need;
     need += align256(sizeof(float) * (size_t)p.nzc * p.ny * (1 + p.n_s));
     if (need > LBM_STATIC_SCRATCH_BYTES)

@@ -226,6 +226,39 @@ int lbm_set_graphs(lbm_ctx* ctx, int enable);
  * lbm_step (LBM_ERR_STATE after it). */
 int lbm_set_branching(lbm_ctx* ctx, int enable);
 
+/* ------------------------------------------------------------------------
+ * Projection phi_m and QoIs of a given field (Sec. 3, coarse graining;
+ * the HF reference trajectories used for tracking, Sec. 4.4, and for
+ * training, Sec. 4.5).
+ *
+ * phi_m maps the state of a high-fidelity (HF) context onto an m-times
+ * coarser lattice (velocities unchanged: the coarse time step is m times
+ * longer).
+ *   2-D, doubly periodic: bicubic interpolation (Keys cubic convolution,
+ *     a = -1/2) at the LF block centres (m i + (m-1)/2, m j + (m-1)/2);
+ *     LF grid nx/m x ny/m.
+ *   3-D channel: wall-anchored stride-m subsampling, odd m: LF fluid row j
+ *     on HF row m j - (m-1)/2 so that the walls coincide, solid rows on solid
+ *     rows, x and z on the block centres; LF grid nx/m x ((ny-2)/m + 2) x nz/m
+ *     (1475x237x490 with m = 5 gives 295x49x98, Sec. 7.1).
+ * Other geometries, even m in 3-D and sizes that do not divide return
+ * LBM_ERR_ARG.
+ *
+ * lbm_project_shape: the LF grid {nx, ny, nz} of phi_m for a configuration.
+ * lbm_project: enqueues, on the HF context's stream, phi_m of its current
+ *   state into caller-owned DEVICE buffers drho[N_LF] (density - 1) and
+ *   u[3][N_LF] (u_z = 0 in 2-D; solid LF rows 0).  Reads only the HF
+ *   populations at the sampled nodes.
+ * lbm_eval_qoi: enqueues, on the context's stream, the context's QoIs
+ *   (its scale-aware QoIs and mean-profile bands, to_mode != LBM_TO_OFF)
+ *   evaluated on a caller-supplied DEVICE velocity u[3][N] of its grid,
+ *   written to the DEVICE array q[N_Q].  Uses the context's TO scratch: do
+ *   not overlap it with lbm_step of the same context on another stream.
+ * ------------------------------------------------------------------------ */
+int lbm_project_shape(const lbm_config* cfg, int m, int32_t* lf_dims);
+int lbm_project(lbm_ctx* hf, int m, float* drho_lf, float* u_lf);
+int lbm_eval_qoi(lbm_ctx* ctx, const float* u, double* q);
+
 /* Autotuner (default on): before the first lbm_step the library times the
  * candidate launch shapes of its kernels on this context's buffers (node-pair
  * vs single-node collide, 4-node vs single-node SGS apply, the z-segment count

@@ -32,6 +32,7 @@ EXPORTED = [
     "lbm_qoi_eval_static", "lbm_filter_flops_per_step",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_admit", "lbm_batch_member", "lbm_batch_run",
     "lbm_batch_poll", "lbm_batch_release", "lbm_batch_stats", "lbm_set_autotune", "lbm_get_tuning", "lbm_set_branching",
+    "lbm_project_shape", "lbm_project", "lbm_eval_qoi",
 ]
 
 
@@ -99,6 +100,9 @@ def _load():
         "lbm_batch_stats": [VP, P(C.c_size_t), P(C.c_size_t), P(C.c_int32)],
         "lbm_set_autotune": [VP, C.c_int],
         "lbm_set_branching": [VP, C.c_int],
+        "lbm_project_shape": [C.POINTER(lbm_config), C.c_int, C.POINTER(C.c_int32)],
+        "lbm_project": [VP, C.c_int, VP, VP],
+        "lbm_eval_qoi": [VP, VP, VP],
         "lbm_get_tuning": [VP, P(C.c_int32), C.c_int],
     }
     for name, args in sig.items():
@@ -365,6 +369,23 @@ def lbm_set_autotune(ctx, enable):
 
 def lbm_set_branching(ctx, enable):
     _check(_lib.lbm_set_branching(ctx, int(bool(enable))), ctx)
+
+
+def lbm_project_shape(cfg, m):
+    """LF grid (nx, ny, nz) of the projection phi_m of a configuration."""
+    d = (C.c_int32 * 3)()
+    _check(_lib.lbm_project_shape(C.byref(cfg), int(m), d), None)
+    return tuple(int(v) for v in d)
+
+
+def lbm_project(ctx, m, drho_ptr, u_ptr):
+    """Enqueue phi_m of the context's state into device buffers (raw pointers)."""
+    _check(_lib.lbm_project(ctx, int(m), C.c_void_p(drho_ptr), C.c_void_p(u_ptr)), ctx)
+
+
+def lbm_eval_qoi(ctx, u_ptr, q_ptr):
+    """Enqueue the context's QoIs of a device velocity field into a device array."""
+    _check(_lib.lbm_eval_qoi(ctx, C.c_void_p(u_ptr), C.c_void_p(q_ptr)), ctx)
 
 
 def lbm_get_tuning(ctx):

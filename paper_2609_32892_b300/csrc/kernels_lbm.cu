@@ -805,4 +805,118 @@ cudaError_t launch_macros(const Params& p, const Layout& L, int which, float* dr
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ projection --
+// phi_m (Sec. 3, coarse graining) of the stored state onto an m-times coarser
+// lattice: the density deviation and velocity sum c f / rho (as
+// macros_kernel) at the HF nodes the projection reads, combined on the LF
+// grid.  One thread per LF node; only the sampled HF nodes' populations are
+// read (1/m^3 of the field in 3-D, 16/m^2 of it in 2-D for m >= 4).
+template <int DIM, typename T>
+__device__ __forceinline__ void node_macros(const T* __restrict__ f, size_t N, size_t n, float& dr, float& ux,
+                                            float& uy, float& uz) {
+    using LT = Lat<DIM>;
+    float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const float gi = ldg_<T>(f + (size_t)i * N + n);
+        r += gi;
+        jx += LT::cx(i) * gi;
+        jy += LT::cy(i) * gi;
+        jz += LT::cz(i) * gi;
+    }
+    const float inv = 1.0f / (1.0f + r);
+    dr = r;
+    ux = jx * inv;
+    uy = jy * inv;
+    uz = jz * inv;
+}
+
+// Keys' cubic convolution weight (a = -1/2) at distance t
+__device__ __forceinline__ float keys_w(float t) {
+    t = fabsf(t);
+    if (t <= 1.f) return (1.5f * t - 2.5f) * t * t + 1.f;
+    if (t < 2.f) return ((-0.5f * t + 2.5f) * t - 4.f) * t + 2.f;
+    return 0.f;
+}
+
+// 2-D doubly periodic: bicubic interpolation at the LF block centres
+// (m i + (m-1)/2, m j + (m-1)/2) in HF node units, over the 4 x 4 nearest
+// HF nodes (taps of zero weight, all but one for odd m, are skipped)
+template <typename T>
+__global__ void __launch_bounds__(256) project2d_kernel(Params p, const T* __restrict__ f, int m, int nxl, int nyl,
+                                                        float* __restrict__ drho, float* __restrict__ u) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nl = nxl * nyl;
+    if (t >= nl) return;
+    const int i = t % nxl, j = t / nxl;
+    const size_t N = (size_t)p.n;
+    const int half = (m - 1) / 2;
+    const float frac = (m % 2 == 0) ? 0.5f : 0.f;  // X - floor(X)
+    float w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[k] = keys_w(frac - (float)(k - 1));
+    const int bx = m * i + half, by = m * j + half;
+    float sr = 0.f, sx = 0.f, sy = 0.f;
+    for (int b = 0; b < 4; ++b) {
+        if (w[b] == 0.f) continue;
+        const int ys = (by + b - 1 + p.ny) % p.ny;
+        float rr = 0.f, rx = 0.f, ry = 0.f;
+        for (int a = 0; a < 4; ++a) {
+            if (w[a] == 0.f) continue;
+            const int xs = (bx + a - 1 + p.nx) % p.nx;
+            float dr, ux, uy, uz;
+            node_macros<2, T>(f, N, (size_t)ys * p.nx + xs, dr, ux, uy, uz);
+            rr = fmaf(w[a], dr, rr);
+            rx = fmaf(w[a], ux, rx);
+            ry = fmaf(w[a], uy, ry);
+        }
+        sr = fmaf(w[b], rr, sr);
+        sx = fmaf(w[b], rx, sx);
+        sy = fmaf(w[b], ry, sy);
+    }
+    drho[t] = sr;
+    u[t] = sx;
+    u[(size_t)nl + t] = sy;
+    u[(size_t)2 * nl + t] = 0.f;
+}
+
+// 3-D channel: wall-anchored stride-m subsampling (odd m): LF fluid row j on
+// HF row m j - (m-1)/2, solid rows on solid rows, x and z on the block centres
+template <typename T>
+__global__ void __launch_bounds__(256) project3d_kernel(Params p, const T* __restrict__ f, int m, int nxl, int nyl,
+                                                        int nzl, float* __restrict__ drho, float* __restrict__ u) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nl = (long long)nxl * nyl * nzl;
+    if (t >= nl) return;
+    const int i = (int)(t % nxl);
+    const long long r = t / nxl;
+    const int j = (int)(r % nyl), k = (int)(r / nyl);
+    float dr = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+    if (j > 0 && j < nyl - 1) {
+        const int c = (m - 1) / 2;
+        const size_t n = ((size_t)(m * k + c) * p.ny + (m * j - c)) * p.nx + (m * i + c);
+        node_macros<3, T>(f, (size_t)p.n, n, dr, ux, uy, uz);
+    }
+    drho[t] = dr;
+    u[t] = ux;
+    u[nl + t] = uy;
+    u[2 * nl + t] = uz;
+}
+
+template <typename T>
+static void do_project(const Params& p, const Layout& L, int which, int m, int nxl, int nyl, int nzl, float* drho,
+                       float* u, cudaStream_t s) {
+    const long long nl = (long long)nxl * nyl * nzl;
+    const unsigned grid = (unsigned)((nl + 255) / 256);
+    if (p.dim == 2)
+        project2d_kernel<T><<<grid, 256, 0, s>>>(p, (const T*)L.f[which], m, nxl, nyl, drho, u);
+    else
+        project3d_kernel<T><<<grid, 256, 0, s>>>(p, (const T*)L.f[which], m, nxl, nyl, nzl, drho, u);
+}
+cudaError_t launch_project(const Params& p, const Layout& L, int which, int m, int nxl, int nyl, int nzl,
+                           float* drho, float* u, cudaStream_t s) {
+    LBM_DISPATCH_STORAGE(p, do_project, p, L, which, m, nxl, nyl, nzl, drho, u, s);
+    return cudaGetLastError();
+}
+
 }  // namespace lbm

@@ -668,6 +668,27 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L
     }
 }
 
+// ------------------------------------------------- QoIs of a given field --
+// The QoI path on a velocity field supplied by the caller (a projected HF
+// field): u [3][N] into the filter input with the solid rows zeroed, then,
+// after the filters, reduction and totals, q_i = Q_i(u) (Eqs. scale-aware-
+// energy / enstrophy: half the squared norms; the bands: sum_y w_j(y) P_0(y)).
+__global__ void __launch_bounds__(256) load_velocity_kernel(Params p, const float* __restrict__ u,
+                                                            float* __restrict__ x6) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.n) return;
+    const size_t N = (size_t)p.n;
+    const int y = (int)((n / p.nx) % p.ny);
+    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+    for (int c = 0; c < p.dim; ++c) x6[c * N + n] = solid ? 0.f : u[c * N + n];
+}
+
+__global__ void qoi_values_kernel(Params p, Layout L, double* __restrict__ q) {
+    const int i = threadIdx.x;
+    const int ns = p.n_s, np1 = 1 + ns, cpl = ns + ns * (ns + 1) / 2;
+    if (i < p.n_q) q[i] = i < ns ? 0.5 * L.tot[i] : L.tot[cpl + (i - ns) * np1];
+}
+
 // ------------------------------------------------------------ launchers --
 static inline unsigned gridn(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
@@ -714,9 +735,9 @@ cudaError_t launch_lrs_pre(const Params& p, const Layout& L, cudaStream_t s) {
     lrs_pre_kernel<<<nb + 1, 256, 0, s>>>(p, L, nb);
     return cudaGetLastError();
 }
-cudaError_t launch_totals(const Params& p, const Layout& L, cudaStream_t s) {
+cudaError_t launch_totals(const Params& p, const Layout& L, bool with_lrs, cudaStream_t s) {
     const int nplane_blk = (p.ny * (1 + p.n_s) + 7) / 8;
-    const int nb = p.ntot + nplane_blk + (p.to_mode == LBM_TO_LRS ? p.n_q : 0);
+    const int nb = p.ntot + nplane_blk + (with_lrs && p.to_mode == LBM_TO_LRS ? p.n_q : 0);
     totals_kernel<<<nb, 256, 0, s>>>(p, L, nplane_blk);
     return cudaGetLastError();
 }
@@ -725,4 +746,15 @@ cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+}  // namespace lbm
+
+namespace lbm {
+cudaError_t launch_load_velocity(const Params& p, const Layout& L, const float* u, cudaStream_t s) {
+    load_velocity_kernel<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(p, u, L.x6);
+    return cudaGetLastError();
+}
+cudaError_t launch_qoi_values(const Params& p, const Layout& L, double* q, cudaStream_t s) {
+    qoi_values_kernel<<<1, 32, 0, s>>>(p, L, q);
+    return cudaGetLastError();
+}
 }  // namespace lbm

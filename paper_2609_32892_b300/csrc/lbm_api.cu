@@ -474,25 +474,12 @@ static void enqueue_filter(Launcher& lc, const Filter& f, int slot, const float*
     }
 }
 
-static void enqueue_step(Launcher& lc, int src) {
+// curl, filters, sensitivities and the block reduction of the velocity in
+// x6: the QoI/Gram part of the TO phase
+static void enqueue_fields(Launcher& lc) {
     lbm_ctx* c = lc.c;
     const Params& p = c->p;
     const Layout& L = c->L;
-    // LRS history matvec and the step's normals: inputs from the previous
-    // step only, so they run on a branch beside the field kernels and join
-    // before the solve (in line when the kernels are timed one by one)
-    const bool pre = p.to_mode == LBM_TO_LRS || p.to_mode == LBM_TO_GAMMA;
-    const bool fork = pre && c->branch && !lc.timed && !lc.count_only;
-    if (fork) {
-        lc.check(cudaEventRecord(c->ev_fork, lc.s));
-        lc.check(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-        LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, c->side));
-        lc.check(cudaEventRecord(c->ev_join, c->side));
-    }
-    if (p.substrate == LBM_SUBSTRATE_WALE) LAUNCH(lc, LBM_K_MOMENTS, launch_moments(p, L, src, lc.s));
-    LAUNCH(lc, LBM_K_COLLIDE, launch_collide(p, L, src, lc.s));
-    if (p.to_mode == LBM_TO_OFF) return;
-    if (pre && !fork) LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, lc.s));
     LAUNCH(lc, LBM_K_CURL, launch_to_curl(p, L, lc.s));
     if (c->has_fft) {
         // one forward transform of (v_x, v_y, omega) serves every Fourier band
@@ -517,8 +504,30 @@ static void enqueue_step(Launcher& lc, int src) {
         vk[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
     }
     LAUNCH(lc, LBM_K_REDUCE, launch_reduce(p, L, vk, lc.s));
+}
+
+static void enqueue_step(Launcher& lc, int src) {
+    lbm_ctx* c = lc.c;
+    const Params& p = c->p;
+    const Layout& L = c->L;
+    // LRS history matvec and the step's normals: inputs from the previous
+    // step only, so they run on a branch beside the field kernels and join
+    // before the solve (in line when the kernels are timed one by one)
+    const bool pre = p.to_mode == LBM_TO_LRS || p.to_mode == LBM_TO_GAMMA;
+    const bool fork = pre && c->branch && !lc.timed && !lc.count_only;
+    if (fork) {
+        lc.check(cudaEventRecord(c->ev_fork, lc.s));
+        lc.check(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, c->side));
+        lc.check(cudaEventRecord(c->ev_join, c->side));
+    }
+    if (p.substrate == LBM_SUBSTRATE_WALE) LAUNCH(lc, LBM_K_MOMENTS, launch_moments(p, L, src, lc.s));
+    LAUNCH(lc, LBM_K_COLLIDE, launch_collide(p, L, src, lc.s));
+    if (p.to_mode == LBM_TO_OFF) return;
+    if (pre && !fork) LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, lc.s));
+    enqueue_fields(lc);
     if (fork) lc.check(cudaStreamWaitEvent(lc.s, c->ev_join, 0));
-    LAUNCH(lc, LBM_K_REDUCE, launch_totals(p, L, lc.s));
+    LAUNCH(lc, LBM_K_REDUCE, launch_totals(p, L, true, lc.s));
     LAUNCH(lc, LBM_K_SOLVE, launch_solve(p, L, lc.s));
     if (p.to_mode != LBM_TO_OBSERVE) LAUNCH(lc, LBM_K_APPLY, launch_apply(p, L, 1 - src, lc.s));
 }
@@ -1255,6 +1264,52 @@ int lbm_get_tuning(lbm_ctx* c, int32_t* values, int count) {
     int32_t v[12] = {c->tuned, c->p.tune.collide_pair, c->p.tune.apply4, c->p.tune.march_lines};
     for (int f = 0; f < 8; ++f) v[4 + f] = c->p.tune.filter_per_sm[f];
     for (int k = 0; k < count && k < 12; ++k) values[k] = v[k];
+    return LBM_OK;
+}
+
+// ------------------------------------------------------ projection phi_m --
+static int lf_dims(const lbm_config* c, int m, int32_t d[3]) {
+    if (m < 1) return fail(nullptr, LBM_ERR_ARG, "projection factor m must be >= 1");
+    if (c->dim == 2) {
+        if (c->walls) return fail(nullptr, LBM_ERR_ARG, "2-D projection (bicubic) needs a doubly periodic grid");
+        if (c->nx % m || c->ny % m) return fail(nullptr, LBM_ERR_ARG, "%dx%d does not coarsen by m = %d", c->nx, c->ny, m);
+        d[0] = c->nx / m; d[1] = c->ny / m; d[2] = 1;
+    } else {
+        if (!c->walls) return fail(nullptr, LBM_ERR_ARG, "3-D projection (wall-anchored subsampling) needs the channel walls");
+        if (m % 2 == 0) return fail(nullptr, LBM_ERR_ARG, "wall-anchored subsampling needs odd m");
+        if (c->nx % m || c->nz % m || (c->ny - 2) % m)
+            return fail(nullptr, LBM_ERR_ARG, "%dx%dx%d does not coarsen by m = %d", c->nx, c->ny, c->nz, m);
+        d[0] = c->nx / m; d[1] = (c->ny - 2) / m + 2; d[2] = c->nz / m;
+    }
+    if (d[0] < 3 || d[1] < 3 || (c->dim == 3 && (d[1] < 4 || d[2] < 3)))
+        return fail(nullptr, LBM_ERR_ARG, "LF grid %dx%dx%d too small", d[0], d[1], d[2]);
+    return LBM_OK;
+}
+
+int lbm_project_shape(const lbm_config* cfg, int m, int32_t* lf) {
+    if (!cfg || !lf) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    return lf_dims(cfg, m, lf);
+}
+
+int lbm_project(lbm_ctx* c, int m, float* drho, float* u) {
+    if (!c || !drho || !u) return fail(c, LBM_ERR_ARG, "NULL argument");
+    int32_t d[3];
+    const int rc = lf_dims(&c->cfg, m, d);
+    if (rc != LBM_OK) return fail(c, rc, "%s", g_err);
+    CK(c, launch_project(c->p, c->L, c->cur, m, d[0], d[1], d[2], drho, u, c->stream));
+    return LBM_OK;
+}
+
+int lbm_eval_qoi(lbm_ctx* c, const float* u, double* q) {
+    if (!c || !u || !q) return fail(c, LBM_ERR_ARG, "NULL argument");
+    if (c->p.to_mode == LBM_TO_OFF) return fail(c, LBM_ERR_STATE, "lbm_eval_qoi needs a context with QoIs (to_mode != off)");
+    Launcher lc{c, c->stream, false, 0};
+    lc.timed = false;
+    LAUNCH(lc, LBM_K_CURL, launch_load_velocity(c->p, c->L, u, lc.s));
+    enqueue_fields(lc);
+    LAUNCH(lc, LBM_K_REDUCE, launch_totals(c->p, c->L, false, lc.s));
+    LAUNCH(lc, LBM_K_SOLVE, launch_qoi_values(c->p, c->L, q, lc.s));
+    if (lc.err != cudaSuccess) return fail(c, LBM_ERR_CUDA, "lbm_eval_qoi: %s", cudaGetErrorString(lc.err));
     return LBM_OK;
 }
 

@@ -125,10 +125,16 @@ cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaSt
 cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* vk, cudaStream_t s);
 // LRS history partials and the step's normals (LRS and gamma modes)
 cudaError_t launch_lrs_pre(const Params& p, const Layout& L, cudaStream_t s);
-cudaError_t launch_totals(const Params& p, const Layout& L, cudaStream_t s);
+cudaError_t launch_totals(const Params& p, const Layout& L, bool with_lrs, cudaStream_t s);
 cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s);
 cudaError_t launch_macros(const Params& p, const Layout& L, int which, float* drho_out, float* u_out,
                           cudaStream_t s);
+// projection phi_m of the stored state onto the nxl x nyl x nzl LF grid
+cudaError_t launch_project(const Params& p, const Layout& L, int which, int m, int nxl, int nyl, int nzl,
+                           float* drho, float* u, cudaStream_t s);
+// the QoIs of a given velocity field: u [3][N] into x6, then q from the totals
+cudaError_t launch_load_velocity(const Params& p, const Layout& L, const float* u, cudaStream_t s);
+cudaError_t launch_qoi_values(const Params& p, const Layout& L, double* q, cudaStream_t s);
 
 void set_global_error(const char* msg);
 

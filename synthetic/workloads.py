@@ -103,7 +103,42 @@ def _c2f():
     return w
 
 
+def _hf_channel():
+    """HF reference run of Sec. 7.1: plain BGK channel on the 1475x237x490 grid
+    (171 M nodes), projected by phi_5 onto the 295x49x98 LF grid."""
+    p = channel_lattice(237)
+    w = _base()
+    w.update(name="channel3d_1475x237x490_bgk_hf", dim=3, nx=1475, ny=237, nz=490, walls=True, tau=p["tau"],
+             forcing="edm", body_force=(p["body_force"], 0.0, 0.0), seed=20260908,
+             init=("channel", 0.1, 0.05), steps=2000)
+    return w
+
+
+def _lf_channel():
+    """The LF channel LES of Sec. 7.1 (295x49x98, WALE + TO-LRS, 12 QoIs): the
+    grid phi_5 of the HF run lands on."""
+    p = channel_lattice(49)
+    w = _c3()
+    w.update(name="channel3d_295x49x98_wale_tolrs", nx=295, ny=49, nz=98, tau=p["tau"],
+             body_force=(p["body_force"], 0.0, 0.0), seed=20260909)
+    return w
+
+
+def _hf_kolmo():
+    """HF reference run of Sec. 6: plain BGK Kolmogorov flow on 2048^2,
+    projected by phi_8 (bicubic) onto the 256^2 LF grid of C2."""
+    p = kolmogorov_lattice(2048)
+    w = _base()
+    w.update(name="kolmogorov2d_2048_bgk_hf", dim=2, nx=2048, ny=2048, tau=p["tau"], forcing="guo",
+             kolmo_amp=p["kolmo_amp"], kolmo_k=4, kolmo_drag=p["kolmo_drag"], seed=20260910,
+             init=("noise", 1e-3), steps=20000)
+    return w
+
+
 WORKLOADS = {
+    "HF_CHANNEL": _hf_channel,
+    "LF_CHANNEL": _lf_channel,
+    "HF_KOLMO": _hf_kolmo,
     "C1": _c1,
     "C2": _c2,
     "C3": _c3,

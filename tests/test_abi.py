@@ -58,3 +58,16 @@ def test_required_bytes_and_config_errors(B):
         B.lbm_required_bytes(bad)
     cfg = B.config_from_workload(synthetic.workload("C3"))
     assert B.lbm_qoi_row_len(cfg) == 2 + 3 * 12
+
+
+def test_projection_shapes_without_gpu(B):
+    """phi_m's LF grid is host arithmetic: the channel of Sec. 7.1 (phi_5) and
+    the 2048^2 Kolmogorov run onto the 256^2 LF grid (phi_8)."""
+    assert B.lbm_project_shape(B.config_from_workload(synthetic.workload("HF_CHANNEL")), 5) == (295, 49, 98)
+    lf = synthetic.workload("LF_CHANNEL")
+    assert (lf["nx"], lf["ny"], lf["nz"]) == (295, 49, 98)
+    assert B.lbm_project_shape(B.config_from_workload(synthetic.workload("HF_KOLMO")), 8) == (256, 256, 1)
+    for name, m in [("HF_CHANNEL", 4), ("HF_CHANNEL", 3), ("HF_KOLMO", 3), ("C4", 0)]:
+        with pytest.raises(B.LbmError) as e:
+            B.lbm_project_shape(B.config_from_workload(synthetic.workload(name)), m)
+        assert e.value.args and "m" in str(e.value)

@@ -346,6 +346,71 @@ def run_serving(args, device):
     return res
 
 
+def run_reference_series(args, device):
+    """HF reference trajectories (Sec. 3 projection, reference of Sec. 4.4):
+    the HF BGK run at the paper's grids with phi_m and the LF QoIs every m
+    HF steps, all on the device.  Per LF row: m HF steps, one projection, one
+    QoI evaluation, timed separately with CUDA events on the run's stream."""
+    import torch
+
+    from paper_2609_32892_b300 import binding as B
+    from paper_2609_32892_b300.reference import HFReference
+
+    out = {}
+    # the channel at the benchmark scale (the paper's 1475x237x490 HF grid
+    # exceeds the library's 2^31 population-index limit) and the paper's
+    # 2048^2 Kolmogorov run onto the 256^2 LF grid
+    for hf_name, lf_name, m in (("HF_CHANNEL_480", "C3", 5), ("HF_KOLMO", "C2", 8)):
+        hf_wl, lf_wl = synthetic.workload(hf_name), synthetic.workload(lf_name)
+        r = HFReference(hf_wl, lf_wl, m, device=device)
+        s = r.hf.stream
+        nq = r.nq
+        q = torch.empty((args.ref_rows + 2, nq), dtype=torch.float64, device=device)
+        # warm-up: the first steps tune launch shapes
+        r.hf.step(m)
+        B.lbm_project(r.hf.ctx, m, r.drho.data_ptr(), r.u.data_ptr())
+        B.lbm_eval_qoi(r.lf.ctx, r.u.data_ptr(), q[0].data_ptr())
+        torch.cuda.synchronize(device)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.ref_rows)]
+        for n in range(args.ref_rows):
+            e = ev[n]
+            e[0].record(s)
+            r.hf.step(m)
+            e[1].record(s)
+            B.lbm_project(r.hf.ctx, m, r.drho.data_ptr(), r.u.data_ptr())
+            e[2].record(s)
+            B.lbm_eval_qoi(r.lf.ctx, r.u.data_ptr(), q[1 + n].data_ptr())
+            e[3].record(s)
+        torch.cuda.synchronize(device)
+        t_step = statistics.median(e[0].elapsed_time(e[1]) for e in ev)
+        t_proj = statistics.median(e[1].elapsed_time(e[2]) for e in ev)
+        t_eval = statistics.median(e[2].elapsed_time(e[3]) for e in ev)
+        t_row = sum(e[0].elapsed_time(e[3]) for e in ev) / args.ref_rows
+        n_hf = hf_wl["nx"] * hf_wl["ny"] * hf_wl["nz"]
+        n_lf = lf_wl["nx"] * lf_wl["ny"] * lf_wl["nz"]
+        q_dim = 19 if hf_wl["dim"] == 3 else 9
+        # bytes the projection must move: the populations of the sampled HF
+        # nodes (1 per LF node in 3-D; 16 per LF node for even m in 2-D) and
+        # the LF (drho, u)
+        taps = 1 if hf_wl["dim"] == 3 else (16 if m % 2 == 0 else 1)
+        proj_bytes = n_lf * (taps * q_dim * 4 + 16)
+        out[hf_wl["name"]] = {
+            "hf_grid": [hf_wl["nx"], hf_wl["ny"], hf_wl["nz"]], "lf_grid": [lf_wl["nx"], lf_wl["ny"], lf_wl["nz"]],
+            "m": m, "n_qoi": nq, "rows_timed": args.ref_rows,
+            "ms_per_row": round(t_row, 4), "rows_per_s": round(1e3 / t_row, 2),
+            "hf_mlups_with_projection": round(n_hf * m / (t_row * 1e-3) / 1e6, 1),
+            "hf_steps_ms": round(t_step, 4), "hf_mlups": round(n_hf * m / (t_step * 1e-3) / 1e6, 1),
+            "project_ms": round(t_proj, 4), "project_gbs": round(proj_bytes / (t_proj * 1e-3) / 1e9, 1),
+            "eval_qoi_ms": round(t_eval, 4),
+            "projection_and_qoi_share": round((t_proj + t_eval) / (t_step + t_proj + t_eval), 4),
+            "finite": bool(torch.isfinite(q[:args.ref_rows + 1]).all().item()),
+        }
+        r.close()
+        del r, q
+        torch.cuda.empty_cache()
+    return out
+
+
 def cpu_oracle_sample(wl, seconds=15.0):
     """The oracle (as it stands) stepping a bounded sample of the workload:
     the same physics and QoI set on a 48x40x24 sub-grid, timed for ~`seconds`."""
@@ -391,6 +456,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-pool-gb", type=int, default=16)
     ap.add_argument("--serve-chunk", type=int, default=32)
+    ap.add_argument("--no-ref", dest="ref", action="store_false")
+    ap.add_argument("--ref-rows", type=int, default=10)
     args = ap.parse_args()
     world, rank, local = _dist()
     wl = synthetic.workload(args.workload, storage=args.storage)
@@ -424,6 +491,11 @@ def main():
         import torch
 
         serving = run_serving(args, torch.device("cuda", local))
+    reference = None
+    if args.ref and rank == 0:
+        import torch
+
+        reference = run_reference_series(args, torch.device("cuda", local))
     if rank == 0:
         cpu = cpu_oracle_sample(wl, args.cpu_seconds) if world == 1 else None
         line = {"metric": METRIC, "value": round(r["mlups"], 1), "unit": "MLUPS", "n_gpus": world,
@@ -434,7 +506,8 @@ def main():
                 "config": config, "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
                 "gpu_launches": int(r["launches"] * args.steps), "clocks": r["clocks"],
                 "step_hbm_gbs": round(r["step_gbs"], 1), "collide_gbs": r["collide_gbs"],
-                "sections": r["sections"], "tuning": r["tuning"], "bgk_480x200x240": r["bgk"], "serving": serving}
+                "sections": r["sections"], "tuning": r["tuning"], "bgk_480x200x240": r["bgk"], "serving": serving,
+                "hf_reference": reference}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

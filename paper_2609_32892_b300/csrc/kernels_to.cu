@@ -582,7 +582,8 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L
     // 4. coefficient source -> dQ, gamma (group gi forms the LRS product of QoI gi)
     if (lrs_pred) {
         double t = 0.0;
-        if (gi < nq) t = xq[gl] * c_q0 + (gl + 8 < nq ? xq[gl + 8] * c_q1 : 0.0);
+        // lanes past the last QoI read nothing (shared memory there is not initialised)
+        if (gi < nq && gl < nq) t = xq[gl] * c_q0 + (gl + 8 < nq ? xq[gl + 8] * c_q1 : 0.0);
         t = group8_sum(t);
         if (gl == 0 && gi < nq) qnew[gi] = L.lrs_sigma[gi] * (L.hsum[gi] + t);  // corrected QoI for the history
     }
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L
     const bool skip = sing || p.to_mode == LBM_TO_OBSERVE;
     if (!skip) {
         double t = 0.0;
-        if (gi < nq) {
+        if (gi < nq && gl < nq) {
             t = M[cur][gi][nq + gl] * wv[gl];
             if (gl + 8 < nq) t = fma(M[cur][gi][nq + gl + 8], wv[gl + 8], t);
         }

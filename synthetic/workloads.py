@@ -114,6 +114,16 @@ def _hf_channel():
     return w
 
 
+def _hf_channel_480():
+    """HF reference run at the 480x200x240 benchmark scale: plain BGK channel on
+    480x192x240 (22.1 M nodes), projected by phi_5 onto C3's 96x40x48 grid."""
+    p = channel_lattice(192)
+    w = _hf_channel()
+    w.update(name="channel3d_480x192x240_bgk_hf", nx=480, ny=192, nz=240, tau=p["tau"],
+             body_force=(p["body_force"], 0.0, 0.0), seed=20260911)
+    return w
+
+
 def _lf_channel():
     """The LF channel LES of Sec. 7.1 (295x49x98, WALE + TO-LRS, 12 QoIs): the
     grid phi_5 of the HF run lands on."""
@@ -137,6 +147,7 @@ def _hf_kolmo():
 
 WORKLOADS = {
     "HF_CHANNEL": _hf_channel,
+    "HF_CHANNEL_480": _hf_channel_480,
     "LF_CHANNEL": _lf_channel,
     "HF_KOLMO": _hf_kolmo,
     "C1": _c1,

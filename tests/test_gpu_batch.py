@@ -108,3 +108,34 @@ def test_server_runs_a_request_stream():
         assert np.all(np.isfinite(r["qoi"]))
     s = serve.summarize(out, wall)
     assert s["member_steps_per_s"] > 0 and s["latency_s_per_tu_p99"] >= s["latency_s_per_tu_p50"]
+
+
+def test_serving_mix_members_stay_stable_over_hundreds_of_steps():
+    """The serving mix's member kinds (2-D Smagorinsky + TO-LRS with 4 QoIs,
+    3-D WALE + TO-LRS with 12 QoIs, automatic reference scales) run a few
+    hundred steps in one batch without an unstable flag, with finite QoIs,
+    and the 4-QoI members agree with the oracle over the run."""
+    import torch
+
+    from gpu_common import run_gpu, run_oracle
+    from paper_2609_32892_b300 import serve
+
+    reqs = serve.scaled_mix(8, 5, 1.0, 0.04)
+    for r in reqs:
+        r["steps"] = 300
+    srv = serve.EnsembleServer(2 << 30, 16, "cuda")
+    out, _, _ = srv.serve(reqs, chunk=25, keep_qoi=True, realtime=False)
+    srv.close()
+    assert all(r["status"] == 0 for r in out.values()), [r["status"] for r in out.values()]
+    for r in out.values():
+        assert np.isfinite(r["qoi"][:, 1:-1]).all()
+    # a small 4-QoI member against the oracle over 150 steps
+    wl = synthetic.workload("C2", nx=40, ny=32, h=5, seed=21)
+    nq = nq_of(wl)
+    c, mu, sig = synthetic.synthetic_lrs(nq, wl["h"], wl["seed"])
+    lrs = (c, mu, sig, np.zeros(nq))
+    _, rg, _, u_g = run_gpu(wl, 150, lrs=lrs)
+    _, ro, _, u_o = run_oracle(wl, 150, lrs=lrs)
+    assert np.all(rg[:, -1] == ro[:, -1])
+    np.testing.assert_allclose(rg[:, 1:1 + nq], ro[:, 1:1 + nq], rtol=1e-3)
+    torch.cuda.synchronize()

@@ -357,10 +357,10 @@ def run_reference_series(args, device):
     from paper_2609_32892_b300.reference import HFReference
 
     out = {}
-    # the channel at the benchmark scale (the paper's 1475x237x490 HF grid
-    # exceeds the library's 2^31 population-index limit) and the paper's
-    # 2048^2 Kolmogorov run onto the 256^2 LF grid
-    for hf_name, lf_name, m in (("HF_CHANNEL_480", "C3", 5), ("HF_KOLMO", "C2", 8)):
+    # the paper's channel pair (1475x237x490 -> 295x49x98), the channel at the
+    # benchmark scale (480x192x240 -> 96x40x48) and the paper's 2048^2
+    # Kolmogorov run onto the 256^2 LF grid
+    for hf_name, lf_name, m in (("HF_CHANNEL", "LF_CHANNEL", 5), ("HF_CHANNEL_480", "C3", 5), ("HF_KOLMO", "C2", 8)):
         hf_wl, lf_wl = synthetic.workload(hf_name), synthetic.workload(lf_name)
         r = HFReference(hf_wl, lf_wl, m, device=device)
         s = r.hf.stream

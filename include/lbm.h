@@ -125,7 +125,10 @@ typedef struct lbm_ctx lbm_ctx;
 int lbm_qoi_row_len(const lbm_config* cfg, int64_t* len);
 
 /* Bytes of device memory lbm_create needs for this configuration.
- * ERR_ARG if the configuration is invalid (the text says why). */
+ * ERR_ARG if the configuration is invalid (the text says why), including
+ * grids with 6 nx ny nz >= 2^31 (node and field-component offsets are
+ * 32-bit; population offsets are 64-bit, so a 171 M-node D3Q19 grid is
+ * accepted). */
 int lbm_required_bytes(const lbm_config* cfg, size_t* bytes);
 
 /* Build a simulation inside the caller's device buffer.

@@ -100,8 +100,10 @@ static int validate(const lbm_config* c) {
     if (c->storage < 0 || c->storage > 2) return fail(nullptr, LBM_ERR_ARG, "bad storage");
     if (c->to_mode < 0 || c->to_mode > 4) return fail(nullptr, LBM_ERR_ARG, "bad to_mode");
     const long long n = (long long)c->nx * c->ny * c->nz;
-    const int q = c->dim == 2 ? 9 : 19;
-    if (n * q >= (1LL << 31) || n * 6 >= (1LL << 31)) return fail(nullptr, LBM_ERR_ARG, "grid too large (Q*N >= 2^31)");
+    // populations are addressed with 64-bit offsets (Q N may exceed 2^31, e.g. the
+    // 171 M-node HF channel); node indices and the per-component offsets of the
+    // velocity and filter fields (up to 6 N) are 32-bit
+    if (n * 6 >= (1LL << 31)) return fail(nullptr, LBM_ERR_ARG, "grid too large (6 N >= 2^31)");
     if (c->to_mode != LBM_TO_OFF) {
         if (c->n_qoi < 0 || c->n_mp < 0 || c->n_qoi + c->n_mp < 1 || c->n_qoi + c->n_mp > LBM_MAX_QOI)
             return fail(nullptr, LBM_ERR_ARG, "need 1..%d QoIs", LBM_MAX_QOI);

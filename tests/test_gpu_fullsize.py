@@ -87,3 +87,42 @@ def test_full_grid_to_lrs_step_properties():
     assert np.all(rows[:, 1:1 + 6:2] > 0)  # E_G3, E_L3, E_L1
     assert abs((rho1 * m).sum() - mass0) / mass0 < 1e-6
     assert np.all(np.isfinite(u1))
+
+
+def test_paper_hf_grid_projected_columns():
+    """The paper's HF channel grid (1475x237x490, 171 M nodes: population
+    offsets up to 18 N = 3.1e9, past 2^31) for two steps, projected by phi_5
+    onto 295x49x98; whole projected columns are compared with oracle windows
+    of the same seeded field."""
+    import torch
+
+    from oracle import projection as P
+    from paper_2609_32892_b300 import LbmSim, binding as B
+
+    wl = synthetic.workload("HF_CHANNEL")
+    m = 5
+    u0 = synthetic.initial_velocity(wl)
+    g = LbmSim(wl)
+    g.init(u0)
+    g.step(2)
+    nxl, nyl, nzl = B.lbm_project_shape(g.cfg, m)
+    nl = nxl * nyl * nzl
+    drho = torch.empty(nl, dtype=torch.float32, device="cuda")
+    u = torch.empty(3 * nl, dtype=torch.float32, device="cuda")
+    B.lbm_project(g.ctx, m, drho.data_ptr(), u.data_ptr())
+    g.sync()
+    ug = u.double().cpu().numpy().reshape(3, nzl, nyl, nxl)
+    rg = 1.0 + drho.double().cpu().numpy().reshape(nzl, nyl, nxl)
+    g.close()
+    rows = P.anchored_rows(wl["ny"], m)
+    cols = [(nxl - 1, nzl - 1), (0, 0), (nxl // 2, nzl - 2), (17, 60)]
+    for i, k in cols:
+        x0, z0 = m * i + (m - 1) // 2, m * k + (m - 1) // 2
+        ww = dict(wl, nx=W, nz=W)
+        o = Simulation(ww, _window_u0(u0, x0, z0))
+        o.run(2)
+        rho_o, u_o = o.macros()
+        c = W // 2
+        np.testing.assert_allclose(ug[:, k, :, i], u_o[:, c, rows, c], rtol=0, atol=2e-6, err_msg=str((i, k)))
+        np.testing.assert_allclose(rg[k, 1:-1, i], rho_o[c, rows[1:-1], c], rtol=0, atol=2e-6, err_msg=str((i, k)))
+    del u0

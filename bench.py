@@ -49,14 +49,14 @@ def _peaks():
     return 6400.0, "fallback"
 
 
-# DRAM traffic of the fused Laplacian-filter launches (lap3_kernel<7,1> and
-# cross3_kernel<2>, the dominant kernel class), from one ncu capture on the
-# 320x200x160 channel (profiles/filters_channel3d_320x200x160.md): read+write
-# bytes per launch averaged over the class, per lattice node.  It is reported
-# only while the kernel source still has the hash it had when captured.
+# DRAM traffic of the fused Laplacian-filter launches (lapf3_kernel, the
+# factorised L_3, and cross3_kernel<2>, the dominant kernel class), from ncu
+# captures on the 320x200x160 channel (profiles/filters_channel3d_320x200x160.md):
+# read+write bytes per launch averaged over the class, per lattice node.  It is
+# reported only while the kernel source still has the hash it had when captured.
 TRAFFIC = {
-    "lap3": {"bytes_per_node": ((275.314688 + 212.014336) + (254.4256 + 206.620672)) / 2 * 1e6 / (320 * 200 * 160),
-             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "85df6288052e4c36"},
+    "lap3": {"bytes_per_node": ((272.899584 + 209.432576) + (254.4256 + 206.620672)) / 2 * 1e6 / (320 * 200 * 160),
+             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "d0aa16b071f0b711"},
 }
 
 
@@ -245,18 +245,29 @@ def run_ours(args, world, rank, local):
                 "frac": round(ach / peak, 4), "peak_kind": peak_kind, "traffic": None,
                 "bytes_per_launch": algo[dominant], "avg_launch_ms": avg_ms}
     elif dominant in ("gauss3", "lap3") and flops[dominant] > 0:
-        # the fused filters are issue/ALU bound: FP32 FLOP/s against the FP32 peak
+        # a fused filter launch reads and writes the six-component field once
+        # (48 B per node); its bound is the roofline's: HBM when its algorithmic
+        # FLOP per byte is below the ridge (FP32 peak / measured HBM), else FP32
         tms, cnt = prof[dominant]
         per_launch = flops[dominant] / (cnt / args.profile_steps)
-        ach = per_launch / (tms / cnt * 1e-3) / 1e12
+        bytes_launch = n_nodes * 2 * 6 * 4
+        avg_ms = tms / cnt
+        tflops = per_launch / (avg_ms * 1e-3) / 1e12
+        gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
+        intensity = per_launch / bytes_launch
+        ridge = FP32_PEAK_TFLOPS * 1e3 / peak
         tr = _traffic(dominant, n_nodes)
-        roof = {"kernel": dominant, "bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
-                "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz",
-                "traffic": None if tr is None else round(tr), "traffic_unit": "bytes per launch (ncu, scaled by nodes)",
-                "algorithmic_bytes_per_launch": n_nodes * 2 * 6 * 4,
-                "flops_per_launch": per_launch, "avg_launch_ms": tms / cnt,
-                "hbm_gbs": round(n_nodes * 2 * 6 * 4 / (tms / cnt * 1e-3) / 1e9, 1)}
+        common = {"kernel": dominant, "traffic": None if tr is None else round(tr),
+                  "traffic_unit": "bytes per launch (ncu, scaled by nodes)", "algorithmic_bytes_per_launch": bytes_launch,
+                  "flops_per_launch": per_launch, "flop_per_byte": round(intensity, 2), "ridge_flop_per_byte": round(ridge, 2),
+                  "avg_launch_ms": avg_ms, "tflops": round(tflops, 3), "hbm_gbs": round(gbs, 1)}
+        if intensity < ridge:
+            roof = dict(common, bound="hbm", achieved=round(gbs, 1), peak=peak, unit="GB/s", frac=round(gbs / peak, 4),
+                        peak_kind=peak_kind)
+        else:
+            roof = dict(common, bound="alu", achieved=round(tflops, 3), peak=round(FP32_PEAK_TFLOPS, 2), unit="TFLOP/s",
+                        frac=round(tflops / FP32_PEAK_TFLOPS, 4),
+                        peak_kind="derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz")
     coll = prof["collide"]
     coll_gbs = algo["collide"] / (coll[0] / coll[1] * 1e-3) / 1e9 if coll[1] else None
     step_gbs = n_nodes * (2 * (19 if wl["dim"] == 3 else 9) * (4 if wl["storage"] == "fp32" else 2)

@@ -280,9 +280,11 @@ int lbm_profile_read(lbm_ctx* ctx, double* ms, int64_t* launches, int count);
 int lbm_launches_per_step(lbm_ctx* ctx, int64_t* launches);
 
 /* Algorithmic floating-point operations of one step's filter applications,
- * per kernel class (LBM_K_GAUSS3, LBM_K_LAP3, LBM_K_FILTER): 2 x (taps of the
- * separable factors) x components x nodes, the minimum a separable
- * evaluation needs (halo recomputation excluded). */
+ * per kernel class (LBM_K_GAUSS3, LBM_K_LAP3, LBM_K_FILTER): 2 x taps x
+ * components x nodes, with G_s and B3 counted as d separable factors and
+ * L_s as the box B_s (d factors of s taps) times the (4d + 1)-point cross
+ * of l at stride s (Sec. 4.1: L_s is L_1 dilated by the s^d block of ones);
+ * halo recomputation excluded. */
 int lbm_filter_flops_per_step(lbm_ctx* ctx, double* flops, int count);
 
 /* ------------------------------------------------------------------------

@@ -350,6 +350,195 @@ __global__ void __launch_bounds__(256) cross3_kernel(Params p, const float* __re
     }
 }
 
+// L_3 factorised.  L_s is L_1 dilated by the Kronecker product with the s^3
+// block of ones, so L_s = c B_s * C_s: B_s the s x s x s box and C_s the cross
+// of l = [1, -4, 6, -4, 1] at stride s along every axis (centre 3 x 6).  For
+// s = 3 that is a 27-point box and a 13-point cross instead of the 3 x 21
+// taps of the separable-sum form.  Per input plane q:
+//   BB(q) = B_x B_y x(q) on the output tile +- 6 (one shared-memory pass),
+//   XY(q) = (l_x + l_y)(BB(q)) at the outputs (centre 12, arms at +-3, +-6),
+//   Y(p)  = XY(p) + l_z(BB)(p) with p = q - 6 (BB of planes p, p +- 3, p +- 6),
+//   out(q - 7) = Y(q - 8) + Y(q - 7) + Y(q - 6) (the box along z).
+// The planes p +- 3, p +- 6 share p's residue mod 3, so the z rings are kept
+// per residue class and the plane loop is unrolled by three: a plane shifts
+// only its own class's ring.  A thread produces 4 consecutive x outputs of
+// one row.  Input planes are staged by asynchronous 16-byte copies, three
+// planes in flight (needs nx % 4 == 0).  Zero extension along y with walls,
+// periodic x and z, as above.
+namespace lf3 {
+constexpr int TX = 32, TY = 32;     // output tile
+constexpr int HX = 8, HY = 7;       // input halo (x padded to 8 for 16-byte chunks)
+constexpr int WP = TX + 2 * HX;     // 48 floats per staged row
+constexpr int NQ = WP / 4;          // 12 chunks per row
+constexpr int TH = TY + 2 * HY;     // 46 staged rows
+constexpr int BH = TY + 12;         // 44 box rows (outputs +- 6)
+constexpr int NT = 256;             // 8 x-quads x 32 rows
+constexpr int SZ = TH * WP;
+constexpr int STAGES = 3;
+}  // namespace lf3
+
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct Lf3Ring {
+    float bb[4][4];  // BB of planes q-12, q-9, q-6, q-3 of this residue class, per output
+    float xy[2][4];  // XY of planes q-6, q-3
+};
+
+__device__ __forceinline__ float4 add3(float4 a, float4 b, float4 c) {
+    return make_float4(a.x + b.x + c.x, a.y + b.y + c.y, a.z + b.z + c.z, a.w + b.w + c.w);
+}
+
+// one plane: the box (after the staged tile is complete), a barrier, then the
+// arms, the z rings and this thread's 4 outputs of plane q - 7
+__device__ __forceinline__ void lf3_plane(const Params& p, int q, int z0, int z1, int y0, int gx0, int yo,
+                                          const float* __restrict__ tl, float* __restrict__ bb, Lf3Ring& rg,
+                                          float (&y1)[4], float (&y2)[4], float* __restrict__ o, float scale,
+                                          int accumulate) {
+    constexpr int NQ = lf3::NQ, BH = lf3::BH, NT = lf3::NT;
+    const int tid = threadIdx.x;
+    // BB row r <-> y = y0 - 6 + r (staged rows r .. r + 2); quad qx covers
+    // staged columns 4 qx .. 4 qx + 3 and needs columns 4 qx - 1 .. 4 qx + 4.
+    // Whole neighbour quads are read: conflict-free 16-byte shared loads.
+    const float4* t4 = reinterpret_cast<const float4*>(tl);
+    for (int task = tid; task < BH * NQ; task += NT) {
+        const int r = task / NQ, qx = task - r * NQ;
+        const float4* row = t4 + r * NQ + qx;
+        const float4 c = add3(row[0], row[NQ], row[2 * NQ]);
+        float l = 0.f, rr = 0.f;
+        if (qx > 0) l = row[-1].w + row[NQ - 1].w + row[2 * NQ - 1].w;
+        if (qx < NQ - 1) rr = row[1].x + row[NQ + 1].x + row[2 * NQ + 1].x;
+        reinterpret_cast<float4*>(bb)[r * NQ + qx] =
+            make_float4(l + c.x + c.y, c.x + c.y + c.z, c.y + c.z + c.w, c.z + c.w + rr);
+    }
+    __syncthreads();
+    const int qo = tid & 7;
+    const int row = yo + 6;
+    const float4* b4 = reinterpret_cast<const float4*>(bb);
+    float v[20];  // BB of this row at staged columns 4 qo .. 4 qo + 19 (outputs at + 8 .. + 11)
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const float4 w = b4[row * NQ + qo + m];
+        v[4 * m] = w.x; v[4 * m + 1] = w.y; v[4 * m + 2] = w.z; v[4 * m + 3] = w.w;
+    }
+    const float4 m6 = b4[(row - 6) * NQ + qo + 2], m3 = b4[(row - 3) * NQ + qo + 2];
+    const float4 p3 = b4[(row + 3) * NQ + qo + 2], p6 = b4[(row + 6) * NQ + qo + 2];
+    const float ym6[4] = {m6.x, m6.y, m6.z, m6.w}, ym3[4] = {m3.x, m3.y, m3.z, m3.w};
+    const float yp3[4] = {p3.x, p3.y, p3.z, p3.w}, yp6[4] = {p6.x, p6.y, p6.z, p6.w};
+    float res[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float c = v[8 + j];
+        const float a3 = (v[5 + j] + v[11 + j]) + (ym3[j] + yp3[j]);
+        const float a6 = (v[2 + j] + v[14 + j]) + (ym6[j] + yp6[j]);
+        const float xy = fmaf(12.f, c, fmaf(-4.f, a3, a6));
+        // Y(q - 6) = XY(q - 6) + l_z(BB)(q - 6) over planes q - 12 .. q
+        const float yz = rg.xy[0][j] + fmaf(6.f, rg.bb[2][j], fmaf(-4.f, rg.bb[1][j] + rg.bb[3][j], rg.bb[0][j] + c));
+        res[j] = (y1[j] + y2[j]) + yz;  // box along z: the output of plane q - 7
+        y1[j] = y2[j];
+        y2[j] = yz;
+        rg.bb[0][j] = rg.bb[1][j]; rg.bb[1][j] = rg.bb[2][j]; rg.bb[2][j] = rg.bb[3][j]; rg.bb[3][j] = c;
+        rg.xy[0][j] = rg.xy[1][j]; rg.xy[1][j] = xy;
+    }
+    const int zo = q - 7;
+    const int y = y0 + yo;
+    // nx % 4 == 0: a quad is wholly inside or wholly outside the row
+    if (zo >= z0 && zo < z1 && y < p.ny && gx0 < p.nx) {
+        const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+        float4* op = reinterpret_cast<float4*>(o + ((size_t)zo * p.ny + y) * p.nx + gx0);
+        float4 w = make_float4(solid ? 0.f : scale * res[0], solid ? 0.f : scale * res[1],
+                               solid ? 0.f : scale * res[2], solid ? 0.f : scale * res[3]);
+        if (accumulate) {
+            const float4 old = *op;
+            w.x += old.x; w.y += old.y; w.z += old.z; w.w += old.w;
+        }
+        *op = w;
+    }
+}
+
+__global__ void __launch_bounds__(256) lapf3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                    float scale, int accumulate, int ncomp, int seg) {
+    constexpr int TX = lf3::TX, TY = lf3::TY, HX = lf3::HX, HY = lf3::HY, NQ = lf3::NQ, TH = lf3::TH;
+    constexpr int NT = lf3::NT, SZ = lf3::SZ;
+    __shared__ __align__(16) float tile[lf3::STAGES][SZ];
+    __shared__ __align__(16) float bb[lf3::BH * lf3::WP];
+    __shared__ int coff[TH * NQ];
+    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int nz = p.nz;
+    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const size_t N = (size_t)p.n;
+    const float* a = in + c * N;
+    float* o = out + c * N;
+    const int yo = threadIdx.x >> 3;
+    const int gx0 = x0 + 4 * (threadIdx.x & 7);
+    // chunk k of a staged plane: row k / NQ <-> y0 - HY + row, columns
+    // 4 (k % NQ) .. + 3 <-> x0 - HX + 4 (k % NQ) .. (periodic in x; with
+    // nx % 4 == 0 a chunk never straddles the period).  The in-plane offsets
+    // (-1: beyond a wall, zero-filled) are the same for every plane.
+    for (int k = threadIdx.x; k < TH * NQ; k += NT) {
+        const int ly = k / NQ, m = k - ly * NQ;
+        int gy = y0 - HY + ly;
+        const int gx = pm(x0 - HX + 4 * m, p.nx);
+        bool ok = true;
+        if (p.walls) ok = gy >= 0 && gy < p.ny;
+        else gy = pm(gy, p.ny);
+        coff[k] = ok ? gy * p.nx + gx : -1;
+    }
+    __syncthreads();
+    auto issue = [&](int q, float* t) {
+        const float* plane = a + (size_t)pm(q, nz) * p.ny * p.nx;
+        for (int k = threadIdx.x; k < TH * NQ; k += NT) {
+            const int ofs = coff[k];
+            cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);
+        }
+    };
+    Lf3Ring ra, rb, rc;
+    float y1[4], y2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        y1[j] = y2[j] = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) ra.bb[m][j] = rb.bb[m][j] = rc.bb[m][j] = 0.f;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) ra.xy[m][j] = rb.xy[m][j] = rc.xy[m][j] = 0.f;
+    }
+    // planes z0 - 7 .. z1 + 6 (output z = q - 7 needs planes up to z + 7),
+    // padded to a multiple of three; the extra planes only skip their stores
+    const int qs = z0 - 7;
+    const int n = (z1 - z0) + 14;
+    const int n3 = (n + 2) / 3 * 3;
+    issue(qs, tile[0]);
+    cp_async_commit();
+    issue(qs + 1, tile[1]);
+    cp_async_commit();
+    for (int s = 0; s < n3; s += 3) {
+        // plane s + K sits in buffer K (s is a multiple of 3).  After the
+        // barrier every thread has left the previous plane's arms (bb may be
+        // rewritten) and its box pass (buffer K + 2 mod 3, which held the
+        // previous plane, may be refilled).
+#define LF3_STEP(K, RING)                                                                                  \
+        {                                                                                                  \
+            const int q = qs + s + K;                                                                      \
+            cp_async_wait1();                                                                              \
+            __syncthreads();                                                                               \
+            if (s + K + 2 < n3) issue(q + 2, tile[(K + 2) % 3]);                                           \
+            cp_async_commit();                                                                             \
+            lf3_plane(p, q, z0, z1, y0, gx0, yo, tile[K], bb, RING, y1, y2, o, scale, accumulate);         \
+        }
+        LF3_STEP(0, ra)
+        LF3_STEP(1, rb)
+        LF3_STEP(2, rc)
+#undef LF3_STEP
+    }
+    cp_async_wait0();
+}
+
 int seg_len(const Params& p, int blocks_xy, int ncomp, int R, int per_sm) {
     // enough z segments for `per_sm` blocks per SM; each segment re-reads 2R planes
     const long long want = 148LL * per_sm;
@@ -387,6 +576,15 @@ cudaError_t run_lap(const Params& p, const float* in, float* out, int ncomp, con
         lap3_kernel<RA, RB><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
     return cudaGetLastError();
 }
+// L_3 by the factorised kernel (box * dilated cross); needs nx % 4 == 0
+cudaError_t run_lapf3(const Params& p, const float* in, float* out, int ncomp, float scale, int acc, int per_sm,
+                      cudaStream_t s) {
+    const int bx = (p.nx + lf3::TX - 1) / lf3::TX, by = (p.ny + lf3::TY - 1) / lf3::TY;
+    const int seg = seg_len(p, bx * by, ncomp, 7, per_sm > 0 ? per_sm : 4);
+    const int nseg = (p.nz + seg - 1) / seg;
+    lapf3_kernel<<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, scale, acc, ncomp, seg);
+    return cudaGetLastError();
+}
 }  // namespace
 
 // G_s / B3 in 3-D with the same 1-D taps on every axis.
@@ -405,7 +603,10 @@ cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncom
 cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp, int s_scale, const Taps& arm,
                         float scale, int accumulate, int per_sm, cudaStream_t s) {
     if (s_scale == 1 && arm.radius == 2) return run_lap<2, 0>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
-    if (s_scale == 3 && arm.radius == 7) return run_lap<7, 1>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
+    if (s_scale == 3 && arm.radius == 7) {
+        if (p.nx % 4 == 0) return run_lapf3(p, in, out, ncomp, scale, accumulate, per_sm, s);
+        return run_lap<7, 1>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
+    }
     return cudaErrorNotSupported;
 }
 

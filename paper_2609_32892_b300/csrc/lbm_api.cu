@@ -409,7 +409,10 @@ static double filter_taps(const Filter& f, int d) {
     if (f.kind == LBM_FILTER_FOURIER) return 0.0;  // transforms, counted separately
     if (f.kind == LBM_FILTER_GAUSS) return d * (2.0 * (d == 2 ? 4 : 2) * f.scale + 1.0);
     if (f.kind == LBM_FILTER_BINOMIAL) return d * 3.0;
-    return d * (5.0 * f.scale + (f.scale > 1 ? (d - 1) * (double)f.scale : 0.0));
+    // L_s = c B_s * C_s: the (4d + 1)-point cross at stride s plus the
+    // separable s^d box (d factors of s taps), the factorised form the 3-D
+    // kernel evaluates
+    return 4.0 * d + 1.0 + (f.scale > 1 ? (double)d * f.scale : 0.0);
 }
 
 static void enqueue_filter(Launcher& lc, const Filter& f, int slot, const float* in, float* out) {

@@ -50,13 +50,13 @@ def _peaks():
 
 
 # DRAM traffic of the fused Laplacian-filter launches (lapf3_kernel, the
-# factorised L_3, and cross3_kernel<2>, the dominant kernel class), from ncu
+# factorised L_3, and crossa3_kernel, the L_1 cross: the dominant kernel class), from ncu
 # captures on the 320x200x160 channel (profiles/filters_channel3d_320x200x160.md):
 # read+write bytes per launch averaged over the class, per lattice node.  It is
 # reported only while the kernel source still has the hash it had when captured.
 TRAFFIC = {
-    "lap3": {"bytes_per_node": ((272.899584 + 209.432576) + (254.4256 + 206.620672)) / 2 * 1e6 / (320 * 200 * 160),
-             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "d0aa16b071f0b711"},
+    "lap3": {"bytes_per_node": ((272.899584 + 209.432576) + (265.769728 + 207.451904)) / 2 * 1e6 / (320 * 200 * 160),
+             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "b875144603c82dd8"},
 }
 
 

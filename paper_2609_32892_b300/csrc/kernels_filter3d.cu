@@ -576,6 +576,117 @@ cudaError_t run_lap(const Params& p, const float* in, float* out, int ncomp, con
         lap3_kernel<RA, RB><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
     return cudaGetLastError();
 }
+// L_1 (the 13-point cross) with planes staged by asynchronous 16-byte copies
+// three deep (nx % 4 == 0): the register-prefetch version waits on DRAM
+// latency (one plane ahead, long-scoreboard stalls).  One barrier per plane:
+// after it every thread has left the previous plane, whose buffer is refilled.
+namespace cx3 {
+constexpr int TX = 32, TY = 16, RA = 2, HX = 4, HY = 2;
+constexpr int WP = TX + 2 * HX;  // 40
+constexpr int NQ = WP / 4;       // 10 chunks per row
+constexpr int TH = TY + 2 * HY;  // 20 staged rows
+constexpr int NT = 256, RPT = TY / (NT / TX);
+constexpr int SZ = TH * WP;
+}  // namespace cx3
+
+__global__ void __launch_bounds__(256) crossa3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                      T3<2> arm, float scale, int accumulate, int ncomp, int seg) {
+    constexpr int TX = cx3::TX, TY = cx3::TY, RA = cx3::RA, HX = cx3::HX, HY = cx3::HY, WP = cx3::WP;
+    constexpr int NQ = cx3::NQ, TH = cx3::TH, NT = cx3::NT, RPT = cx3::RPT, SZ = cx3::SZ;
+    constexpr int KZ = 2 * RA + 1;
+    __shared__ __align__(16) float tile[3][SZ];
+    __shared__ int coff[TH * NQ];
+    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int nz = p.nz;
+    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int lx = threadIdx.x % TX, yr = threadIdx.x / TX;
+    const int x = x0 + lx;
+    const size_t N = (size_t)p.n;
+    const float* a = in + c * N;
+    float* o = out + c * N;
+    for (int k = threadIdx.x; k < TH * NQ; k += NT) {
+        const int ly = k / NQ, m = k - ly * NQ;
+        int gy = y0 - HY + ly;
+        const int gx = pm(x0 - HX + 4 * m, p.nx);
+        bool ok = true;
+        if (p.walls) ok = gy >= 0 && gy < p.ny;
+        else gy = pm(gy, p.ny);
+        coff[k] = ok ? gy * p.nx + gx : -1;
+    }
+    __syncthreads();
+    auto issue = [&](int q, float* t) {
+        const float* plane = a + (size_t)pm(q, nz) * p.ny * p.nx;
+        for (int k = threadIdx.x; k < TH * NQ; k += NT) {
+            const int ofs = coff[k];
+            cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);
+        }
+    };
+    float rxy[RPT][RA + 1], rz[RPT][KZ];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+#pragma unroll
+        for (int k = 0; k < RA + 1; ++k) rxy[j][k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KZ; ++k) rz[j][k] = 0.f;
+    }
+    const int qs = z0 - RA, qe = z1 + RA;
+    issue(qs, tile[0]);
+    cp_async_commit();
+    issue(qs + 1, tile[1]);
+    cp_async_commit();
+    int b = 0;
+    for (int q = qs; q < qe; ++q) {
+        cp_async_wait1();
+        __syncthreads();
+        if (q + 2 < qe) issue(q + 2, tile[b == 0 ? 2 : b - 1]);
+        cp_async_commit();
+        const float* tl = tile[b];
+        const int zo = q - RA;
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int ry = yr * RPT + j + HY;
+            const float* row = tl + ry * WP + lx + HX;
+            const float ctr = row[0];
+            float axy = 2.f * arm.t[RA] * ctr;
+#pragma unroll
+            for (int r = 1; r <= RA; ++r)
+                axy += arm.t[RA + r] * ((row[-r] + row[r]) + (row[-r * WP] + row[r * WP]));
+#pragma unroll
+            for (int k = 0; k < RA; ++k) rxy[j][k] = rxy[j][k + 1];
+            rxy[j][RA] = axy;
+#pragma unroll
+            for (int k = 0; k < KZ - 1; ++k) rz[j][k] = rz[j][k + 1];
+            rz[j][KZ - 1] = ctr;
+            const int y = y0 + yr * RPT + j;
+            if (zo >= z0 && x < p.nx && y < p.ny) {
+                // rxy[k] holds plane q - RA + k, so the current output plane is rxy[0]
+                float v = rxy[j][0] + arm.t[RA] * rz[j][RA];
+#pragma unroll
+                for (int r = 1; r <= RA; ++r) v += arm.t[RA + r] * (rz[j][RA - r] + rz[j][RA + r]);
+                const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+                v = solid ? 0.f : scale * v;
+                float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
+                *op = accumulate ? (*op + v) : v;
+            }
+        }
+        b = b == 2 ? 0 : b + 1;
+    }
+    cp_async_wait0();
+}
+
+// L_1 with asynchronously staged planes; needs nx % 4 == 0
+cudaError_t run_crossa3(const Params& p, const float* in, float* out, int ncomp, const Taps& arm, float scale, int acc,
+                        int per_sm, cudaStream_t s) {
+    T3<2> tp;
+    for (int i = 0; i < 5; ++i) tp.t[i] = arm.t[i];
+    const int bx = (p.nx + cx3::TX - 1) / cx3::TX, by = (p.ny + cx3::TY - 1) / cx3::TY;
+    const int seg = seg_len(p, bx * by, ncomp, 2, per_sm > 0 ? per_sm : 4);
+    const int nseg = (p.nz + seg - 1) / seg;
+    crossa3_kernel<<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+    return cudaGetLastError();
+}
+
 // L_3 by the factorised kernel (box * dilated cross); needs nx % 4 == 0
 cudaError_t run_lapf3(const Params& p, const float* in, float* out, int ncomp, float scale, int acc, int per_sm,
                       cudaStream_t s) {
@@ -602,7 +713,10 @@ cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncom
 // L_s in 3-D for s = 1 (arm radius 2, no box) and s = 3 (arm 7, box 1).
 cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp, int s_scale, const Taps& arm,
                         float scale, int accumulate, int per_sm, cudaStream_t s) {
-    if (s_scale == 1 && arm.radius == 2) return run_lap<2, 0>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
+    if (s_scale == 1 && arm.radius == 2) {
+        if (p.nx % 4 == 0) return run_crossa3(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
+        return run_lap<2, 0>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
+    }
     if (s_scale == 3 && arm.radius == 7) {
         if (p.nx % 4 == 0) return run_lapf3(p, in, out, ncomp, scale, accumulate, per_sm, s);
         return run_lap<7, 1>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);

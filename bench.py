@@ -462,7 +462,7 @@ def main():
     ap.add_argument("--no-bgk", dest="bgk", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", dest="serve", action="store_false")
-    ap.add_argument("--serve-n", type=int, default=32)
+    ap.add_argument("--serve-n", type=int, default=256)
     ap.add_argument("--serve-scale", type=float, default=0.1)
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-pool-gb", type=int, default=16)

@@ -92,12 +92,14 @@ def test_projection_rejects_bad_factor():
 
 
 @pytest.mark.parametrize("name,kw", [("C2", dict(nx=44, ny=36)), ("C3", dict(nx=33, ny=22, nz=13)),
-                                     ("C3", dict(nx=36, ny=22, nz=60)), ("C2F", dict())])
+                                     ("C3", dict(nx=36, ny=22, nz=60)),
+                                     ("C3", dict(nx=36, ny=20, nz=14, walls=False, n_mp=0)), ("C2F", dict())])
 def test_eval_qoi_matches_oracle(name, kw):
     """Q(u) of a host velocity field: scale QoIs (G, L, Fourier bands) and
     mean-profile bands.  nx = 33 takes the register-prefetch 3-D Laplacian
     kernels, nx = 36 the factorised / asynchronously staged ones (nx % 4 == 0),
-    with nz = 60 split into three z segments per block column."""
+    with nz = 60 split into three z segments per block column; the periodic
+    3-D case wraps the staged y halo instead of zero-filling it."""
     import torch
     from paper_2609_32892_b300 import LbmSim, binding as B
 

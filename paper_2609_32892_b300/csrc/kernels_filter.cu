@@ -156,4 +156,129 @@ cudaError_t launch_pass_fast(const Params& p, const float* in, float* out, int n
     return cudaErrorNotSupported;
 }
 
+// ------------------------------------------------------ fused 2-D filters --
+// One launch per application on a doubly periodic 2-D grid (the separate x
+// and y passes cost two launches and a round trip of the intermediate field,
+// which dominates small members).  A block stages a (TY + 2R) x (TX + 2R)
+// tile of one component in shared memory with periodic wrap, applies the x
+// factor into a second array (8 consecutive outputs per task from 8 + 2R
+// staged values) and the y factor from there (4 rows per thread); the L_1
+// cross reads the tile directly.
+namespace f2 {
+constexpr int TX = 32, TY = 32, NT = 256;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) gauss2_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                     TapsR<R> tp, float scale, int accumulate) {
+    constexpr int TX = f2::TX, TY = f2::TY, NT = f2::NT, W = TX + 2 * R, H = TY + 2 * R;
+    __shared__ float tile[H * W];
+    __shared__ float xt[H * TX];
+    const size_t N = (size_t)p.n;
+    const float* a = in + blockIdx.z * N;
+    float* o = out + blockIdx.z * N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    for (int i = threadIdx.x; i < H * W; i += NT) {
+        const int ly = i / W, lx = i - ly * W;
+        const int gx = posmod(x0 - R + lx, p.nx), gy = posmod(y0 - R + ly, p.ny);
+        tile[i] = __ldg(a + (size_t)gy * p.nx + gx);
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < H * (TX / 8); task += NT) {
+        const int ry = task / (TX / 8), k = task - ry * (TX / 8);
+        const float* row = tile + ry * W + 8 * k;
+        float v[8 + 2 * R];
+#pragma unroll
+        for (int m = 0; m < 8 + 2 * R; ++m) v[m] = row[m];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float sx = 0.f;
+#pragma unroll
+            for (int r = -R; r <= R; ++r) sx = fmaf(tp.t[r + R], v[j + R - r], sx);
+            xt[ry * TX + 8 * k + j] = sx;
+        }
+    }
+    __syncthreads();
+    const int lx = threadIdx.x & (TX - 1), r0 = (threadIdx.x / TX) * 4;
+    float col[4 + 2 * R];
+#pragma unroll
+    for (int m = 0; m < 4 + 2 * R; ++m) col[m] = xt[(r0 + m) * TX + lx];
+    const int x = x0 + lx;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int y = y0 + r0 + j;
+        if (x < p.nx && y < p.ny) {
+            float sy = 0.f;
+#pragma unroll
+            for (int r = -R; r <= R; ++r) sy = fmaf(tp.t[r + R], col[j + R - r], sy);
+            float* op = o + (size_t)y * p.nx + x;
+            const float v = scale * sy;
+            *op = accumulate ? *op + v : v;
+        }
+    }
+}
+
+// L_1 in 2-D: the 9-point cross of l = [1, -4, 6, -4, 1] along x and y
+__global__ void __launch_bounds__(256) cross2_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                     TapsR<2> ell, float scale, int accumulate) {
+    constexpr int R = 2, TX = f2::TX, TY = f2::TY, NT = f2::NT, W = TX + 2 * R, H = TY + 2 * R;
+    __shared__ float tile[H * W];
+    const size_t N = (size_t)p.n;
+    const float* a = in + blockIdx.z * N;
+    float* o = out + blockIdx.z * N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    for (int i = threadIdx.x; i < H * W; i += NT) {
+        const int ly = i / W, lx = i - ly * W;
+        const int gx = posmod(x0 - R + lx, p.nx), gy = posmod(y0 - R + ly, p.ny);
+        tile[i] = __ldg(a + (size_t)gy * p.nx + gx);
+    }
+    __syncthreads();
+    const int lx = threadIdx.x & (TX - 1), r0 = (threadIdx.x / TX) * 4;
+    const int x = x0 + lx;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int y = y0 + r0 + j;
+        if (x < p.nx && y < p.ny) {
+            const float* c = tile + (r0 + j + R) * W + lx + R;
+            float s2 = 2.f * ell.t[R] * c[0];
+#pragma unroll
+            for (int r = 1; r <= R; ++r) s2 = fmaf(ell.t[R + r], (c[-r] + c[r]) + (c[-r * W] + c[r * W]), s2);
+            float* op = o + (size_t)y * p.nx + x;
+            const float v = scale * s2;
+            *op = accumulate ? *op + v : v;
+        }
+    }
+}
+
+template <int R>
+static cudaError_t run_gauss2(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
+                              int accumulate, cudaStream_t s) {
+    TapsR<R> tr;
+    for (int i = 0; i < 2 * R + 1; ++i) tr.t[i] = t.t[i];
+    const dim3 grid((p.nx + f2::TX - 1) / f2::TX, (p.ny + f2::TY - 1) / f2::TY, ncomp);
+    gauss2_kernel<R><<<grid, f2::NT, 0, s>>>(p, in, out, tr, scale, accumulate);
+    return cudaGetLastError();
+}
+
+// Returns cudaErrorNotSupported unless the grid is 2-D and doubly periodic and
+// a specialised instance exists (the separable passes serve the rest).
+cudaError_t launch_filter2_fused(const Params& p, const float* in, float* out, int ncomp, bool laplacian, int s_scale,
+                                 const Taps& t, float scale, int accumulate, cudaStream_t s) {
+    if (p.dim != 2 || p.walls) return cudaErrorNotSupported;
+    if (laplacian) {
+        if (s_scale != 1 || t.radius != 2) return cudaErrorNotSupported;
+        TapsR<2> tr;
+        for (int i = 0; i < 5; ++i) tr.t[i] = t.t[i];
+        const dim3 grid((p.nx + f2::TX - 1) / f2::TX, (p.ny + f2::TY - 1) / f2::TY, ncomp);
+        cross2_kernel<<<grid, f2::NT, 0, s>>>(p, in, out, tr, scale, accumulate);
+        return cudaGetLastError();
+    }
+    switch (t.radius) {
+        case 1: return run_gauss2<1>(p, in, out, ncomp, t, scale, accumulate, s);
+        case 4: return run_gauss2<4>(p, in, out, ncomp, t, scale, accumulate, s);
+        case 12: return run_gauss2<12>(p, in, out, ncomp, t, scale, accumulate, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
 }  // namespace lbm

@@ -441,6 +441,18 @@ static void enqueue_filter(Launcher& lc, const Filter& f, int slot, const float*
         }
     }
     if (lc.count_only) c->filter_flops[LBM_K_FILTER] += flops;
+    if (d == 2 && !p.walls) {
+        // doubly periodic 2-D: one fused launch when a specialised kernel exists
+        const bool lap = f.kind == LBM_FILTER_LAPLACE;
+        const Taps t = lap ? ell_taps(f.scale) : (f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps());
+        const float sc = lap ? (float)(1.0 / (8.0 * d * (double)f.scale * f.scale)) : 1.f;
+        const bool ok = lap ? (f.scale == 1 && t.radius == 2)
+                            : (t.radius == 1 || t.radius == 4 || t.radius == 12);
+        if (ok) {
+            LAUNCH(lc, LBM_K_FILTER, launch_filter2_fused(p, in, out, nc, lap, f.scale, t, sc, 0, lc.s));
+            return;
+        }
+    }
     if (f.kind == LBM_FILTER_GAUSS || f.kind == LBM_FILTER_BINOMIAL) {
         const Taps t = f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps();
         if (d == 2) {

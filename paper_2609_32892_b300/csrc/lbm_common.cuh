@@ -112,6 +112,10 @@ cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp,
                         float scale, int accumulate, cudaStream_t s);
 cudaError_t launch_pass_fast(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t,
                              float scale, int accumulate, cudaStream_t s);
+// one fused launch for a whole 2-D filter application on a doubly periodic
+// grid (G_s / B3 of radius 1, 4, 12; L_1); cudaErrorNotSupported otherwise
+cudaError_t launch_filter2_fused(const Params& p, const float* in, float* out, int ncomp, bool laplacian, int s_scale,
+                                 const Taps& t, float scale, int accumulate, cudaStream_t s);
 // per_sm: target blocks per SM (z segments); 0 = built-in default
 cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
                           int accumulate, int per_sm, cudaStream_t s);

@@ -270,9 +270,20 @@ int lbm_eval_qoi(lbm_ctx* ctx, const float* u, double* q);
  * candidate evaluates the same arithmetic.  lbm_set_autotune must precede the
  * first lbm_step; 0 keeps the built-in shapes.  lbm_get_tuning returns
  * [tuned, collide_pair, apply4, march_threads, blocks_per_sm of filter slot
- * 0..7 (0 = default)] (up to count values). */
+ * 0..7 (0 = default), throughput goal] (up to count values). */
 int lbm_set_autotune(lbm_ctx* ctx, int enable);
 int lbm_get_tuning(lbm_ctx* ctx, int32_t* values, int count);
+
+/* Launch goal (default LBM_GOAL_LATENCY): launch shapes that make this
+ * context's step fastest when it has the GPU to itself; for small grids the
+ * fused 3-D filters then split z into many short segments, re-reading 2R halo
+ * planes each.  LBM_GOAL_THROUGHPUT: one z segment per block column, the
+ * least total work, for a context that shares the GPU with many others
+ * (members of an lbm_batch use it).  Results are identical either way.  Must
+ * precede the first lbm_step (LBM_ERR_STATE after it); lbm_get_tuning
+ * reports it as value 12 (1: throughput). */
+enum { LBM_GOAL_LATENCY = 0, LBM_GOAL_THROUGHPUT = 1 };
+int lbm_set_launch_goal(lbm_ctx* ctx, int goal);
 int lbm_profile(lbm_ctx* ctx, int enable);
 int lbm_profile_read(lbm_ctx* ctx, double* ms, int64_t* launches, int count);
 
@@ -328,6 +339,13 @@ int lbm_batch_member(lbm_batch* b, int32_t slot, lbm_ctx** ctx);
 /* Queue up to `steps` more steps of every active member (stopping at each
  * member's horizon).  Asynchronous. */
 int lbm_batch_run(lbm_batch* b, int64_t steps);
+
+/* Flow control for a scheduler: block until at most `rounds` (0..3) of the
+ * most recent lbm_batch_run calls are still executing on any member.
+ * rounds = 1 keeps one call queued behind the running one, so the device is
+ * never drained between calls while the host admits and releases members
+ * (members that were not active in a call do not wait for it). */
+int lbm_batch_wait(lbm_batch* b, int32_t rounds);
 
 /* Members whose horizon has been reached on the device (non-blocking):
  * up to cap completions into out, count in *n.  Each is reported once. */

@@ -32,7 +32,7 @@ EXPORTED = [
     "lbm_qoi_eval_static", "lbm_filter_flops_per_step",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_admit", "lbm_batch_member", "lbm_batch_run",
     "lbm_batch_poll", "lbm_batch_release", "lbm_batch_stats", "lbm_set_autotune", "lbm_get_tuning", "lbm_set_branching",
-    "lbm_project_shape", "lbm_project", "lbm_eval_qoi",
+    "lbm_project_shape", "lbm_project", "lbm_eval_qoi", "lbm_set_launch_goal", "lbm_batch_wait",
 ]
 
 
@@ -100,6 +100,8 @@ def _load():
         "lbm_batch_stats": [VP, P(C.c_size_t), P(C.c_size_t), P(C.c_int32)],
         "lbm_set_autotune": [VP, C.c_int],
         "lbm_set_branching": [VP, C.c_int],
+        "lbm_set_launch_goal": [VP, C.c_int],
+        "lbm_batch_wait": [VP, C.c_int32],
         "lbm_project_shape": [C.POINTER(lbm_config), C.c_int, C.POINTER(C.c_int32)],
         "lbm_project": [VP, C.c_int, VP, VP],
         "lbm_eval_qoi": [VP, VP, VP],
@@ -345,6 +347,10 @@ def lbm_batch_run(b, steps):
     _check(_lib.lbm_batch_run(b, int(steps)))
 
 
+def lbm_batch_wait(b, rounds):
+    _check(_lib.lbm_batch_wait(b, int(rounds)))
+
+
 def lbm_batch_poll(b, cap=256):
     arr = (lbm_completion * cap)()
     n = C.c_int32()
@@ -371,6 +377,13 @@ def lbm_set_branching(ctx, enable):
     _check(_lib.lbm_set_branching(ctx, int(bool(enable))), ctx)
 
 
+GOAL_LATENCY, GOAL_THROUGHPUT = 0, 1
+
+
+def lbm_set_launch_goal(ctx, goal):
+    _check(_lib.lbm_set_launch_goal(ctx, int(goal)), ctx)
+
+
 def lbm_project_shape(cfg, m):
     """LF grid (nx, ny, nz) of the projection phi_m of a configuration."""
     d = (C.c_int32 * 3)()
@@ -389,7 +402,7 @@ def lbm_eval_qoi(ctx, u_ptr, q_ptr):
 
 
 def lbm_get_tuning(ctx):
-    v = (C.c_int32 * 12)()
-    _check(_lib.lbm_get_tuning(ctx, v, 12), ctx)
+    v = (C.c_int32 * 13)()
+    _check(_lib.lbm_get_tuning(ctx, v, 13), ctx)
     return {"tuned": int(v[0]), "collide_pair": int(v[1]), "apply4": int(v[2]), "march_threads": int(v[3]),
-            "filter_blocks_per_sm": [int(v[4 + f]) for f in range(8)]}
+            "filter_blocks_per_sm": [int(v[4 + f]) for f in range(8)], "throughput_goal": int(v[12])}

@@ -540,12 +540,15 @@ __global__ void __launch_bounds__(256) lapf3_kernel(Params p, const float* __res
 }
 
 int seg_len(const Params& p, int blocks_xy, int ncomp, int R, int per_sm) {
-    // enough z segments for `per_sm` blocks per SM; each segment re-reads 2R planes
+    // enough z segments for `per_sm` blocks per SM; each segment re-reads 2R
+    // planes.  Short segments (down to R planes) serve small grids, where the
+    // sequential march of one block, not the halo work, sets the time.
+    if (p.tune.one_seg) return p.nz;  // throughput goal: no halo planes re-read
     const long long want = 148LL * per_sm;
     long long nseg = (want + (long long)blocks_xy * ncomp - 1) / ((long long)blocks_xy * ncomp);
     if (nseg < 1) nseg = 1;
     int seg = (int)((p.nz + nseg - 1) / nseg);
-    if (seg < 4 * R) seg = 4 * R;
+    if (seg < R) seg = R;
     if (seg > p.nz) seg = p.nz;
     return seg;
 }

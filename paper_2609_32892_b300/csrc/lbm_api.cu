@@ -224,6 +224,7 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     p->tune.march_lines = 148 * 2048;
     p->tune.collide_pair = c->substrate == LBM_SUBSTRATE_WALE ? 0 : 1;
     p->tune.apply4 = 1;
+    p->tune.one_seg = 0;
     if (p->h > 0) {
         const long long rows = (long long)(2 * p->h + 1) * p->n_q + 1;
         // about 64 blocks (the solve sums their partials two per lane)
@@ -689,12 +690,13 @@ static void lrs_parts(lbm_ctx* c, void* ptr[4], size_t bytes[4]) {
 #include <tuple>
 
 namespace {
-using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, Tune> g_tune_cache;
 
 TuneKey tune_key(const Params& p) {
-    return TuneKey(p.dim, p.nx, p.ny, p.nz, p.walls, p.storage, p.substrate, p.to_mode != LBM_TO_OFF, p.n_filters);
+    return TuneKey(p.dim, p.nx, p.ny, p.nz, p.walls, p.storage, p.substrate, p.to_mode != LBM_TO_OFF, p.n_filters,
+                   p.tune.one_seg);
 }
 }  // namespace
 
@@ -750,7 +752,7 @@ static int autotune(lbm_ctx* c) {
             p.tune.apply4 = pick;
         }
         const int nc = p.ncomp;
-        if (p.dim == 3) {
+        if (p.dim == 3 && !p.tune.one_seg) {
             static const int cand[] = {2, 4, 8, 16};
             for (size_t f = 0; f < c->filters.size() && f < 8; ++f) {
                 const Filter& fl = c->filters[f];
@@ -770,7 +772,7 @@ static int autotune(lbm_ctx* c) {
                 }
                 p.tune.filter_per_sm[f] = pick;
             }
-        } else {
+        } else if (p.dim == 2) {
             // 2-D: the y-axis march of the first compact filter
             const Filter* fp = nullptr;
             for (const Filter& f : c->filters)
@@ -1278,9 +1280,18 @@ int lbm_set_autotune(lbm_ctx* c, int enable) {
 
 int lbm_get_tuning(lbm_ctx* c, int32_t* values, int count) {
     if (!c || !values) return fail(c, LBM_ERR_ARG, "NULL argument");
-    int32_t v[12] = {c->tuned, c->p.tune.collide_pair, c->p.tune.apply4, c->p.tune.march_lines};
+    int32_t v[13] = {c->tuned, c->p.tune.collide_pair, c->p.tune.apply4, c->p.tune.march_lines};
     for (int f = 0; f < 8; ++f) v[4 + f] = c->p.tune.filter_per_sm[f];
-    for (int k = 0; k < count && k < 12; ++k) values[k] = v[k];
+    v[12] = c->p.tune.one_seg;
+    for (int k = 0; k < count && k < 13; ++k) values[k] = v[k];
+    return LBM_OK;
+}
+
+int lbm_set_launch_goal(lbm_ctx* c, int goal) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    if (goal != LBM_GOAL_LATENCY && goal != LBM_GOAL_THROUGHPUT) return fail(c, LBM_ERR_ARG, "bad launch goal %d", goal);
+    if (c->graph || c->tuned) return fail(c, LBM_ERR_STATE, "lbm_set_launch_goal must precede the first lbm_step");
+    c->p.tune.one_seg = goal == LBM_GOAL_THROUGHPUT ? 1 : 0;
     return LBM_OK;
 }
 

@@ -15,11 +15,15 @@ struct Block {
     size_t off, size;
 };
 
+constexpr int kRounds = 4;  // lbm_batch_run calls whose end each member remembers
+
 struct Member {
     bool used = false;
     lbm_ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t rev[kRounds] = {};      // end of this member's work of run call r (slot r % kRounds)
+    int64_t rround[kRounds] = {-1, -1, -1, -1};
     size_t off = 0, size = 0;
     int64_t horizon = 0, queued = 0;
     uint64_t tag = 0;
@@ -44,7 +48,14 @@ struct lbm_batch {
     std::vector<Block> free_list;  // sorted by offset, coalesced
     std::vector<Member> m;
     cudaEvent_t epoch;
+    int64_t round = 0;  // lbm_batch_run calls so far
 };
+
+static void destroy_member_events(Member& mm) {
+    if (mm.done) cudaEventDestroy(mm.done);
+    for (int k = 0; k < kRounds; ++k)
+        if (mm.rev[k]) cudaEventDestroy(mm.rev[k]);
+}
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -105,7 +116,7 @@ int lbm_batch_release(lbm_batch* b, int32_t slot) {
     Member& mm = b->m[slot];
     if (mm.stream) cudaStreamSynchronize(mm.stream);
     lbm_destroy(mm.ctx);
-    if (mm.done) cudaEventDestroy(mm.done);
+    destroy_member_events(mm);
     if (mm.stream) cudaStreamDestroy(mm.stream);
     pool_free(b, mm.off, mm.size);
     mm = Member();
@@ -139,19 +150,24 @@ int lbm_batch_admit(lbm_batch* b, const lbm_config* cfg, const double* u0, int64
     Member& mm = b->m[s];
     cudaError_t e = cudaStreamCreateWithFlags(&mm.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&mm.done, cudaEventDefault);
+    for (int k = 0; k < kRounds && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&mm.rev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        destroy_member_events(mm);
         if (mm.stream) cudaStreamDestroy(mm.stream);
         pool_free(b, off, need);
         mm = Member();
         return berr(LBM_ERR_CUDA, "lbm_batch_admit: %s", cudaGetErrorString(e));
     }
     rc = lbm_create(cfg, b->pool + off, need, mm.stream, &mm.ctx);
-    // members overlap one another; a per-member branch only adds queue traffic
+    // members overlap one another: a per-member branch only adds queue
+    // traffic, and launch shapes should minimise total work, not one
+    // member's step time
     if (rc == LBM_OK) rc = lbm_set_branching(mm.ctx, 0);
+    if (rc == LBM_OK) rc = lbm_set_launch_goal(mm.ctx, LBM_GOAL_THROUGHPUT);
     if (rc == LBM_OK) rc = lbm_init_macros(mm.ctx, nullptr, u0);
     if (rc != LBM_OK) {
         if (mm.ctx) lbm_destroy(mm.ctx);
-        cudaEventDestroy(mm.done);
+        destroy_member_events(mm);
         cudaStreamDestroy(mm.stream);
         pool_free(b, off, need);
         mm = Member();
@@ -182,11 +198,29 @@ int lbm_batch_run(lbm_batch* b, int64_t steps) {
         const int rc = lbm_step(mm.ctx, n);
         if (rc) return rc;
         mm.queued += n;
+        const int k = (int)(b->round % kRounds);
+        const cudaError_t er = cudaEventRecord(mm.rev[k], mm.stream);
+        if (er != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: %s", cudaGetErrorString(er));
+        mm.rround[k] = b->round;
         if (mm.queued >= mm.horizon && !mm.done_recorded) {
             const cudaError_t e = cudaEventRecord(mm.done, mm.stream);
             if (e != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: %s", cudaGetErrorString(e));
             mm.done_recorded = true;
         }
+    }
+    ++b->round;
+    return LBM_OK;
+}
+
+int lbm_batch_wait(lbm_batch* b, int32_t rounds) {
+    if (!b || rounds < 0 || rounds >= kRounds) return berr(LBM_ERR_ARG, "lbm_batch_wait: rounds must be 0..%d", kRounds - 1);
+    const int64_t target = b->round - 1 - rounds;  // the latest call that must have finished
+    if (target < 0) return LBM_OK;
+    const int k = (int)(target % kRounds);
+    for (Member& mm : b->m) {
+        if (!mm.used || mm.rround[k] != target) continue;  // not active in that call
+        const cudaError_t e = cudaEventSynchronize(mm.rev[k]);
+        if (e != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_wait: %s", cudaGetErrorString(e));
     }
     return LBM_OK;
 }

@@ -76,6 +76,7 @@ struct Tune {
     int march_lines;    // 1-D passes along y/z: target threads in flight (line segments)
     int collide_pair;   // node-pair collide when nx is even
     int apply4;         // 4-node SGS apply when nx % 4 == 0
+    int one_seg;        // fused 3-D filters: one z segment per block column (least total work)
 };
 
 struct Params {

@@ -4,7 +4,8 @@ Requests (LES ensemble members of different grids, seeds and horizons) arrive
 over time.  The server admits a request as soon as a slot and enough pool
 memory are free (first come, first served), queues `chunk` steps of every
 active member per round so that members admitted while others run overlap on
-the device, and collects completions without blocking.  Per request it
+the device, keeps one round queued behind the running one (the device never
+drains between rounds), and collects completions without blocking.  Per request it
 records the queueing delay, the completion time (device clock) and the
 latency per simulated time unit.
 
@@ -93,8 +94,9 @@ class EnsembleServer:
             if active:
                 B.lbm_batch_run(self.batch, chunk)
                 rounds += 1
-                # keep the host at most one round ahead of the device
-                torch.cuda.synchronize(self.pool.device)
+                # keep one round queued behind the running one: the device is
+                # never drained while the host admits and releases members
+                B.lbm_batch_wait(self.batch, 1)
                 for c in B.lbm_batch_poll(self.batch):
                     i = c["tag"]
                     rec = out[i]

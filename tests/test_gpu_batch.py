@@ -139,3 +139,34 @@ def test_serving_mix_members_stay_stable_over_hundreds_of_steps():
     assert np.all(rg[:, -1] == ro[:, -1])
     np.testing.assert_allclose(rg[:, 1:1 + nq], ro[:, 1:1 + nq], rtol=1e-3)
     torch.cuda.synchronize()
+
+
+def test_batch_wait_bounds_rounds_in_flight():
+    """lbm_batch_wait(b, 0) returns once every queued call has finished, so
+    members that reached their horizon are reported by the next poll; out of
+    range round counts are refused."""
+    import torch
+
+    from paper_2609_32892_b300 import binding as B
+
+    wls = [synthetic.workload("C2", nx=40, ny=32, h=3, seed=31), synthetic.workload("C3", nx=20, ny=20, nz=12, h=2, seed=32)]
+    pool_bytes = sum(B.lbm_required_bytes(B.config_from_workload(w)) for w in wls) + (1 << 20)
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
+    b = B.lbm_batch_create(4, pool.data_ptr(), pool_bytes)
+    for i, w in enumerate(wls):
+        s = B.lbm_batch_admit(b, B.config_from_workload(w, member=i), synthetic.initial_velocity(w), 6, i)
+        nq = nq_of(w)
+        c, mu, sig = synthetic.synthetic_lrs(nq, w["h"], w["seed"])
+        B.lbm_set_lrs(B.lbm_batch_member(b, s), c, mu, sig, np.zeros(nq))
+    B.lbm_batch_wait(b, 1)  # nothing queued yet: returns at once
+    for _ in range(2):
+        B.lbm_batch_run(b, 3)
+        B.lbm_batch_wait(b, 1)
+    B.lbm_batch_wait(b, 0)
+    done = B.lbm_batch_poll(b)
+    assert sorted(d["tag"] for d in done) == [0, 1]
+    assert all(d["status"] == 0 and d["steps"] == 6 for d in done)
+    for bad in (-1, 4):
+        with pytest.raises(B.LbmError):
+            B.lbm_batch_wait(b, bad)
+    B.lbm_batch_destroy(b)

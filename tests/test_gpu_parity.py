@@ -190,6 +190,31 @@ def test_branched_step_equals_in_line_step(name, kw):
         np.testing.assert_array_equal(rho_a, rho)
 
 
+@pytest.mark.parametrize("name,kw", [("C3", dict(nx=36, ny=22, nz=40, h=2)), ("C3", dict(nx=19, ny=22, nz=30, h=2))])
+def test_throughput_goal_equals_latency_goal(name, kw):
+    """One z segment per filter block column (the throughput goal) and the
+    autotuned short segments of the latency goal give bit-identical results."""
+    from paper_2609_32892_b300 import LbmSim, binding as B
+
+    wl = synthetic.workload(name, **kw)
+    lrs = lrs_inputs(wl, np.zeros(nq_of(wl)))
+    out = []
+    for goal in (B.GOAL_LATENCY, B.GOAL_THROUGHPUT):
+        g = LbmSim(wl)
+        g.init(synthetic.initial_velocity(wl))
+        g.set_lrs(*lrs)
+        B.lbm_set_launch_goal(g.ctx, goal)
+        g.step(6)
+        g.sync()
+        assert B.lbm_get_tuning(g.ctx)["throughput_goal"] == goal
+        out.append((g.qoi(), g.populations()))
+        with pytest.raises(B.LbmError):
+            B.lbm_set_launch_goal(g.ctx, goal)  # after the first step
+        g.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
 def test_lrs_reference_scales_from_first_step():
     """sigma_ref <= 0 is taken from the first predictor QoIs, on both sides."""
     wl = synthetic.workload("C2", nx=36, ny=30, h=2)

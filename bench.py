@@ -149,7 +149,7 @@ def _lrs_for(wl):
 
 
 def _algorithmic_bytes(wl, n):
-    """Per-class minimal DRAM bytes per launch (roofline)."""
+    """Per-class minimal DRAM bytes per launch: what each kernel must read and write per node."""
     q = 19 if wl["dim"] == 3 else 9
     b = {"fp32": 4, "fp16": 2, "bf16": 2}[wl["storage"]]
     d = wl["dim"]

@@ -357,6 +357,63 @@ def run_serving(args, device):
     return res
 
 
+def run_precision(args, device):
+    """Reduced-precision population storage against FP32 over long runs: the
+    configured 256^2 Kolmogorov LES (Smagorinsky) and 96x40x48 channel LES
+    (WALE), 2e4 steps each in FP32, shifted FP16 and BF16 storage from the
+    same initial field, with every QoI evaluated each step (observe mode: the
+    synthetic LRS coefficients are not a trained model and random-walk over
+    such horizons).  The trajectories decorrelate (the flows are chaotic), so
+    the comparison is statistical: per QoI, the relative difference of the
+    time-means and the two-sample Kolmogorov-Smirnov distance over the second
+    half of the run, next to the same figures for FP32 started from another
+    seeded field (the statistical noise floor).  FP32 itself is pinned to the
+    FP64 oracle by the parity tests."""
+    from scipy.stats import ks_2samp
+
+    from paper_2609_32892_b300 import LbmSim, binding as B
+
+    out = {}
+    for name in ("C2", "C3"):
+        series = {}
+        # fp32_reseeded: FP32 from another seeded initial field, the noise floor
+        # of the statistics (finite, correlated samples of a chaotic flow)
+        for st in ("fp32", "fp16", "bf16", "fp32_reseeded"):
+            base = synthetic.workload(name)
+            wl = synthetic.workload(name, storage=st.split("_")[0], to_mode="observe",
+                                    seed=base["seed"] + (1 if st == "fp32_reseeded" else 0))
+            nq = len(wl["qois"]) + wl["n_mp"]
+            sim = LbmSim(wl, device=device)
+            sim.init(synthetic.initial_velocity(wl))
+            rows, status = [], "stable"
+            try:
+                for _ in range(args.prec_steps // 2000):
+                    sim.step(2000)
+                    sim.sync()
+                    rows.append(sim.qoi())  # drains the device ring (4096 rows)
+            except B.LbmError as e:
+                status = f"unstable after {sum(len(r) for r in rows)} steps: {e}"
+            sim.close()
+            r = np.concatenate(rows) if rows else np.zeros((0, 2 + 3 * nq))
+            series[st] = {"q": r[:, 1:1 + nq], "status": status}
+        res = {"grid": [synthetic.workload(name)[k] for k in ("nx", "ny", "nz")], "to_mode": "observe",
+               "status": {st: series[st]["status"] for st in series}}
+        n = min(series[st]["q"].shape[0] for st in series)
+        res["steps"] = int(n)
+        if n >= 200:
+            half = n // 2
+            ref = series["fp32"]["q"][half:n]
+            for st in ("fp16", "bf16", "fp32_reseeded"):
+                q = series[st]["q"][half:n]
+                mean_rel = np.abs(q.mean(axis=0) - ref.mean(axis=0)) / np.abs(ref.mean(axis=0))
+                ks = [float(ks_2samp(q[:, i], ref[:, i]).statistic) for i in range(ref.shape[1])]
+                res[st] = {"time_mean_rel_diff_max": float(np.max(mean_rel)),
+                           "time_mean_rel_diff_median": float(np.median(mean_rel)),
+                           "ks_max": max(ks), "ks_median": float(np.median(ks))}
+        out[synthetic.workload(name)["name"]] = res
+    return out
+
+
 def run_reference_series(args, device):
     """HF reference trajectories (Sec. 3 projection, reference of Sec. 4.4):
     the HF BGK run at the paper's grids with phi_m and the LF QoIs every m
@@ -468,6 +525,8 @@ def main():
     ap.add_argument("--serve-pool-gb", type=int, default=16)
     ap.add_argument("--serve-chunk", type=int, default=32)
     ap.add_argument("--no-ref", dest="ref", action="store_false")
+    ap.add_argument("--no-precision", dest="precision", action="store_false")
+    ap.add_argument("--prec-steps", type=int, default=20000)
     ap.add_argument("--ref-rows", type=int, default=10)
     args = ap.parse_args()
     world, rank, local = _dist()
@@ -502,6 +561,11 @@ def main():
         import torch
 
         serving = run_serving(args, torch.device("cuda", local))
+    precision = None
+    if args.precision and rank == 0:
+        import torch
+
+        precision = run_precision(args, torch.device("cuda", local))
     reference = None
     if args.ref and rank == 0:
         import torch
@@ -518,7 +582,7 @@ def main():
                 "gpu_launches": int(r["launches"] * args.steps), "clocks": r["clocks"],
                 "step_hbm_gbs": round(r["step_gbs"], 1), "collide_gbs": r["collide_gbs"],
                 "sections": r["sections"], "tuning": r["tuning"], "bgk_480x200x240": r["bgk"], "serving": serving,
-                "hf_reference": reference}
+                "hf_reference": reference, "storage_precision": precision}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

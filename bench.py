@@ -280,7 +280,7 @@ def run_ours(args, world, rank, local):
     if lrs is not None:
         sim.set_lrs(*lrs)
     sim.step(args.steps)
-    rows = sim.qoi()
+    rows, _ = B.lbm_qoi(sim.ctx, sim.row_len, capacity=args.steps + 8)
     B.lbm_sync(sim.ctx)
     t_e2e = time.perf_counter() - t0
     h2d = u0.size * 8 + (sum(a.size * 8 for a in lrs) if lrs is not None else 0)

@@ -7,6 +7,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <memory>
+#include <thread>
 #include <vector>
 
 #include <cufft.h>
@@ -46,6 +48,7 @@ struct lbm_ctx {
     long long launches_per_step;
     double filter_flops[LBM_K_COUNT];  // algorithmic flops per step by kernel class
     float* aux;                // [4][N] scratch for macros / init
+    float* hpin;               // [4][N] pinned host staging for macros / init (on first use)
     size_t elem;               // bytes per stored population
     char err[256];
     // profiling
@@ -803,6 +806,44 @@ tuned:
     return LBM_OK;
 }
 
+// Host-side element loops over whole fields (FP64 <-> FP32 conversion for
+// uploads and downloads) split over up to 16 threads: for a 23 M-node field
+// a single thread spends longer converting than the GPU spends stepping.
+template <typename F>
+static void parallel_for(size_t n, F body) {
+    unsigned t = std::thread::hardware_concurrency();
+    if (t > 16) t = 16;
+    if (t < 2 || n < ((size_t)1 << 20)) {
+        body((size_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    const size_t chunk = (n + t - 1) / t;
+    for (unsigned k = 0; k < t; ++k) {
+        const size_t a = k * chunk, b = a + chunk < n ? a + chunk : n;
+        if (a >= b) break;
+        pool.emplace_back([=] { body(a, b); });
+    }
+    for (std::thread& th : pool) th.join();
+}
+
+// The context's pinned host staging for whole-field transfers ([4][N]
+// floats), allocated on first use for fields of 2^20 nodes or more: a
+// pageable copy of a 23 M-node field runs at a fraction of the DMA rate.
+// Small fields (ensemble members, admitted while others run) keep a
+// temporary pageable buffer, since a pinned allocation may synchronise the
+// device.  Also the fallback if pinned memory is refused.
+static float* host_stage(lbm_ctx* c, std::unique_ptr<float[]>& fallback) {
+    if (!c->hpin && c->p.n >= (1LL << 20)) {
+        void* ptr = nullptr;
+        if (cudaMallocHost(&ptr, sizeof(float) * 4 * (size_t)c->p.n) == cudaSuccess) c->hpin = (float*)ptr;
+        else cudaGetLastError();
+    }
+    if (c->hpin) return c->hpin;
+    fallback.reset(new float[4 * (size_t)c->p.n]);
+    return fallback.get();
+}
+
 // ================================================================== C ABI ==
 extern "C" {
 
@@ -920,6 +961,7 @@ int lbm_destroy(lbm_ctx* c) {
     for (int i = 0; i < 2 * 96; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->hpin) cudaFreeHost(c->hpin);
     if (c->side) {
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
@@ -962,10 +1004,17 @@ static int reset_counters(lbm_ctx* c) {
 int lbm_init_macros(lbm_ctx* c, const double* rho, const double* u) {
     if (!c || !u) return fail(c, LBM_ERR_ARG, "NULL argument");
     const size_t N = (size_t)c->p.n;
-    std::vector<float> h(4 * N);
-    for (size_t i = 0; i < N; ++i) h[i] = rho ? (float)(rho[i] - 1.0) : 0.f;
-    for (size_t i = 0; i < 3 * N; ++i) h[N + i] = (float)u[i];
-    CK(c, cudaMemcpyAsync(c->aux, h.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice, c->stream));
+    std::unique_ptr<float[]> tmp;
+    float* hp = host_stage(c, tmp);  // every element is written below
+    parallel_for(N, [&](size_t a, size_t b) {
+        for (size_t i = a; i < b; ++i) hp[i] = rho ? (float)(rho[i] - 1.0) : 0.f;
+        for (size_t i = a; i < b; ++i) {
+            hp[N + i] = (float)u[i];
+            hp[2 * N + i] = (float)u[N + i];
+            hp[3 * N + i] = (float)u[2 * N + i];
+        }
+    });
+    CK(c, cudaMemcpyAsync(c->aux, hp, sizeof(float) * 4 * N, cudaMemcpyHostToDevice, c->stream));
     c->cur = 0;
     CK(c, launch_init_feq(c->p, c->L, c->aux, c->aux + N, 0, c->stream));
     int rc = reset_counters(c);
@@ -1115,11 +1164,18 @@ int lbm_get_macros(lbm_ctx* c, double* rho, double* u) {
     if (!c || !rho || !u) return fail(c, LBM_ERR_ARG, "NULL argument");
     const size_t N = (size_t)c->p.n;
     CK(c, launch_macros(c->p, c->L, c->cur, c->aux, c->aux + N, c->stream));
-    std::vector<float> h(4 * N);
-    CK(c, cudaMemcpyAsync(h.data(), c->aux, sizeof(float) * 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    std::unique_ptr<float[]> tmp;
+    float* hp = host_stage(c, tmp);
+    CK(c, cudaMemcpyAsync(hp, c->aux, sizeof(float) * 4 * N, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    for (size_t i = 0; i < N; ++i) rho[i] = 1.0 + (double)h[i];
-    for (size_t i = 0; i < 3 * N; ++i) u[i] = (double)h[N + i];
+    parallel_for(N, [&](size_t a, size_t b) {
+        for (size_t i = a; i < b; ++i) {
+            rho[i] = 1.0 + (double)hp[i];
+            u[i] = (double)hp[N + i];
+            u[N + i] = (double)hp[2 * N + i];
+            u[2 * N + i] = (double)hp[3 * N + i];
+        }
+    });
     return LBM_OK;
 }
 

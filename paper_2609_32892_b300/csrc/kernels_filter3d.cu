@@ -579,35 +579,46 @@ cudaError_t run_lap(const Params& p, const float* in, float* out, int ncomp, con
         lap3_kernel<RA, RB><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
     return cudaGetLastError();
 }
-// L_1 (the 13-point cross) with planes staged by asynchronous 16-byte copies
-// three deep (nx % 4 == 0): the register-prefetch version waits on DRAM
-// latency (one plane ahead, long-scoreboard stalls).  One barrier per plane:
-// after it every thread has left the previous plane, whose buffer is refilled.
-namespace cx3 {
+// L_1 (the 13-point cross, arm radius 2) with planes staged by asynchronous
+// 16-byte copies (nx % 4 == 0).  A thread produces the 4 consecutive x outputs
+// of one row from 16-byte shared loads: its row's quads at x - 4 .. x + 7 for
+// the x arm, the output quad of rows y +- 1, y +- 2 for the y arm and of
+// planes z +- 1, z +- 2 for the z arm.  The five planes an output plane reads
+// stay staged in a ring of eight plane buffers (five read, two in flight, one
+// being refilled), so nothing is carried in registers from plane to plane.
+// One barrier per plane: after it every thread has left the previous output
+// plane, the last reader of plane z - 3, whose buffer takes plane z + 5.
+namespace cq3 {
 constexpr int TX = 32, TY = 16, RA = 2, HX = 4, HY = 2;
-constexpr int WP = TX + 2 * HX;  // 40
-constexpr int NQ = WP / 4;       // 10 chunks per row
-constexpr int TH = TY + 2 * HY;  // 20 staged rows
-constexpr int NT = 256, RPT = TY / (NT / TX);
-constexpr int SZ = TH * WP;
-}  // namespace cx3
+constexpr int WP = TX + 2 * HX;    // 40 floats per staged row
+constexpr int NQ = WP / 4;         // 10 chunks per row
+constexpr int TH = TY + 2 * HY;    // 20 staged rows
+constexpr int NT = (TX / 4) * TY;  // 128: one thread per output quad
+constexpr int SZ = TH * WP;        // 800 floats per plane
+constexpr int NB = 8;              // plane buffers (a power of two)
+}  // namespace cq3
 
-__global__ void __launch_bounds__(256) crossa3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(128) crossq3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
                                                       T3<2> arm, float scale, int accumulate, int ncomp, int seg) {
-    constexpr int TX = cx3::TX, TY = cx3::TY, RA = cx3::RA, HX = cx3::HX, HY = cx3::HY, WP = cx3::WP;
-    constexpr int NQ = cx3::NQ, TH = cx3::TH, NT = cx3::NT, RPT = cx3::RPT, SZ = cx3::SZ;
-    constexpr int KZ = 2 * RA + 1;
-    __shared__ __align__(16) float tile[3][SZ];
+    constexpr int TX = cq3::TX, TY = cq3::TY, RA = cq3::RA, HX = cq3::HX, HY = cq3::HY;
+    constexpr int NQ = cq3::NQ, TH = cq3::TH, NT = cq3::NT, SZ = cq3::SZ, NB = cq3::NB;
+    __shared__ __align__(16) float tile[NB][SZ];
     __shared__ int coff[TH * NQ];
     const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
     const int nz = p.nz;
     const int z0 = zs * seg, z1 = min(nz, z0 + seg);
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int lx = threadIdx.x % TX, yr = threadIdx.x / TX;
-    const int x = x0 + lx;
+    const int qx = threadIdx.x & 7, ry = threadIdx.x >> 3;
+    const int gx0 = x0 + 4 * qx, y = y0 + ry;
     const size_t N = (size_t)p.n;
     const float* a = in + c * N;
     float* o = out + c * N;
+    // chunk k: staged row k / NQ <-> y0 - HY + row, columns 4 (k % NQ) .. + 3
+    // <-> x0 - HX + 4 (k % NQ) .. (periodic in x; a chunk never straddles the
+    // period).  Offsets (-1: beyond a wall, zero-filled) are the same for
+    // every plane.
     for (int k = threadIdx.x; k < TH * NQ; k += NT) {
         const int ly = k / NQ, m = k - ly * NQ;
         int gy = y0 - HY + ly;
@@ -618,75 +629,74 @@ __global__ void __launch_bounds__(256) crossa3_kernel(Params p, const float* __r
         coff[k] = ok ? gy * p.nx + gx : -1;
     }
     __syncthreads();
-    auto issue = [&](int q, float* t) {
-        const float* plane = a + (size_t)pm(q, nz) * p.ny * p.nx;
-        for (int k = threadIdx.x; k < TH * NQ; k += NT) {
-            const int ofs = coff[k];
-            cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);
-        }
-    };
-    float rxy[RPT][RA + 1], rz[RPT][KZ];
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-#pragma unroll
-        for (int k = 0; k < RA + 1; ++k) rxy[j][k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < KZ; ++k) rz[j][k] = 0.f;
-    }
-    const int qs = z0 - RA, qe = z1 + RA;
-    issue(qs, tile[0]);
-    cp_async_commit();
-    issue(qs + 1, tile[1]);
-    cp_async_commit();
-    int b = 0;
-    for (int q = qs; q < qe; ++q) {
-        cp_async_wait1();
-        __syncthreads();
-        if (q + 2 < qe) issue(q + 2, tile[b == 0 ? 2 : b - 1]);
-        cp_async_commit();
-        const float* tl = tile[b];
-        const int zo = q - RA;
-#pragma unroll
-        for (int j = 0; j < RPT; ++j) {
-            const int ry = yr * RPT + j + HY;
-            const float* row = tl + ry * WP + lx + HX;
-            const float ctr = row[0];
-            float axy = 2.f * arm.t[RA] * ctr;
-#pragma unroll
-            for (int r = 1; r <= RA; ++r)
-                axy += arm.t[RA + r] * ((row[-r] + row[r]) + (row[-r * WP] + row[r * WP]));
-#pragma unroll
-            for (int k = 0; k < RA; ++k) rxy[j][k] = rxy[j][k + 1];
-            rxy[j][RA] = axy;
-#pragma unroll
-            for (int k = 0; k < KZ - 1; ++k) rz[j][k] = rz[j][k + 1];
-            rz[j][KZ - 1] = ctr;
-            const int y = y0 + yr * RPT + j;
-            if (zo >= z0 && x < p.nx && y < p.ny) {
-                // rxy[k] holds plane q - RA + k, so the current output plane is rxy[0]
-                float v = rxy[j][0] + arm.t[RA] * rz[j][RA];
-#pragma unroll
-                for (int r = 1; r <= RA; ++r) v += arm.t[RA + r] * (rz[j][RA - r] + rz[j][RA + r]);
-                const bool solid = p.walls && (y == 0 || y == p.ny - 1);
-                v = solid ? 0.f : scale * v;
-                float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
-                *op = accumulate ? (*op + v) : v;
+    // plane q (z0 - RA <= q <= z1 + RA - 1) goes to buffer q mod NB; every
+    // call commits one group, empty past the last plane needed
+    auto issue = [&](int q) {
+        if (q < z1 + RA) {
+            float* t = tile[q & (NB - 1)];
+            const float* plane = a + (size_t)pm(q, nz) * p.ny * p.nx;
+            for (int k = threadIdx.x; k < TH * NQ; k += NT) {
+                const int ofs = coff[k];
+                cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);
             }
         }
-        b = b == 2 ? 0 : b + 1;
+        cp_async_commit();
+    };
+    for (int q = z0 - RA; q <= z0 + RA + 2; ++q) issue(q);  // planes z0 - 2 .. z0 + 4
+    const bool live = gx0 < p.nx && y < p.ny;
+    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+    const int rq = (ry + HY) * NQ + qx + 1;  // the output quad in a staged plane
+    for (int zo = z0; zo < z1; ++zo) {
+        cp_async_wait2();  // planes up to zo + 2 have landed (zo + 3, zo + 4 may be in flight)
+        __syncthreads();
+        issue(zo + RA + 3);
+        const float4* t0 = reinterpret_cast<const float4*>(tile[zo & (NB - 1)]);
+        const float4* m1 = reinterpret_cast<const float4*>(tile[(zo - 1) & (NB - 1)]);
+        const float4* p1 = reinterpret_cast<const float4*>(tile[(zo + 1) & (NB - 1)]);
+        const float4* m2 = reinterpret_cast<const float4*>(tile[(zo - 2) & (NB - 1)]);
+        const float4* p2 = reinterpret_cast<const float4*>(tile[(zo + 2) & (NB - 1)]);
+        const float4 xl = t0[rq - 1], xc = t0[rq], xr = t0[rq + 1];
+        const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
+        const float4 a1 = t0[rq - NQ], b1 = t0[rq + NQ], a2 = t0[rq - 2 * NQ], b2 = t0[rq + 2 * NQ];
+        const float ym1[4] = {a1.x, a1.y, a1.z, a1.w}, yp1[4] = {b1.x, b1.y, b1.z, b1.w};
+        const float ym2[4] = {a2.x, a2.y, a2.z, a2.w}, yp2[4] = {b2.x, b2.y, b2.z, b2.w};
+        const float4 c1 = m1[rq], d1 = p1[rq], c2 = m2[rq], d2 = p2[rq];
+        const float zm1[4] = {c1.x, c1.y, c1.z, c1.w}, zp1[4] = {d1.x, d1.y, d1.z, d1.w};
+        const float zm2[4] = {c2.x, c2.y, c2.z, c2.w}, zp2[4] = {d2.x, d2.y, d2.z, d2.w};
+        float res[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float ctr = v[4 + j];
+            float axy = 2.f * arm.t[RA] * ctr;
+            axy += arm.t[RA + 1] * ((v[3 + j] + v[5 + j]) + (ym1[j] + yp1[j]));
+            axy += arm.t[RA + 2] * ((v[2 + j] + v[6 + j]) + (ym2[j] + yp2[j]));
+            float w = axy + arm.t[RA] * ctr;
+            w += arm.t[RA + 1] * (zm1[j] + zp1[j]);
+            w += arm.t[RA + 2] * (zm2[j] + zp2[j]);
+            res[j] = solid ? 0.f : scale * w;
+        }
+        if (live) {
+            float4* op = reinterpret_cast<float4*>(o + ((size_t)zo * p.ny + y) * p.nx + gx0);
+            float4 w = make_float4(res[0], res[1], res[2], res[3]);
+            if (accumulate) {
+                const float4 old = *op;
+                w.x += old.x; w.y += old.y; w.z += old.z; w.w += old.w;
+            }
+            *op = w;
+        }
     }
     cp_async_wait0();
 }
 
 // L_1 with asynchronously staged planes; needs nx % 4 == 0
-cudaError_t run_crossa3(const Params& p, const float* in, float* out, int ncomp, const Taps& arm, float scale, int acc,
+cudaError_t run_crossq3(const Params& p, const float* in, float* out, int ncomp, const Taps& arm, float scale, int acc,
                         int per_sm, cudaStream_t s) {
     T3<2> tp;
     for (int i = 0; i < 5; ++i) tp.t[i] = arm.t[i];
-    const int bx = (p.nx + cx3::TX - 1) / cx3::TX, by = (p.ny + cx3::TY - 1) / cx3::TY;
-    const int seg = seg_len(p, bx * by, ncomp, 2, per_sm > 0 ? per_sm : 4);
+    const int bx = (p.nx + cq3::TX - 1) / cq3::TX, by = (p.ny + cq3::TY - 1) / cq3::TY;
+    const int seg = seg_len(p, bx * by, ncomp, 2, per_sm > 0 ? per_sm : 8);
     const int nseg = (p.nz + seg - 1) / seg;
-    crossa3_kernel<<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+    crossq3_kernel<<<dim3(bx, by, ncomp * nseg), cq3::NT, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
     return cudaGetLastError();
 }
 
@@ -717,7 +727,7 @@ cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncom
 cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp, int s_scale, const Taps& arm,
                         float scale, int accumulate, int per_sm, cudaStream_t s) {
     if (s_scale == 1 && arm.radius == 2) {
-        if (p.nx % 4 == 0) return run_crossa3(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
+        if (p.nx % 4 == 0) return run_crossq3(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
         return run_lap<2, 0>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
     }
     if (s_scale == 3 && arm.radius == 7) {

@@ -716,6 +716,40 @@ static void do_init(const Params& p, const Layout& L, const float* drho, const f
     else
         init_feq_kernel<3, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[which], drho, u);
 }
+// moments_kernel for node pairs (nx even): the pair pull of collide2_kernel
+// (aligned 2-element loads, x neighbours by warp shuffle), the same moments,
+// 2-element stores.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(128) moments2_kernel(Params p, const T* __restrict__ src, float* __restrict__ vn,
+                                                       const float* __restrict__ kolmo) {
+    using LT = Lat<DIM>;
+    const long long npair = p.n / 2;
+    long long pi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = pi < npair;
+    if (!live) pi = npair - 1;
+    const int N = (int)p.n;
+    const int n0 = (int)(2 * pi);
+    const int x0 = n0 % p.nx;
+    const int t = n0 / p.nx;
+    const int y = t % p.ny;
+    const int z = t / p.ny;
+    float g0[LT::Q], g1[LT::Q];
+    pull2<DIM, T>(p, src, x0, y, z, n0, g0, g1);
+    if (!live) return;
+    float2* v0 = reinterpret_cast<float2*>(vn + n0);
+    float2* v1 = reinterpret_cast<float2*>(vn + (size_t)N + n0);
+    float2* v2 = reinterpret_cast<float2*>(vn + 2 * (size_t)N + n0);
+    if (p.walls && (y == 0 || y == p.ny - 1)) {
+        *v0 = *v1 = *v2 = make_float2(0.f, 0.f);
+        return;
+    }
+    const Macro a = macros_of<DIM>(p, g0, kolmo, y);
+    const Macro b = macros_of<DIM>(p, g1, kolmo, y);
+    *v0 = make_float2(a.ux, b.ux);
+    *v1 = make_float2(a.uy, b.uy);
+    *v2 = make_float2(a.uz, b.uz);
+}
+
 cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* drho, const float* u, int which,
                             cudaStream_t s) {
     LBM_DISPATCH_STORAGE(p, do_init, p, L, drho, u, which, s);
@@ -724,6 +758,14 @@ cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* drho,
 
 template <typename T>
 static void do_moments(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    if (p.nx % 2 == 0) {
+        const unsigned g2 = grid_of(p.n / 2, 128);
+        if (p.dim == 2)
+            moments2_kernel<2, T><<<g2, 128, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
+        else
+            moments2_kernel<3, T><<<g2, 128, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
+        return;
+    }
     if (p.dim == 2)
         moments_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
     else

@@ -122,14 +122,16 @@ __global__ void __launch_bounds__(128) gauss3_kernel(Params p, const float* __re
         for (int k = 0; k < 2 * R + 1; ++k) ring[j][k] = 0.f;
     LD ld;
     ld.init(p, x0, y0);
-    ld.load(p, a, pm(z0 - R, nz));
+    int zq = pm(z0 - R, nz);  // z index of the plane loaded last (advanced by one per plane)
+    ld.load(p, a, zq);
     // Two barriers per plane: the x factor reads `tile` only before the second
     // barrier and the y factor reads `xt` only before the next plane's first,
     // so the next plane's stores cannot overtake a reader.
     for (int q = z0 - R; q < z1 + R; ++q) {
         ld.store(tile);
         __syncthreads();
-        if (q + 1 < z1 + R) ld.load(p, a, pm(q + 1, nz));
+        zq = zq + 1 == nz ? 0 : zq + 1;
+        if (q + 1 < z1 + R) ld.load(p, a, zq);
         // x factor: task = (tile row, 8-wide segment)
         for (int task = threadIdx.x; task < HH * (TX / 8); task += NT) {
             const int ry = task / (TX / 8), k = task % (TX / 8);
@@ -203,12 +205,14 @@ __global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __rest
     }
     LD ld;
     ld.init(p, x0, y0);
-    ld.load(p, a, pm(z0 - RA, nz));
+    int zq = pm(z0 - RA, nz);  // z index of the plane loaded last (advanced by one per plane)
+    ld.load(p, a, zq);
     int b = 0;
     for (int q = z0 - RA; q < z1 + RA; ++q, b ^= 1) {
         ld.store(tile[b]);
         __syncthreads();
-        if (q + 1 < z1 + RA) ld.load(p, a, pm(q + 1, nz));
+        zq = zq + 1 == nz ? 0 : zq + 1;
+        if (q + 1 < z1 + RA) ld.load(p, a, zq);
         const float* tl = tile[b];
         for (int task = threadIdx.x; task < W * (TY / 4); task += NT) {
             const int cx = task % W, run = task / W;
@@ -312,12 +316,14 @@ __global__ void __launch_bounds__(256) cross3_kernel(Params p, const float* __re
     }
     LD ld;
     ld.init(p, x0, y0);
-    ld.load(p, a, pm(z0 - RA, nz));
+    int zq = pm(z0 - RA, nz);  // z index of the plane loaded last (advanced by one per plane)
+    ld.load(p, a, zq);
     int b = 0;
     for (int q = z0 - RA; q < z1 + RA; ++q, b ^= 1) {
         ld.store(tile[b]);
         __syncthreads();
-        if (q + 1 < z1 + RA) ld.load(p, a, pm(q + 1, nz));
+        zq = zq + 1 == nz ? 0 : zq + 1;
+        if (q + 1 < z1 + RA) ld.load(p, a, zq);
         const float* tl = tile[b];
         const int zo = q - RA;
 #pragma unroll
@@ -491,8 +497,12 @@ __global__ void __launch_bounds__(256) lapf3_kernel(Params p, const float* __res
         coff[k] = ok ? gy * p.nx + gx : -1;
     }
     __syncthreads();
-    auto issue = [&](int q, float* t) {
-        const float* plane = a + (size_t)pm(q, nz) * p.ny * p.nx;
+    // planes are staged in order, so the z index advances by one per call
+    // (a compare instead of a modulo)
+    int zq = pm(z0 - 7, nz);
+    auto issue = [&](float* t) {
+        const float* plane = a + (size_t)zq * p.ny * p.nx;
+        zq = zq + 1 == nz ? 0 : zq + 1;
         for (int k = threadIdx.x; k < TH * NQ; k += NT) {
             const int ofs = coff[k];
             cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);
@@ -513,9 +523,9 @@ __global__ void __launch_bounds__(256) lapf3_kernel(Params p, const float* __res
     const int qs = z0 - 7;
     const int n = (z1 - z0) + 14;
     const int n3 = (n + 2) / 3 * 3;
-    issue(qs, tile[0]);
+    issue(tile[0]);
     cp_async_commit();
-    issue(qs + 1, tile[1]);
+    issue(tile[1]);
     cp_async_commit();
     for (int s = 0; s < n3; s += 3) {
         // plane s + K sits in buffer K (s is a multiple of 3).  After the
@@ -527,7 +537,7 @@ __global__ void __launch_bounds__(256) lapf3_kernel(Params p, const float* __res
             const int q = qs + s + K;                                                                      \
             cp_async_wait1();                                                                              \
             __syncthreads();                                                                               \
-            if (s + K + 2 < n3) issue(q + 2, tile[(K + 2) % 3]);                                           \
+            if (s + K + 2 < n3) issue(tile[(K + 2) % 3]);                                                  \
             cp_async_commit();                                                                             \
             lf3_plane(p, q, z0, z1, y0, gx0, yo, tile[K], bb, RING, y1, y2, o, scale, accumulate);         \
         }
@@ -631,10 +641,12 @@ __global__ void __launch_bounds__(128) crossq3_kernel(Params p, const float* __r
     __syncthreads();
     // plane q (z0 - RA <= q <= z1 + RA - 1) goes to buffer q mod NB; every
     // call commits one group, empty past the last plane needed
+    int zq = pm(z0 - RA, nz);  // z index of the next plane staged (calls come in plane order)
     auto issue = [&](int q) {
         if (q < z1 + RA) {
             float* t = tile[q & (NB - 1)];
-            const float* plane = a + (size_t)pm(q, nz) * p.ny * p.nx;
+            const float* plane = a + (size_t)zq * p.ny * p.nx;
+            zq = zq + 1 == nz ? 0 : zq + 1;
             for (int k = threadIdx.x; k < TH * NQ; k += NT) {
                 const int ofs = coff[k];
                 cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);

@@ -372,13 +372,14 @@ __global__ void __launch_bounds__(256) cross3_kernel(Params p, const float* __re
 // planes in flight (needs nx % 4 == 0).  Zero extension along y with walls,
 // periodic x and z, as above.
 namespace lf3 {
-constexpr int TX = 32, TY = 32;     // output tile
+constexpr int TX = 32, TY = 30;     // output tile (30 rows: the box pass is 504 tasks, two per thread)
 constexpr int HX = 8, HY = 7;       // input halo (x padded to 8 for 16-byte chunks)
 constexpr int WP = TX + 2 * HX;     // 48 floats per staged row
 constexpr int NQ = WP / 4;          // 12 chunks per row
-constexpr int TH = TY + 2 * HY;     // 46 staged rows
-constexpr int BH = TY + 12;         // 44 box rows (outputs +- 6)
-constexpr int NT = 256;             // 8 x-quads x 32 rows
+constexpr int TH = TY + 2 * HY;     // 44 staged rows
+constexpr int BH = TY + 12;         // 42 box rows (outputs +- 6)
+constexpr int NT = 256;             // 8 x-quads x 32 rows, rows 30 and 31 idle after the box pass
+static_assert(BH * NQ <= 2 * NT, "box pass in two rounds");
 constexpr int SZ = TH * WP;
 constexpr int STAGES = 3;
 }  // namespace lf3
@@ -424,7 +425,9 @@ __device__ __forceinline__ void lf3_plane(const Params& p, int q, int z0, int z1
     }
     __syncthreads();
     const int qo = tid & 7;
-    const int row = yo + 6;
+    // threads past the last output row (yo = 30, 31) repeat row 29's work
+    // without storing: one code path for the whole block
+    const int row = min(yo, lf3::TY - 1) + 6;
     const float4* b4 = reinterpret_cast<const float4*>(bb);
     float v[20];  // BB of this row at staged columns 4 qo .. 4 qo + 19 (outputs at + 8 .. + 11)
 #pragma unroll
@@ -454,7 +457,7 @@ __device__ __forceinline__ void lf3_plane(const Params& p, int q, int z0, int z1
     const int zo = q - 7;
     const int y = y0 + yo;
     // nx % 4 == 0: a quad is wholly inside or wholly outside the row
-    if (zo >= z0 && zo < z1 && y < p.ny && gx0 < p.nx) {
+    if (zo >= z0 && zo < z1 && yo < lf3::TY && y < p.ny && gx0 < p.nx) {
         const bool solid = p.walls && (y == 0 || y == p.ny - 1);
         float4* op = reinterpret_cast<float4*>(o + ((size_t)zo * p.ny + y) * p.nx + gx0);
         float4 w = make_float4(solid ? 0.f : scale * res[0], solid ? 0.f : scale * res[1],

@@ -590,12 +590,16 @@ __device__ __forceinline__ void ld4f(const float* p, float* v) {
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 
-template <int DIM, typename T>
+// NS > 0: the number of scale QoIs fixed at compile time, so the sensitivity
+// loop unrolls and every 16-byte field load can be in flight at once (the
+// kernel waits on DRAM latency); NS = 0 reads it from p.n_s.
+template <int DIM, typename T, int NS>
 __global__ void __launch_bounds__(128) apply4_kernel(Params p, T* __restrict__ f, const float* __restrict__ rho,
                                                      const float* __restrict__ vps, VPtrs vk,
                                                      const double* __restrict__ beta,
                                                      const double* __restrict__ w_mp) {
     using LT = Lat<DIM>;
+    const int ns = NS > 0 ? NS : p.n_s;
     const long long n4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n4 >= p.n / 4) return;
     const size_t N = (size_t)p.n;
@@ -603,7 +607,9 @@ __global__ void __launch_bounds__(128) apply4_kernel(Params p, T* __restrict__ f
     const int y = (int)((n0 / p.nx) % p.ny);
     if (p.walls && (y == 0 || y == p.ny - 1)) return;
     float dx[4] = {0.f, 0.f, 0.f, 0.f}, dy[4] = {0.f, 0.f, 0.f, 0.f}, dz[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k = 0; k < p.n_s; ++k) {
+#pragma unroll
+    for (int k = 0; k < (NS > 0 ? NS : kMaxQoi); ++k) {
+        if (NS == 0 && k >= ns) break;
         const float b = (float)beta[k];
         const float* v = vk.v[k];
         float a[4];
@@ -810,6 +816,22 @@ cudaError_t launch_collide(const Params& p, const Layout& L, int src, cudaStream
     return cudaGetLastError();
 }
 
+template <int DIM, typename T>
+static void do_apply4(const Params& p, const Layout& L, T* f, const VPtrs& vk, cudaStream_t s) {
+    const unsigned g = grid_of(p.n / 4, 128);
+#define LBM_APPLY4(NS) apply4_kernel<DIM, T, NS><<<g, 128, 0, s>>>(p, f, L.rho, L.vps, vk, L.beta, L.w_mp)
+    switch (p.n_s) {
+        case 1: LBM_APPLY4(1); break;
+        case 2: LBM_APPLY4(2); break;
+        case 3: LBM_APPLY4(3); break;
+        case 4: LBM_APPLY4(4); break;
+        case 5: LBM_APPLY4(5); break;
+        case 6: LBM_APPLY4(6); break;
+        default: LBM_APPLY4(0); break;
+    }
+#undef LBM_APPLY4
+}
+
 template <typename T>
 static void do_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) {
     VPtrs vk;
@@ -820,9 +842,9 @@ static void do_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) 
     }
     if (p.nx % 4 == 0 && p.tune.apply4) {
         if (p.dim == 2)
-            apply4_kernel<2, T><<<grid_of(p.n / 4, 128), 128, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
+            do_apply4<2, T>(p, L, (T*)L.f[dst], vk, s);
         else
-            apply4_kernel<3, T><<<grid_of(p.n / 4, 128), 128, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
+            do_apply4<3, T>(p, L, (T*)L.f[dst], vk, s);
         return;
     }
     if (p.dim == 2)

@@ -245,6 +245,9 @@ __global__ void __launch_bounds__(256) curl4_kernel(Params p, const float* __res
 // with compensation.  No double-precision arithmetic here: on this GPU an
 // FP64 warp tree over the values of every block costs more than the whole
 // field traversal.
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float lane4(const float4& v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
+
 struct RedPtrs {
     const float* v[kMaxQoi];
 };
@@ -266,19 +269,8 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = 0.f;
     const bool solid = p.walls && (y == 0 || y == p.ny - 1);
-    const int cnt = solid ? 0 : (z1 - z0) * p.nx;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int z = z0 + e / p.nx;
-        const int x = e % p.nx;
-        const size_t n = ((size_t)z * p.ny + y) * p.nx + x;
-        float u[3], w[NS][3];
-        u[0] = vps[n]; u[1] = vps[N + n]; u[2] = d == 3 ? vps[2 * N + n] : 0.f;
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            w[k][0] = vk.v[k][n];
-            w[k][1] = vk.v[k][N + n];
-            w[k][2] = d == 3 ? vk.v[k][2 * N + n] : 0.f;
-        }
+    // one node's contributions from its velocity u and sensitivities w
+    auto add_node = [&](const float (&u)[3], const float (&w)[NS][3]) {
         int idx = 0;
 #pragma unroll
         for (int k = 0; k < NS; ++k) acc[idx++] += u[0] * w[k][0] + u[1] * w[k][1] + u[2] * w[k][2];
@@ -289,6 +281,51 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
         acc[idx++] += u[0];
 #pragma unroll
         for (int k = 0; k < NS; ++k) acc[idx++] += w[k][0];
+    };
+    if (p.nx % 4 == 0) {
+        // four x-consecutive nodes per iteration: 16-byte loads, one index
+        // division per quad
+        const int nq = p.nx >> 2;
+        const int cnt = solid ? 0 : (z1 - z0) * nq;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const int zz = e / nq;
+            const size_t n = ((size_t)(z0 + zz) * p.ny + y) * p.nx + 4 * (e - zz * nq);
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 u0 = ldg4(vps + n), u1 = ldg4(vps + N + n), u2 = d == 3 ? ldg4(vps + 2 * N + n) : zero;
+            float4 w4[NS][3];
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                w4[k][0] = ldg4(vk.v[k] + n);
+                w4[k][1] = ldg4(vk.v[k] + N + n);
+                w4[k][2] = d == 3 ? ldg4(vk.v[k] + 2 * N + n) : zero;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float u[3] = {lane4(u0, c), lane4(u1, c), lane4(u2, c)};
+                float w[NS][3];
+#pragma unroll
+                for (int k = 0; k < NS; ++k)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) w[k][a] = lane4(w4[k][a], c);
+                add_node(u, w);
+            }
+        }
+    } else {
+        const int cnt = solid ? 0 : (z1 - z0) * p.nx;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const int z = z0 + e / p.nx;
+            const int x = e % p.nx;
+            const size_t n = ((size_t)z * p.ny + y) * p.nx + x;
+            float u[3], w[NS][3];
+            u[0] = vps[n]; u[1] = vps[N + n]; u[2] = d == 3 ? vps[2 * N + n] : 0.f;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                w[k][0] = vk.v[k][n];
+                w[k][1] = vk.v[k][N + n];
+                w[k][2] = d == 3 ? vk.v[k][2 * N + n] : 0.f;
+            }
+            add_node(u, w);
+        }
     }
     __shared__ float sh[4][NV];
     __shared__ float tot[NV];

@@ -590,16 +590,15 @@ __device__ __forceinline__ void ld4f(const float* p, float* v) {
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 
-// NS > 0: the number of scale QoIs fixed at compile time, so the sensitivity
-// loop unrolls and every 16-byte field load can be in flight at once (the
-// kernel waits on DRAM latency); NS = 0 reads it from p.n_s.
+// NS: the number of scale QoIs (1-8, = p.n_s) fixed at compile time, so the
+// sensitivity loop unrolls and every 16-byte field load can be in flight at
+// once (the kernel waits on DRAM latency).
 template <int DIM, typename T, int NS>
 __global__ void __launch_bounds__(128) apply4_kernel(Params p, T* __restrict__ f, const float* __restrict__ rho,
                                                      const float* __restrict__ vps, VPtrs vk,
                                                      const double* __restrict__ beta,
                                                      const double* __restrict__ w_mp) {
     using LT = Lat<DIM>;
-    const int ns = NS > 0 ? NS : p.n_s;
     const long long n4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n4 >= p.n / 4) return;
     const size_t N = (size_t)p.n;
@@ -608,8 +607,7 @@ __global__ void __launch_bounds__(128) apply4_kernel(Params p, T* __restrict__ f
     if (p.walls && (y == 0 || y == p.ny - 1)) return;
     float dx[4] = {0.f, 0.f, 0.f, 0.f}, dy[4] = {0.f, 0.f, 0.f, 0.f}, dz[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < (NS > 0 ? NS : kMaxQoi); ++k) {
-        if (NS == 0 && k >= ns) break;
+    for (int k = 0; k < NS; ++k) {
         const float b = (float)beta[k];
         const float* v = vk.v[k];
         float a[4];
@@ -817,7 +815,7 @@ cudaError_t launch_collide(const Params& p, const Layout& L, int src, cudaStream
 }
 
 template <int DIM, typename T>
-static void do_apply4(const Params& p, const Layout& L, T* f, const VPtrs& vk, cudaStream_t s) {
+static bool do_apply4(const Params& p, const Layout& L, T* f, const VPtrs& vk, cudaStream_t s) {
     const unsigned g = grid_of(p.n / 4, 128);
 #define LBM_APPLY4(NS) apply4_kernel<DIM, T, NS><<<g, 128, 0, s>>>(p, f, L.rho, L.vps, vk, L.beta, L.w_mp)
     switch (p.n_s) {
@@ -827,9 +825,12 @@ static void do_apply4(const Params& p, const Layout& L, T* f, const VPtrs& vk, c
         case 4: LBM_APPLY4(4); break;
         case 5: LBM_APPLY4(5); break;
         case 6: LBM_APPLY4(6); break;
-        default: LBM_APPLY4(0); break;
+        case 7: LBM_APPLY4(7); break;
+        case 8: LBM_APPLY4(8); break;
+        default: return false;  // the configuration allows at most 8 scale QoIs
     }
 #undef LBM_APPLY4
+    return true;
 }
 
 template <typename T>
@@ -841,11 +842,8 @@ static void do_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) 
         vk.v[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
     }
     if (p.nx % 4 == 0 && p.tune.apply4) {
-        if (p.dim == 2)
-            do_apply4<2, T>(p, L, (T*)L.f[dst], vk, s);
-        else
-            do_apply4<3, T>(p, L, (T*)L.f[dst], vk, s);
-        return;
+        if (p.dim == 2 ? do_apply4<2, T>(p, L, (T*)L.f[dst], vk, s) : do_apply4<3, T>(p, L, (T*)L.f[dst], vk, s))
+            return;
     }
     if (p.dim == 2)
         apply_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);

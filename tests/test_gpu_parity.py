@@ -102,6 +102,21 @@ def test_channel_wale_lrs_3d(nx):
     _compare_rows(wl, rg, ro)
 
 
+def test_maximum_qoi_set_3d():
+    """The largest QoI set a context takes: 8 scale-aware QoIs (E and Z of
+    G_3, L_3, L_1 and the binomial B3) plus the 6 mean-profile bands, 14 in
+    all, TO-LRS with h = 2 on a 36 x 22 x 13 channel for 5 steps (nx % 4 = 0:
+    the four-node apply and reduction at their largest unrolled counts)."""
+    qois = list(synthetic.workloads.SCALE_QOIS_3D) + [("E", "B", 1), ("Z", "B", 1)]
+    wl = synthetic.workload("C3", nx=36, ny=22, nz=13, h=2, qois=qois)
+    assert nq_of(wl) == 14
+    lrs = lrs_inputs(wl, oracle_sigma_ref(wl, 2))
+    _, ro, rho_o, u_o = run_oracle(wl, 5, lrs=lrs)
+    _, rg, rho_g, u_g = run_gpu(wl, 5, lrs=lrs)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)
+
+
 @pytest.mark.parametrize("nx", [33, 68])
 def test_channel_bgk_3d_long(nx):
     """Plain BGK channel (the 480x200x240 workload's physics) on nx x 18 x 11,

@@ -245,7 +245,6 @@ __global__ void __launch_bounds__(256) curl4_kernel(Params p, const float* __res
 // with compensation.  No double-precision arithmetic here: on this GPU an
 // FP64 warp tree over the values of every block costs more than the whole
 // field traversal.
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float lane4(const float4& v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
 
 struct RedPtrs {
@@ -291,13 +290,13 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
             const int zz = e / nq;
             const size_t n = ((size_t)(z0 + zz) * p.ny + y) * p.nx + 4 * (e - zz * nq);
             const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 u0 = ldg4(vps + n), u1 = ldg4(vps + N + n), u2 = d == 3 ? ldg4(vps + 2 * N + n) : zero;
+            const float4 u0 = ld4(vps + n), u1 = ld4(vps + N + n), u2 = d == 3 ? ld4(vps + 2 * N + n) : zero;
             float4 w4[NS][3];
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
-                w4[k][0] = ldg4(vk.v[k] + n);
-                w4[k][1] = ldg4(vk.v[k] + N + n);
-                w4[k][2] = d == 3 ? ldg4(vk.v[k] + 2 * N + n) : zero;
+                w4[k][0] = ld4(vk.v[k] + n);
+                w4[k][1] = ld4(vk.v[k] + N + n);
+                w4[k][2] = d == 3 ? ld4(vk.v[k] + 2 * N + n) : zero;
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {

@@ -49,16 +49,16 @@ def _peaks():
     return 6400.0, "fallback"
 
 
-# DRAM traffic of the fused Laplacian-filter launches (lapf3_kernel, the
-# factorised L_3, and crossq3_kernel, the L_1 cross: the dominant kernel class),
-# from one ncu capture on the 320x200x160 channel
+# DRAM traffic of the Laplacian-filter launches (box3_kernel + cross3s_kernel,
+# the two passes of L_3, and crossq3_kernel, the L_1 cross: the dominant kernel
+# class), from one ncu capture on the 320x200x160 channel
 # (profiles/filters_channel3d_320x200x160.md): read+write bytes per launch
 # averaged over the class (two launches of each per step), per lattice node.  It
 # is reported only while the kernel source still has the hash it had when
 # captured.
 TRAFFIC = {
-    "lap3": {"bytes_per_node": (494.563776 + 462.223488) / 2 * 1e6 / (320 * 200 * 160),
-             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "b24b45acf0b21271"},
+    "lap3": {"bytes_per_node": (459.428608 + 522.394176 + 462.292352) / 3 * 1e6 / (320 * 200 * 160),
+             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "64495484a745ea28"},
 }
 
 

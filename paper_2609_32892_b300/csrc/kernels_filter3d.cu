@@ -13,7 +13,13 @@
 //   gauss3_kernel<R>      G_s (or B3): the same (2R+1)-tap factor on x, y, z
 //   lap3_kernel<RA, RB>   L_s = c sum_a [l dilated along a] x [box_s on the
 //                         other two axes], arm radius RA = (5s-1)/2, box
-//                         radius RB = (s-1)/2 (RB = 0: the box is the identity)
+//                         radius RB = (s-1)/2 (RB = 0: the box is the identity;
+//                         cross3_kernel<RA>); used when nx % 4 != 0
+//
+// With nx % 4 == 0 the Laplacian class has its own kernels, one thread per
+// output quad with 16-byte accesses: crossq3_kernel (L_1, planes staged by
+// asynchronous copies and kept in a ring) and, for L_3, box3_kernel followed
+// by cross3s_kernel (the 3 x 3 x 3 box, then the cross at stride 3).
 //
 // Periodic along x and z; along y with walls the halo outside the array reads
 // zero (solid rows already hold zero), and outputs on solid rows are zero, so
@@ -356,34 +362,7 @@ __global__ void __launch_bounds__(256) cross3_kernel(Params p, const float* __re
     }
 }
 
-// L_3 factorised.  L_s is L_1 dilated by the Kronecker product with the s^3
-// block of ones, so L_s = c B_s * C_s: B_s the s x s x s box and C_s the cross
-// of l = [1, -4, 6, -4, 1] at stride s along every axis (centre 3 x 6).  For
-// s = 3 that is a 27-point box and a 13-point cross instead of the 3 x 21
-// taps of the separable-sum form.  Per input plane q:
-//   BB(q) = B_x B_y x(q) on the output tile +- 6 (one shared-memory pass),
-//   XY(q) = (l_x + l_y)(BB(q)) at the outputs (centre 12, arms at +-3, +-6),
-//   Y(p)  = XY(p) + l_z(BB)(p) with p = q - 6 (BB of planes p, p +- 3, p +- 6),
-//   out(q - 7) = Y(q - 8) + Y(q - 7) + Y(q - 6) (the box along z).
-// The planes p +- 3, p +- 6 share p's residue mod 3, so the z rings are kept
-// per residue class and the plane loop is unrolled by three: a plane shifts
-// only its own class's ring.  A thread produces 4 consecutive x outputs of
-// one row.  Input planes are staged by asynchronous 16-byte copies, three
-// planes in flight (needs nx % 4 == 0).  Zero extension along y with walls,
-// periodic x and z, as above.
-namespace lf3 {
-constexpr int TX = 32, TY = 30;     // output tile (30 rows: the box pass is 504 tasks, two per thread)
-constexpr int HX = 8, HY = 7;       // input halo (x padded to 8 for 16-byte chunks)
-constexpr int WP = TX + 2 * HX;     // 48 floats per staged row
-constexpr int NQ = WP / 4;          // 12 chunks per row
-constexpr int TH = TY + 2 * HY;     // 44 staged rows
-constexpr int BH = TY + 12;         // 42 box rows (outputs +- 6)
-constexpr int NT = 256;             // 8 x-quads x 32 rows, rows 30 and 31 idle after the box pass
-static_assert(BH * NQ <= 2 * NT, "box pass in two rounds");
-constexpr int SZ = TH * WP;
-constexpr int STAGES = 3;
-}  // namespace lf3
-
+// asynchronous 16-byte global -> shared copies (zero-fill when src_bytes = 0)
 __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, int src_bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
@@ -391,166 +370,6 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, int s
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-struct Lf3Ring {
-    float bb[4][4];  // BB of planes q-12, q-9, q-6, q-3 of this residue class, per output
-    float xy[2][4];  // XY of planes q-6, q-3
-};
-
-__device__ __forceinline__ float4 add3(float4 a, float4 b, float4 c) {
-    return make_float4(a.x + b.x + c.x, a.y + b.y + c.y, a.z + b.z + c.z, a.w + b.w + c.w);
-}
-
-// one plane: the box (after the staged tile is complete), a barrier, then the
-// arms, the z rings and this thread's 4 outputs of plane q - 7
-__device__ __forceinline__ void lf3_plane(const Params& p, int q, int z0, int z1, int y0, int gx0, int yo,
-                                          const float* __restrict__ tl, float* __restrict__ bb, Lf3Ring& rg,
-                                          float (&y1)[4], float (&y2)[4], float* __restrict__ o, float scale,
-                                          int accumulate) {
-    constexpr int NQ = lf3::NQ, BH = lf3::BH, NT = lf3::NT;
-    const int tid = threadIdx.x;
-    // BB row r <-> y = y0 - 6 + r (staged rows r .. r + 2); quad qx covers
-    // staged columns 4 qx .. 4 qx + 3 and needs columns 4 qx - 1 .. 4 qx + 4.
-    // Whole neighbour quads are read: conflict-free 16-byte shared loads.
-    const float4* t4 = reinterpret_cast<const float4*>(tl);
-    for (int task = tid; task < BH * NQ; task += NT) {
-        const int r = task / NQ, qx = task - r * NQ;
-        const float4* row = t4 + r * NQ + qx;
-        const float4 c = add3(row[0], row[NQ], row[2 * NQ]);
-        float l = 0.f, rr = 0.f;
-        if (qx > 0) l = row[-1].w + row[NQ - 1].w + row[2 * NQ - 1].w;
-        if (qx < NQ - 1) rr = row[1].x + row[NQ + 1].x + row[2 * NQ + 1].x;
-        reinterpret_cast<float4*>(bb)[r * NQ + qx] =
-            make_float4(l + c.x + c.y, c.x + c.y + c.z, c.y + c.z + c.w, c.z + c.w + rr);
-    }
-    __syncthreads();
-    const int qo = tid & 7;
-    // threads past the last output row (yo = 30, 31) repeat row 29's work
-    // without storing: one code path for the whole block
-    const int row = min(yo, lf3::TY - 1) + 6;
-    const float4* b4 = reinterpret_cast<const float4*>(bb);
-    float v[20];  // BB of this row at staged columns 4 qo .. 4 qo + 19 (outputs at + 8 .. + 11)
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        const float4 w = b4[row * NQ + qo + m];
-        v[4 * m] = w.x; v[4 * m + 1] = w.y; v[4 * m + 2] = w.z; v[4 * m + 3] = w.w;
-    }
-    const float4 m6 = b4[(row - 6) * NQ + qo + 2], m3 = b4[(row - 3) * NQ + qo + 2];
-    const float4 p3 = b4[(row + 3) * NQ + qo + 2], p6 = b4[(row + 6) * NQ + qo + 2];
-    const float ym6[4] = {m6.x, m6.y, m6.z, m6.w}, ym3[4] = {m3.x, m3.y, m3.z, m3.w};
-    const float yp3[4] = {p3.x, p3.y, p3.z, p3.w}, yp6[4] = {p6.x, p6.y, p6.z, p6.w};
-    float res[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float c = v[8 + j];
-        const float a3 = (v[5 + j] + v[11 + j]) + (ym3[j] + yp3[j]);
-        const float a6 = (v[2 + j] + v[14 + j]) + (ym6[j] + yp6[j]);
-        const float xy = fmaf(12.f, c, fmaf(-4.f, a3, a6));
-        // Y(q - 6) = XY(q - 6) + l_z(BB)(q - 6) over planes q - 12 .. q
-        const float yz = rg.xy[0][j] + fmaf(6.f, rg.bb[2][j], fmaf(-4.f, rg.bb[1][j] + rg.bb[3][j], rg.bb[0][j] + c));
-        res[j] = (y1[j] + y2[j]) + yz;  // box along z: the output of plane q - 7
-        y1[j] = y2[j];
-        y2[j] = yz;
-        rg.bb[0][j] = rg.bb[1][j]; rg.bb[1][j] = rg.bb[2][j]; rg.bb[2][j] = rg.bb[3][j]; rg.bb[3][j] = c;
-        rg.xy[0][j] = rg.xy[1][j]; rg.xy[1][j] = xy;
-    }
-    const int zo = q - 7;
-    const int y = y0 + yo;
-    // nx % 4 == 0: a quad is wholly inside or wholly outside the row
-    if (zo >= z0 && zo < z1 && yo < lf3::TY && y < p.ny && gx0 < p.nx) {
-        const bool solid = p.walls && (y == 0 || y == p.ny - 1);
-        float4* op = reinterpret_cast<float4*>(o + ((size_t)zo * p.ny + y) * p.nx + gx0);
-        float4 w = make_float4(solid ? 0.f : scale * res[0], solid ? 0.f : scale * res[1],
-                               solid ? 0.f : scale * res[2], solid ? 0.f : scale * res[3]);
-        if (accumulate) {
-            const float4 old = *op;
-            w.x += old.x; w.y += old.y; w.z += old.z; w.w += old.w;
-        }
-        *op = w;
-    }
-}
-
-__global__ void __launch_bounds__(256) lapf3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                    float scale, int accumulate, int ncomp, int seg) {
-    constexpr int TX = lf3::TX, TY = lf3::TY, HX = lf3::HX, HY = lf3::HY, NQ = lf3::NQ, TH = lf3::TH;
-    constexpr int NT = lf3::NT, SZ = lf3::SZ;
-    __shared__ __align__(16) float tile[lf3::STAGES][SZ];
-    __shared__ __align__(16) float bb[lf3::BH * lf3::WP];
-    __shared__ int coff[TH * NQ];
-    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
-    const int nz = p.nz;
-    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const size_t N = (size_t)p.n;
-    const float* a = in + c * N;
-    float* o = out + c * N;
-    const int yo = threadIdx.x >> 3;
-    const int gx0 = x0 + 4 * (threadIdx.x & 7);
-    // chunk k of a staged plane: row k / NQ <-> y0 - HY + row, columns
-    // 4 (k % NQ) .. + 3 <-> x0 - HX + 4 (k % NQ) .. (periodic in x; with
-    // nx % 4 == 0 a chunk never straddles the period).  The in-plane offsets
-    // (-1: beyond a wall, zero-filled) are the same for every plane.
-    for (int k = threadIdx.x; k < TH * NQ; k += NT) {
-        const int ly = k / NQ, m = k - ly * NQ;
-        int gy = y0 - HY + ly;
-        const int gx = pm(x0 - HX + 4 * m, p.nx);
-        bool ok = true;
-        if (p.walls) ok = gy >= 0 && gy < p.ny;
-        else gy = pm(gy, p.ny);
-        coff[k] = ok ? gy * p.nx + gx : -1;
-    }
-    __syncthreads();
-    // planes are staged in order, so the z index advances by one per call
-    // (a compare instead of a modulo)
-    int zq = pm(z0 - 7, nz);
-    auto issue = [&](float* t) {
-        const float* plane = a + (size_t)zq * p.ny * p.nx;
-        zq = zq + 1 == nz ? 0 : zq + 1;
-        for (int k = threadIdx.x; k < TH * NQ; k += NT) {
-            const int ofs = coff[k];
-            cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);
-        }
-    };
-    Lf3Ring ra, rb, rc;
-    float y1[4], y2[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        y1[j] = y2[j] = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) ra.bb[m][j] = rb.bb[m][j] = rc.bb[m][j] = 0.f;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) ra.xy[m][j] = rb.xy[m][j] = rc.xy[m][j] = 0.f;
-    }
-    // planes z0 - 7 .. z1 + 6 (output z = q - 7 needs planes up to z + 7),
-    // padded to a multiple of three; the extra planes only skip their stores
-    const int qs = z0 - 7;
-    const int n = (z1 - z0) + 14;
-    const int n3 = (n + 2) / 3 * 3;
-    issue(tile[0]);
-    cp_async_commit();
-    issue(tile[1]);
-    cp_async_commit();
-    for (int s = 0; s < n3; s += 3) {
-        // plane s + K sits in buffer K (s is a multiple of 3).  After the
-        // barrier every thread has left the previous plane's arms (bb may be
-        // rewritten) and its box pass (buffer K + 2 mod 3, which held the
-        // previous plane, may be refilled).
-#define LF3_STEP(K, RING)                                                                                  \
-        {                                                                                                  \
-            const int q = qs + s + K;                                                                      \
-            cp_async_wait1();                                                                              \
-            __syncthreads();                                                                               \
-            if (s + K + 2 < n3) issue(tile[(K + 2) % 3]);                                                  \
-            cp_async_commit();                                                                             \
-            lf3_plane(p, q, z0, z1, y0, gx0, yo, tile[K], bb, RING, y1, y2, o, scale, accumulate);         \
-        }
-        LF3_STEP(0, ra)
-        LF3_STEP(1, rb)
-        LF3_STEP(2, rc)
-#undef LF3_STEP
-    }
-    cp_async_wait0();
-}
 
 int seg_len(const Params& p, int blocks_xy, int ncomp, int R, int per_sm) {
     // enough z segments for `per_sm` blocks per SM; each segment re-reads 2R
@@ -715,16 +534,209 @@ cudaError_t run_crossq3(const Params& p, const float* in, float* out, int ncomp,
     return cudaGetLastError();
 }
 
-// L_3 by the factorised kernel (box * dilated cross); needs nx % 4 == 0
-cudaError_t run_lapf3(const Params& p, const float* in, float* out, int ncomp, float scale, int acc, int per_sm,
-                      cudaStream_t s) {
-    const int bx = (p.nx + lf3::TX - 1) / lf3::TX, by = (p.ny + lf3::TY - 1) / lf3::TY;
-    const int seg = seg_len(p, bx * by, ncomp, 7, per_sm > 0 ? per_sm : 4);
+// L_3 in two passes (nx % 4 == 0).  L_s is L_1 dilated by the Kronecker
+// product with the s^3 block of ones, so L_s = c C_s * B_s: B_s the s x s x s
+// box and C_s the cross of l = [1, -4, 6, -4, 1] at stride s along every axis
+// (centre 3 x 6).  For s = 3 that is a 27-point box and a 13-point cross
+// instead of the 3 x 21 taps of the separable-sum form (lap3_kernel<7, 1>).
+// The box B = B_3 x is written to a scratch field, then the cross is applied
+// to B.  B is computed on every row of the array, solid rows included
+// (B at a solid row holds the box of its fluid neighbours); beyond the array B
+// is zero because the solid rows of x are, so the cross reads B with zero
+// extension and zeroes its solid output rows: P K P exactly, as the fused
+// kernel.  Both passes are plain streams over the field (48 B per node each).
+namespace bx3 {
+constexpr int TX = 32, TY = 16, NT = 128;  // 8 x-quads x 16 rows
+}  // namespace bx3
+
+// B = B_3 x: a thread owns one output quad (4 x-consecutive nodes) of a row
+// and marches along its z segment, keeping the in-plane box of the planes
+// z - 1 and z in registers; rows y +- 1 come through L1, planes through L2.
+__global__ void __launch_bounds__(128) box3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                   int ncomp, int seg) {
+    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
+    const int x = blockIdx.x * bx3::TX + 4 * (threadIdx.x & 7);
+    const int y = blockIdx.y * bx3::TY + (threadIdx.x >> 3);
+    if (x >= nx || y >= ny || z0 >= z1) return;
+    const size_t N = (size_t)p.n, plane_n = (size_t)ny * nx;
+    const float* a = in + c * N;
+    float* o = out + c * N;
+    // the three source rows (-1: beyond a wall, reads zero)
+    int rows[3] = {y - 1, y, y + 1};
+    if (p.walls) {
+        if (rows[0] < 0) rows[0] = -1;
+        if (rows[2] >= ny) rows[2] = -1;
+    } else {
+        rows[0] = rows[0] < 0 ? ny - 1 : rows[0];
+        rows[2] = rows[2] >= ny ? 0 : rows[2];
+    }
+    const int xl = x == 0 ? nx - 1 : x - 1, xr = x + 4 == nx ? 0 : x + 4;
+    // in-plane box of plane zq at this quad: column sums over the rows, then
+    // the x box of the column sums
+    auto box2 = [&](int zq) {
+        const float* pl = a + (size_t)zq * plane_n;
+        float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+        float ls = 0.f, hs = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            if (rows[r] < 0) continue;
+            const float* row = pl + (size_t)rows[r] * nx;
+            const float4 m = __ldg(reinterpret_cast<const float4*>(row + x));
+            cs.x += m.x; cs.y += m.y; cs.z += m.z; cs.w += m.w;
+            ls += __ldg(row + xl);
+            hs += __ldg(row + xr);
+        }
+        return make_float4(ls + cs.x + cs.y, cs.x + cs.y + cs.z, cs.y + cs.z + cs.w, cs.z + cs.w + hs);
+    };
+    int zq = pm(z0 - 1, nz);
+    float4 bm = box2(zq);
+    zq = zq + 1 == nz ? 0 : zq + 1;
+    float4 b0 = box2(zq);
+    for (int z = z0; z < z1; ++z) {
+        zq = zq + 1 == nz ? 0 : zq + 1;
+        const float4 bp = box2(zq);
+        *reinterpret_cast<float4*>(o + (size_t)z * plane_n + (size_t)y * nx + x) =
+            make_float4(bm.x + b0.x + bp.x, bm.y + b0.y + bp.y, bm.z + b0.z + bp.z, bm.w + b0.w + bp.w);
+        bm = b0;
+        b0 = bp;
+    }
+}
+
+// out = c C_3 B: the 13-point cross of l = (1, -4, 6, -4, 1) at stride 3.  One
+// thread per output quad: the x and y arms from the output plane staged in
+// shared memory by 16-byte asynchronous copies (two planes in flight), the z
+// arm (planes z +- 3, z +- 6) by 16-byte loads that L2 serves (every plane
+// is staged by this block within six planes of its use as a z neighbour).
+namespace cs3 {
+constexpr int TX = 32, TY = 16, HX = 8, HY = 6;
+constexpr int WP = TX + 2 * HX;    // 48 floats per staged row
+constexpr int NQ = WP / 4;         // 12 chunks per row
+constexpr int TH = TY + 2 * HY;    // 28 staged rows
+constexpr int NT = (TX / 4) * TY;  // 128: one thread per output quad
+constexpr int SZ = TH * WP;
+}  // namespace cs3
+
+__device__ __forceinline__ int wrapz(int v, int n) {
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
+}
+
+__global__ void __launch_bounds__(128) cross3s_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                      float scale, int accumulate, int ncomp, int seg) {
+    constexpr int TX = cs3::TX, TY = cs3::TY, HX = cs3::HX, HY = cs3::HY;
+    constexpr int NQ = cs3::NQ, TH = cs3::TH, NT = cs3::NT, SZ = cs3::SZ;
+    __shared__ __align__(16) float tile[3][SZ];
+    __shared__ int coff[TH * NQ];
+    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int nz = p.nz;
+    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int qx = threadIdx.x & 7, ry = threadIdx.x >> 3;
+    const int gx0 = x0 + 4 * qx, y = y0 + ry;
+    const size_t N = (size_t)p.n, plane_n = (size_t)p.ny * p.nx;
+    const float* a = in + c * N;
+    float* o = out + c * N;
+    // chunk k: staged row k / NQ <-> y0 - HY + row, columns 4 (k % NQ) .. + 3
+    // <-> x0 - HX + 4 (k % NQ) ..; -1 beyond a wall (zero-filled)
+    for (int k = threadIdx.x; k < TH * NQ; k += NT) {
+        const int ly = k / NQ, m = k - ly * NQ;
+        int gy = y0 - HY + ly;
+        const int gx = pm(x0 - HX + 4 * m, p.nx);
+        bool ok = true;
+        if (p.walls) ok = gy >= 0 && gy < p.ny;
+        else gy = pm(gy, p.ny);
+        coff[k] = ok ? gy * p.nx + gx : -1;
+    }
+    __syncthreads();
+    int zq = z0;  // z index of the next plane staged (planes z0 .. z1 - 1, in order)
+    auto issue = [&](float* t) {
+        const float* plane = a + (size_t)zq * plane_n;
+        ++zq;
+        for (int k = threadIdx.x; k < TH * NQ; k += NT) {
+            const int ofs = coff[k];
+            cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);
+        }
+    };
+    const bool live = gx0 < p.nx && y < p.ny;
+    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
+    const size_t col = live ? (size_t)y * p.nx + gx0 : 0;  // this quad within a plane
+    const int rq = (ry + HY) * NQ + qx + 2;                 // the output quad in a staged plane
+    if (z0 < z1) issue(tile[0]);
+    cp_async_commit();
+    if (z0 + 1 < z1) issue(tile[1]);
+    cp_async_commit();
+    int b = 0;
+    for (int zo = z0; zo < z1; ++zo) {
+        // z arm first: its L2 latency overlaps the wait for the staged plane
+        float4 zm6 = make_float4(0.f, 0.f, 0.f, 0.f), zm3 = zm6, zp3 = zm6, zp6 = zm6;
+        if (live) {
+            zm6 = __ldg(reinterpret_cast<const float4*>(a + (size_t)wrapz(zo - 6, nz) * plane_n + col));
+            zm3 = __ldg(reinterpret_cast<const float4*>(a + (size_t)wrapz(zo - 3, nz) * plane_n + col));
+            zp3 = __ldg(reinterpret_cast<const float4*>(a + (size_t)wrapz(zo + 3, nz) * plane_n + col));
+            zp6 = __ldg(reinterpret_cast<const float4*>(a + (size_t)wrapz(zo + 6, nz) * plane_n + col));
+        }
+        cp_async_wait1();
+        __syncthreads();
+        if (zo + 2 < z1) issue(tile[b == 0 ? 2 : b - 1]);
+        cp_async_commit();
+        const float4* t4 = reinterpret_cast<const float4*>(tile[b]);
+        // staged columns 4 qx .. 4 qx + 19; the outputs sit at + 8 .. + 11
+        float v[20];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const float4 w = t4[rq - 2 + m];
+            v[4 * m] = w.x; v[4 * m + 1] = w.y; v[4 * m + 2] = w.z; v[4 * m + 3] = w.w;
+        }
+        const float4 ym6 = t4[rq - 6 * NQ], ym3 = t4[rq - 3 * NQ], yp3 = t4[rq + 3 * NQ], yp6 = t4[rq + 6 * NQ];
+        const float am6[4] = {ym6.x, ym6.y, ym6.z, ym6.w}, am3[4] = {ym3.x, ym3.y, ym3.z, ym3.w};
+        const float ap3[4] = {yp3.x, yp3.y, yp3.z, yp3.w}, ap6[4] = {yp6.x, yp6.y, yp6.z, yp6.w};
+        const float bm6[4] = {zm6.x, zm6.y, zm6.z, zm6.w}, bm3[4] = {zm3.x, zm3.y, zm3.z, zm3.w};
+        const float bp3[4] = {zp3.x, zp3.y, zp3.z, zp3.w}, bp6[4] = {zp6.x, zp6.y, zp6.z, zp6.w};
+        float res[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float ctr = v[8 + j];
+            const float a3 = (v[5 + j] + v[11 + j]) + (am3[j] + ap3[j]) + (bm3[j] + bp3[j]);
+            const float a6 = (v[2 + j] + v[14 + j]) + (am6[j] + ap6[j]) + (bm6[j] + bp6[j]);
+            const float w = fmaf(18.f, ctr, fmaf(-4.f, a3, a6));
+            res[j] = solid ? 0.f : scale * w;
+        }
+        if (live) {
+            float4* op = reinterpret_cast<float4*>(o + (size_t)zo * plane_n + col);
+            float4 w = make_float4(res[0], res[1], res[2], res[3]);
+            if (accumulate) {
+                const float4 old = *op;
+                w.x += old.x; w.y += old.y; w.z += old.z; w.w += old.w;
+            }
+            *op = w;
+        }
+        b = b == 2 ? 0 : b + 1;
+    }
+    cp_async_wait0();
+}
+
+}  // namespace
+
+// L_3 in two passes when nx % 4 == 0 (the caller launches box, then cross)
+bool lap3_split(const Params& p, int s_scale) { return s_scale == 3 && p.nx % 4 == 0; }
+cudaError_t launch_box3(const Params& p, const float* in, float* out, int ncomp, int per_sm, cudaStream_t s) {
+    const int bx = (p.nx + bx3::TX - 1) / bx3::TX, by = (p.ny + bx3::TY - 1) / bx3::TY;
+    const int seg = seg_len(p, bx * by, ncomp, 1, per_sm > 0 ? per_sm : 8);
     const int nseg = (p.nz + seg - 1) / seg;
-    lapf3_kernel<<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, scale, acc, ncomp, seg);
+    box3_kernel<<<dim3(bx, by, ncomp * nseg), bx3::NT, 0, s>>>(p, in, out, ncomp, seg);
     return cudaGetLastError();
 }
-}  // namespace
+cudaError_t launch_cross3s(const Params& p, const float* in, float* out, int ncomp, float scale, int accumulate,
+                           int per_sm, cudaStream_t s) {
+    const int bx = (p.nx + cs3::TX - 1) / cs3::TX, by = (p.ny + cs3::TY - 1) / cs3::TY;
+    const int seg = seg_len(p, bx * by, ncomp, 1, per_sm > 0 ? per_sm : 8);
+    const int nseg = (p.nz + seg - 1) / seg;
+    cross3s_kernel<<<dim3(bx, by, ncomp * nseg), cs3::NT, 0, s>>>(p, in, out, scale, accumulate, ncomp, seg);
+    return cudaGetLastError();
+}
 
 // G_s / B3 in 3-D with the same 1-D taps on every axis.
 cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
@@ -745,10 +757,8 @@ cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp,
         if (p.nx % 4 == 0) return run_crossq3(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
         return run_lap<2, 0>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
     }
-    if (s_scale == 3 && arm.radius == 7) {
-        if (p.nx % 4 == 0) return run_lapf3(p, in, out, ncomp, scale, accumulate, per_sm, s);
-        return run_lap<7, 1>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
-    }
+    // L_3 with nx % 4 == 0 goes through lap3_split (box, then cross)
+    if (s_scale == 3 && arm.radius == 7) return run_lap<7, 1>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
     return cudaErrorNotSupported;
 }
 

@@ -439,6 +439,13 @@ static void enqueue_filter(Launcher& lc, const Filter& f, int slot, const float*
         } else if (launch_lap3_supported(f.scale)) {
             const float scale = (float)(1.0 / (8.0 * d * (double)f.scale * f.scale * f.scale));
             if (lc.count_only) c->filter_flops[LBM_K_LAP3] += flops;
+            if (lap3_split(p, f.scale)) {
+                // L_3 = c C_3 * B_3 in two streams over the field: the box into
+                // the scratch field, then the cross at stride 3
+                LAUNCH(lc, LBM_K_LAP3, launch_box3(p, in, t1, nc, p.tune.filter_per_sm[slot], lc.s));
+                LAUNCH(lc, LBM_K_LAP3, launch_cross3s(p, t1, out, nc, scale, 0, p.tune.filter_per_sm[slot], lc.s));
+                return;
+            }
             LAUNCH(lc, LBM_K_LAP3,
                    launch_lap3(p, in, out, nc, f.scale, ell_taps(f.scale), scale, 0, p.tune.filter_per_sm[slot], lc.s));
             return;
@@ -768,8 +775,13 @@ static int autotune(lbm_ctx* c) {
                 int pick = 0;
                 for (int v : cand) {
                     const float t = time_ms(c, [&] {
-                        chk(lap ? launch_lap3(p, c->L.x6, c->L.acc, nc, fl.scale, t0, 1.f, 0, v, c->stream)
-                                : launch_gauss3(p, c->L.x6, c->L.acc, nc, t0, 1.f, 0, v, c->stream));
+                        if (lap && lap3_split(p, fl.scale)) {
+                            chk(launch_box3(p, c->L.x6, c->L.t1, nc, v, c->stream));
+                            chk(launch_cross3s(p, c->L.t1, c->L.acc, nc, 1.f, 0, v, c->stream));
+                        } else {
+                            chk(lap ? launch_lap3(p, c->L.x6, c->L.acc, nc, fl.scale, t0, 1.f, 0, v, c->stream)
+                                    : launch_gauss3(p, c->L.x6, c->L.acc, nc, t0, 1.f, 0, v, c->stream));
+                        }
                     }, 5);
                     if (t < best) { best = t; pick = v; }
                 }

@@ -124,6 +124,11 @@ cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp,
                         float scale, int accumulate, int per_sm, cudaStream_t s);
 inline bool launch_gauss3_supported(int radius) { return radius == 1 || radius == 2 || radius == 4 || radius == 6; }
 inline bool launch_lap3_supported(int s_scale) { return s_scale == 1 || s_scale == 3; }
+// L_3 as two launches through a scratch field (box, then cross at stride 3)
+bool lap3_split(const Params& p, int s_scale);
+cudaError_t launch_box3(const Params& p, const float* in, float* out, int ncomp, int per_sm, cudaStream_t s);
+cudaError_t launch_cross3s(const Params& p, const float* in, float* out, int ncomp, float scale, int accumulate,
+                           int per_sm, cudaStream_t s);
 cudaError_t launch_band_mask(const Params& p, const float2* in, float2* out, int ncomp, int lo, int hi,
                              cudaStream_t s);
 cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s);

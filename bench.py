@@ -57,8 +57,8 @@ def _peaks():
 # is reported only while the kernel source still has the hash it had when
 # captured.
 TRAFFIC = {
-    "lap3": {"bytes_per_node": (459.428608 + 522.394176 + 462.292352) / 3 * 1e6 / (320 * 200 * 160),
-             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "64495484a745ea28"},
+    "lap3": {"bytes_per_node": (461.013696 + 522.231168 + 462.320256) / 3 * 1e6 / (320 * 200 * 160),
+             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "170718aa4413ea34"},
 }
 
 

@@ -594,13 +594,23 @@ __global__ void __launch_bounds__(128) box3_kernel(Params p, const float* __rest
     float4 bm = box2(zq);
     zq = zq + 1 == nz ? 0 : zq + 1;
     float4 b0 = box2(zq);
-    for (int z = z0; z < z1; ++z) {
-        zq = zq + 1 == nz ? 0 : zq + 1;
-        const float4 bp = box2(zq);
-        *reinterpret_cast<float4*>(o + (size_t)z * plane_n + (size_t)y * nx + x) =
+    // two output planes per iteration: the loads of planes z + 1 and z + 2
+    // are independent, so a thread has 18 in flight (the kernel waits on
+    // memory latency); with an odd segment the last plane z + 2 is read but
+    // not used
+    float* oq = o + (size_t)y * nx + x;
+    for (int z = z0; z < z1; z += 2) {
+        const int z1q = zq + 1 == nz ? 0 : zq + 1;
+        const int z2q = z1q + 1 == nz ? 0 : z1q + 1;
+        const float4 bp = box2(z1q), bq = box2(z2q);
+        *reinterpret_cast<float4*>(oq + (size_t)z * plane_n) =
             make_float4(bm.x + b0.x + bp.x, bm.y + b0.y + bp.y, bm.z + b0.z + bp.z, bm.w + b0.w + bp.w);
-        bm = b0;
-        b0 = bp;
+        if (z + 1 < z1)
+            *reinterpret_cast<float4*>(oq + (size_t)(z + 1) * plane_n) =
+                make_float4(b0.x + bp.x + bq.x, b0.y + bp.y + bq.y, b0.z + bp.z + bq.z, b0.w + bp.w + bq.w);
+        bm = bp;
+        b0 = bq;
+        zq = z2q;
     }
 }
 

@@ -42,6 +42,52 @@ def test_laplacian_kernel_hand_values():
     assert abs(c[0, 0] / k3[6, 0] - 12.0) < 1e-12  # centre vs outer arm tip value 1
 
 
+def _shift_zero_y(a, r, walls):
+    """b(z, y, x) = a(z - rz, y - ry, x - rx): np.roll along x and z, and along
+    y either np.roll (periodic) or a zero-padded slice (walls)."""
+    rx, ry, rz = r
+    b = np.roll(a, shift=(rz, rx), axis=(0, 2))
+    if not walls:
+        return np.roll(b, ry, axis=1)
+    ny = a.shape[1]
+    p = np.pad(b, ((0, 0), (abs(ry), abs(ry)), (0, 0)))
+    return p[:, abs(ry) - ry: abs(ry) - ry + ny, :]
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_laplacian_l3_is_box_then_strided_cross(walls):
+    """Eq. laplace: L_3 is L_1 dilated by the 3^3 block of ones, so it equals
+    c C_3 * B_3, the 27-point box followed by the 13-point cross of
+    l = [1, -4, 6, -4, 1] at stride 3, with c = 2 / (27 * 48) from sum |L_3| = 2.
+    Applied with zero extension beyond the walls, the box must also be taken
+    on the solid rows (whose input is zero but whose box is not) for the two
+    passes to give the dense kernel's P K P on Omega."""
+    rng = np.random.default_rng(5)
+    shape = (13, 17, 15)
+    mask = np.ones(shape)
+    if walls:
+        mask[:, 0, :] = 0.0
+        mask[:, -1, :] = 0.0
+    a = rng.standard_normal(shape) * mask
+    dense = filters.apply_kernel(a, filters.laplacian_kernel(3, 3), mask, walls)
+    box = sum(_shift_zero_y(a, (dx, dy, dz), walls) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1))
+    cross = 18.0 * box
+    for e in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+        for k, w in ((3, -4.0), (6, 1.0)):
+            cross = cross + w * (_shift_zero_y(box, tuple(k * c for c in e), walls)
+                                 + _shift_zero_y(box, tuple(-k * c for c in e), walls))
+    np.testing.assert_allclose(cross * mask / (27.0 * 48.0) * 2.0, dense, rtol=0, atol=1e-13)
+    if walls:
+        # dropping the solid rows' box changes the rows within 6 of a wall
+        cut = _shift_zero_y(box * mask, (0, 0, 0), walls)
+        wrong = 18.0 * cut
+        for e in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+            for k, w in ((3, -4.0), (6, 1.0)):
+                wrong = wrong + w * (_shift_zero_y(cut, tuple(k * c for c in e), walls)
+                                     + _shift_zero_y(cut, tuple(-k * c for c in e), walls))
+        assert np.abs(wrong * mask / 648.0 - dense).max() > 1e-3
+
+
 def _mode(shape, kvec):
     nz, ny, nx = shape
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")

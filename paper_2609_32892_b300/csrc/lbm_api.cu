@@ -1389,7 +1389,7 @@ int lbm_project_shape(const lbm_config* cfg, int m, int32_t* lf) {
 
 int lbm_project(lbm_ctx* c, int m, float* drho, float* u) {
     if (!c || !drho || !u) return fail(c, LBM_ERR_ARG, "NULL argument");
-    int32_t d[3];
+    int32_t d[3] = {0, 0, 0};
     const int rc = lf_dims(&c->cfg, m, d);
     if (rc != LBM_OK) return fail(c, rc, "%s", g_err);
     CK(c, launch_project(c->p, c->L, c->cur, m, d[0], d[1], d[2], drho, u, c->stream));

@@ -214,7 +214,7 @@ enum {
     LBM_K_MOMENTS = 0, LBM_K_COLLIDE = 1, LBM_K_CURL = 2, LBM_K_FILTER = 3, LBM_K_SENS = 4,
     LBM_K_REDUCE = 5, LBM_K_LRS = 6, LBM_K_SOLVE = 7, LBM_K_APPLY = 8,
     LBM_K_GAUSS3 = 9,  /* fused 3-D Gaussian / binomial filter applications */
-    LBM_K_LAP3 = 10,   /* fused 3-D Laplacian filter applications           */
+    LBM_K_LAP3 = 10,   /* 3-D Laplacian filters: L_1 one launch, L_3 two    */
     LBM_K_FFT = 11,    /* cuFFT transforms of the Fourier-band filters      */
     LBM_K_COUNT = 12
 };

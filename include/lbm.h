@@ -71,7 +71,9 @@ enum {
     LBM_TO_OBSERVE = 1,  /* QoIs and Gram on the predictor, no forcing (dQ = 0)      */
     LBM_TO_GAMMA = 2,    /* gamma_i = gamma_std * z_i, z Philox normals per step     */
     LBM_TO_LRS = 3,      /* online TO-LRS: dQ = LRS(q_h) - q^{n*} (Eq. LRS)         */
-    LBM_TO_TRACK = 4     /* dQ = Q_ref(t^n) - q^{n*} (Eq. dQ-from-ref)              */
+    LBM_TO_TRACK = 4,    /* dQ = Q_ref(t^n) - q^{n*} (Eq. dQ-from-ref)              */
+    LBM_TO_FIXED_GAMMA = 5  /* gamma_i given by the caller (lbm_set_to_coeffs), held
+                               for every step; dQ_i = gamma_i sum V_i . O_i          */
 };
 
 #define LBM_MAX_QOI 16   /* scale-aware QoIs + mean-profile bands */
@@ -162,6 +164,25 @@ int lbm_init_macros(lbm_ctx* ctx, const double* rho, const double* u);
  * Only valid for LBM_TO_LRS.  Synchronous. */
 int lbm_set_lrs(lbm_ctx* ctx, const double* C, const double* mu, const double* Sigma,
                 const double* sigma_ref, const double* q_hist, const double* qs_hist);
+
+/* Coefficient source of the TO forcing in one call (Sec. 4.3-4.4: the
+ * coefficients gamma_i of Eq. TO-ansatz, from Eq. tau-from-dQ).
+ *   mode        must equal cfg.to_mode of the context (ERR_STATE otherwise):
+ *               the device arrays of each source are placed at lbm_create
+ *   h           LRS history length; must equal cfg.h for LBM_TO_LRS, else ignored
+ *   C, mu, Sigma, sigma_ref   LBM_TO_LRS only, as in lbm_set_lrs (zero initial
+ *               histories); NULL for the other modes
+ *   gamma_fixed [N] host FP64, N = n_qoi + n_mp: LBM_TO_FIXED_GAMMA only
+ *               (required there, finite); every step then applies
+ *               dv_SGS = sum_i gamma_i O_i and reports dQ_i = gamma_i sum V_i . O_i
+ * LBM_TO_OFF, LBM_TO_OBSERVE, LBM_TO_GAMMA (gamma_std * Philox normals) and
+ * LBM_TO_TRACK (lbm_set_track_reference) take no coefficients here: the call
+ * only checks the mode.  Synchronous.  A context in LBM_TO_LRS or
+ * LBM_TO_FIXED_GAMMA refuses lbm_step (ERR_STATE) until its coefficients are set.
+ * Errors: ERR_ARG (NULL or invalid array, h mismatch, Sigma not SPD),
+ * ERR_STATE (mode mismatch), ERR_CUDA. */
+int lbm_set_to_coeffs(lbm_ctx* ctx, int mode, int32_t h, const double* C, const double* mu, const double* Sigma,
+                      const double* sigma_ref, const double* gamma_fixed);
 
 /* Reference QoI series for LBM_TO_TRACK (or the spin-up of LBM_TO_LRS):
  * qref[len][N], row n used at step n (len <= cfg.track_len; steps past the

@@ -13,7 +13,7 @@ State between steps: the post-collision populations f^p of the last step
      f^eq(v + F/rho) - f^eq(v) (Eq. LES-2 without the SGS term), or Guo;
   5. v^{p,n*} = sum_i c_i f^{p*}_i / rho: the predictor;
   6. QoIs q^{n*}, sensitivities V_j and the Gram matrix on v^{p,n*};
-  7. dQ from the coefficient source (random gamma, LRS, tracking);
+  7. dQ from the coefficient source (random gamma, fixed gamma, LRS, tracking);
   8. c_ij, gamma_i, dv_SGS (Sec. 4.2-4.3);
   9. f^p = f^{p*} + f^eq(rho, v^{p*} + dv_SGS) - f^eq(rho, v^{p*}), which
      telescopes with step 4 to the single-difference form of Eq. LES-2.
@@ -32,11 +32,11 @@ from .philox import STREAM_GAMMA, STREAM_LRS, normals
 FLAG_SINGULAR = 1
 FLAG_UNSTABLE = 2
 
-MODES = ("off", "observe", "gamma", "lrs", "track")
+MODES = ("off", "observe", "gamma", "fixed", "lrs", "track")
 
 
 class Simulation:
-    def __init__(self, wl, u0, rho0=None, lrs=None, track_ref=None, member=0):
+    def __init__(self, wl, u0, rho0=None, lrs=None, track_ref=None, member=0, gamma_fixed=None):
         self.wl = dict(wl)
         self.dim = wl["dim"]
         self.nx, self.ny, self.nz = wl["nx"], wl["ny"], wl["nz"]
@@ -64,6 +64,8 @@ class Simulation:
             hist = lrs[4:] if len(lrs) > 4 else (None, None)
             self.lrs = LRSModel(c, mu, sigma, sigma_ref, wl["h"], *hist)
         self.track_ref = None if track_ref is None else np.asarray(track_ref, dtype=np.float64)
+        # 'fixed': the caller's coefficients gamma_i, held for every step
+        self.gamma_fixed = None if gamma_fixed is None else np.asarray(gamma_fixed, dtype=np.float64)
         self.n = 0
         self.profile_sum = np.zeros(self.ny)
         y = np.arange(self.ny, dtype=np.float64)
@@ -134,6 +136,12 @@ class Simulation:
                 z = np.array(normals(self.seed, self.member, self.n, STREAM_GAMMA, nq))
                 if not singular:
                     gamma = self.wl["gamma_std"] * z
+                    dq = gamma * den
+            elif self.mode == "fixed":
+                # gamma_i given (Eq. TO-ansatz with fixed coefficients): the
+                # change it makes in Q_i is dQ_i = gamma_i sum V_i . O_i
+                if not singular:
+                    gamma = self.gamma_fixed.copy()
                     dq = gamma * den
             elif self.mode == "lrs" and self.n < self.wl.get("spinup", 0):
                 # spin-up of an online run: nudged to the reference series

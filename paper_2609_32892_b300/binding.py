@@ -20,13 +20,13 @@ SUBSTRATE = {"none": 0, "smag": 1, "wale": 2}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 QOI_KIND = {"E": 0, "Z": 1}
 FILTER = {"G": 0, "L": 1, "B": 2, "F": 3}
-TO_MODE = {"off": 0, "observe": 1, "gamma": 2, "lrs": 3, "track": 4}
+TO_MODE = {"off": 0, "observe": 1, "gamma": 2, "lrs": 3, "track": 4, "fixed": 5}
 MAX_QOI = 16
 FLAG_SINGULAR, FLAG_UNSTABLE = 1, 2
 K_NAMES = ["moments", "collide", "curl", "filter", "sens", "reduce", "lrs", "solve", "apply", "gauss3", "lap3", "fft"]
 EXPORTED = [
     "lbm_qoi_row_len", "lbm_required_bytes", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_macros",
-    "lbm_set_lrs", "lbm_set_track_reference", "lbm_step", "lbm_sync", "lbm_qoi", "lbm_get_macros",
+    "lbm_set_lrs", "lbm_set_to_coeffs", "lbm_set_track_reference", "lbm_step", "lbm_sync", "lbm_qoi", "lbm_get_macros",
     "lbm_get_populations", "lbm_set_populations", "lbm_get_profile", "lbm_get_step", "lbm_state_bytes",
     "lbm_save", "lbm_load", "lbm_set_graphs", "lbm_profile", "lbm_profile_read", "lbm_launches_per_step",
     "lbm_qoi_eval_static", "lbm_filter_flops_per_step",
@@ -72,6 +72,7 @@ def _load():
         "lbm_last_error": [VP, C.c_char_p, C.c_size_t],
         "lbm_init_macros": [VP, PD, PD],
         "lbm_set_lrs": [VP, PD, PD, PD, PD, PD, PD],
+        "lbm_set_to_coeffs": [VP, C.c_int, C.c_int32, PD, PD, PD, PD, PD],
         "lbm_set_track_reference": [VP, PD, I64],
         "lbm_step": [VP, I64],
         "lbm_sync": [VP],
@@ -209,6 +210,13 @@ def lbm_init_macros(ctx, rho, u):
 def lbm_set_lrs(ctx, c_mat, mu, sigma, sigma_ref, q_hist=None, qs_hist=None):
     a = [_f64(x) for x in (c_mat, mu, sigma, sigma_ref, q_hist, qs_hist)]
     _check(_lib.lbm_set_lrs(ctx, *[_ptr(x) for x in a]), ctx)
+
+
+def lbm_set_to_coeffs(ctx, mode, h=0, c_mat=None, mu=None, sigma=None, sigma_ref=None, gamma_fixed=None):
+    """mode: a TO_MODE name or value (must be the context's configured mode)."""
+    m = TO_MODE[mode] if isinstance(mode, str) else int(mode)
+    a = [_f64(x) for x in (c_mat, mu, sigma, sigma_ref, gamma_fixed)]
+    _check(_lib.lbm_set_to_coeffs(ctx, m, int(h), *[_ptr(x) for x in a]), ctx)
 
 
 def lbm_set_track_reference(ctx, qref):

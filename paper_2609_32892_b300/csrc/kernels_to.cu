@@ -723,6 +723,11 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L
                 g = p.gamma_std * L.znorm[i];
                 d = g / gii;
             }
+        } else if (p.to_mode == LBM_TO_FIXED_GAMMA) {
+            if (!sing) {
+                g = L.gfix[i];
+                d = g / gii;
+            }
         } else if (p.to_mode == LBM_TO_TRACK) {
             const long long row = step < p.track_len ? step : p.track_len - 1;
             d = L.track[(size_t)row * nq + i] - q[i];

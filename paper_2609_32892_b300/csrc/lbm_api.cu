@@ -58,6 +58,7 @@ struct lbm_ctx {
     double prof_ms[LBM_K_COUNT];
     long long prof_n[LBM_K_COUNT];
     int lrs_set;
+    int fixed_set;    // LBM_TO_FIXED_GAMMA: gamma_i given
     int autotune;     // tune launch shapes before the first step (default on)
     int branch;       // LRS history / normals on a parallel branch of the step (default on)
     int tuned;
@@ -101,7 +102,7 @@ static int validate(const lbm_config* c) {
     if (c->forcing != LBM_FORCING_EDM && c->forcing != LBM_FORCING_GUO) return fail(nullptr, LBM_ERR_ARG, "bad forcing");
     if (c->substrate < 0 || c->substrate > 2) return fail(nullptr, LBM_ERR_ARG, "bad substrate");
     if (c->storage < 0 || c->storage > 2) return fail(nullptr, LBM_ERR_ARG, "bad storage");
-    if (c->to_mode < 0 || c->to_mode > 4) return fail(nullptr, LBM_ERR_ARG, "bad to_mode");
+    if (c->to_mode < 0 || c->to_mode > 5) return fail(nullptr, LBM_ERR_ARG, "bad to_mode");
     const long long n = (long long)c->nx * c->ny * c->nz;
     // populations are addressed with 64-bit offsets (Q N may exceed 2^31, e.g. the
     // 171 M-node HF channel); node indices and the per-component offsets of the
@@ -311,6 +312,7 @@ static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filt
             l.fft_work = cv.take<char>(fft_work_bytes(p));
         }
         l.beta = cv.take<double>(kMaxQoi);
+        if (p.to_mode == LBM_TO_FIXED_GAMMA) l.gfix = cv.take<double>(kMaxQoi);
         l.ring = cv.take<double>((size_t)p.ring_cap * p.row_len);
         l.profile = cv.take<double>(p.ny);
     }
@@ -657,6 +659,25 @@ static void widen(const std::vector<char>& raw, int dim, int q, size_t N, double
         for (size_t n = 0; n < N; ++n) f[(size_t)i * N + n] = lat_w(dim, i) + (double)to_f<T>(g[(size_t)i * N + n]);
 }
 
+// coefficient-source arrays in blob order: the LRS model (C, mu, chol(Sigma),
+// sigma_ref) or the fixed gamma_i; unused entries have zero bytes
+static void coef_parts(lbm_ctx* c, void* ptr[4], size_t bytes[4]) {
+    const Params& p = c->p;
+    const size_t nq = (size_t)p.n_q;
+    for (int k = 0; k < 4; ++k) {
+        ptr[k] = nullptr;
+        bytes[k] = 0;
+    }
+    if (p.h > 0) {
+        ptr[0] = c->L.lrs_C;     bytes[0] = sizeof(double) * ((size_t)(2 * p.h + 1) * nq + 1) * nq;
+        ptr[1] = c->L.lrs_mu;    bytes[1] = sizeof(double) * nq;
+        ptr[2] = c->L.lrs_L;     bytes[2] = sizeof(double) * nq * nq;
+        ptr[3] = c->L.lrs_sigma; bytes[3] = sizeof(double) * nq;
+    } else if (p.to_mode == LBM_TO_FIXED_GAMMA) {
+        ptr[0] = c->L.gfix;      bytes[0] = sizeof(double) * nq;
+    }
+}
+
 // checkpoint blob: magic, sizes, DevState, populations, histories, ring, profile, cursor
 struct BlobHead {
     uint64_t magic, fbytes, hbytes, rbytes, pbytes, cbytes, tbytes;
@@ -671,22 +692,14 @@ static void blob_sizes(lbm_ctx* c, BlobHead* h) {
     h->hbytes = p.h > 0 ? sizeof(double) * (size_t)p.h * p.n_q : 0;
     h->rbytes = c->L.ring ? sizeof(double) * (size_t)p.ring_cap * p.row_len : 0;
     h->pbytes = c->L.profile ? sizeof(double) * (size_t)p.ny : 0;
-    // LRS model: C, mu, chol(Sigma), sigma_ref (possibly set from the first step)
-    h->cbytes = p.h > 0 ? sizeof(double) * (((size_t)(2 * p.h + 1) * p.n_q + 1) * p.n_q + 2 * (size_t)p.n_q +
-                                            (size_t)p.n_q * p.n_q)
-                        : 0;
+    // coefficient source: the LRS model (C, mu, chol(Sigma), sigma_ref, the last
+    // possibly set from the first step) or the fixed gamma_i
+    void* ptr[4];
+    size_t nb[4];
+    coef_parts(c, ptr, nb);
+    h->cbytes = nb[0] + nb[1] + nb[2] + nb[3];
     h->tbytes = p.track_len > 0 ? sizeof(double) * (size_t)p.track_len * p.n_q : 0;
     h->host_read = c->host_read;
-}
-
-// LRS arrays in blob order
-static void lrs_parts(lbm_ctx* c, void* ptr[4], size_t bytes[4]) {
-    const Params& p = c->p;
-    const size_t nq = (size_t)p.n_q;
-    ptr[0] = c->L.lrs_C;     bytes[0] = sizeof(double) * ((size_t)(2 * p.h + 1) * nq + 1) * nq;
-    ptr[1] = c->L.lrs_mu;    bytes[1] = sizeof(double) * nq;
-    ptr[2] = c->L.lrs_L;     bytes[2] = sizeof(double) * nq * nq;
-    ptr[3] = c->L.lrs_sigma; bytes[3] = sizeof(double) * nq;
 }
 
 // ------------------------------------------------------------- autotuner --
@@ -1087,6 +1100,28 @@ int lbm_set_lrs(lbm_ctx* c, const double* C, const double* mu, const double* Sig
     return sync_check(c);
 }
 
+int lbm_set_to_coeffs(lbm_ctx* c, int mode, int32_t h, const double* C, const double* mu, const double* Sigma,
+                      const double* sigma_ref, const double* gamma_fixed) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    const Params& p = c->p;
+    if (mode < LBM_TO_OFF || mode > LBM_TO_FIXED_GAMMA) return fail(c, LBM_ERR_ARG, "bad mode %d", mode);
+    if (mode != p.to_mode)
+        return fail(c, LBM_ERR_STATE, "the context was created for to_mode %d, not %d", p.to_mode, mode);
+    if (mode == LBM_TO_LRS) {
+        if (h != p.h) return fail(c, LBM_ERR_ARG, "h = %d, the context holds h = %d", (int)h, p.h);
+        return lbm_set_lrs(c, C, mu, Sigma, sigma_ref, nullptr, nullptr);
+    }
+    if (mode == LBM_TO_FIXED_GAMMA) {
+        if (!gamma_fixed) return fail(c, LBM_ERR_ARG, "gamma_fixed is NULL");
+        for (int i = 0; i < p.n_q; ++i)
+            if (!isfinite(gamma_fixed[i])) return fail(c, LBM_ERR_ARG, "gamma_fixed[%d] is not finite", i);
+        CK(c, cudaMemcpyAsync(c->L.gfix, gamma_fixed, sizeof(double) * p.n_q, cudaMemcpyHostToDevice, c->stream));
+        c->fixed_set = 1;
+        return sync_check(c);
+    }
+    return LBM_OK;
+}
+
 int lbm_set_track_reference(lbm_ctx* c, const double* qref, int64_t len) {
     if (!c || !qref) return fail(c, LBM_ERR_ARG, "NULL argument");
     if (c->p.track_len < 1) return fail(c, LBM_ERR_STATE, "needs LBM_TO_TRACK or an LRS spin-up (track_len >= 1)");
@@ -1102,7 +1137,9 @@ int lbm_set_track_reference(lbm_ctx* c, const double* qref, int64_t len) {
 int lbm_step(lbm_ctx* c, int64_t nsteps) {
     if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
-    if (c->p.to_mode == LBM_TO_LRS && !c->lrs_set) return fail(c, LBM_ERR_STATE, "call lbm_set_lrs first");
+    if (c->p.to_mode == LBM_TO_LRS && !c->lrs_set) return fail(c, LBM_ERR_STATE, "call lbm_set_lrs or lbm_set_to_coeffs first");
+    if (c->p.to_mode == LBM_TO_FIXED_GAMMA && !c->fixed_set)
+        return fail(c, LBM_ERR_STATE, "call lbm_set_to_coeffs with gamma_fixed first");
     if (c->autotune && !c->tuned && nsteps > 0) {
         const int rc = autotune(c);
         if (rc) return rc;
@@ -1283,8 +1320,9 @@ int lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
     if (h.cbytes) {
         void* ptr[4];
         size_t nb[4];
-        lrs_parts(c, ptr, nb);
+        coef_parts(c, ptr, nb);
         for (int k = 0; k < 4; ++k) {
+            if (!nb[k]) continue;
             CK(c, cudaMemcpyAsync(o, ptr[k], nb[k], cudaMemcpyDeviceToHost, c->stream));
             o += nb[k];
         }
@@ -1327,8 +1365,9 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t bytes) {
     if (h.cbytes) {
         void* ptr[4];
         size_t nb[4];
-        lrs_parts(c, ptr, nb);
+        coef_parts(c, ptr, nb);
         for (int k = 0; k < 4; ++k) {
+            if (!nb[k]) continue;
             CK(c, cudaMemcpyAsync(ptr[k], o, nb[k], cudaMemcpyHostToDevice, c->stream));
             o += nb[k];
         }
@@ -1336,6 +1375,7 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t bytes) {
     if (h.tbytes) CK(c, cudaMemcpyAsync(c->L.track, o, h.tbytes, cudaMemcpyHostToDevice, c->stream));
     c->host_read = h.host_read;
     c->lrs_set = c->lrs_set || c->p.h > 0;
+    c->fixed_set = c->fixed_set || c->p.to_mode == LBM_TO_FIXED_GAMMA;
     return sync_check(c);
 }
 

@@ -62,6 +62,7 @@ struct Layout {
     double* w_mp;        // [n_mp][ny] band weights
     double* g_mpmp;      // [n_mp][n_mp]
     double* beta;        // [N_Q] SGS coefficients of the current step (beta = G^-1 dQ)
+    double* gfix;        // [N_Q] caller's gamma_i (LBM_TO_FIXED_GAMMA)
     double* ring;        // [ring_cap][row_len]
     double* profile;     // [ny]
     float2* spec;        // [3][ny][nx/2+1] spectrum of (v_x, v_y, omega) (Fourier bands)

@@ -27,6 +27,9 @@ class LbmSim:
     def set_lrs(self, c, mu, sigma, sigma_ref, q_hist=None, qs_hist=None):
         B.lbm_set_lrs(self.ctx, c, mu, sigma, sigma_ref, q_hist, qs_hist)
 
+    def set_to_coeffs(self, mode, h=0, c=None, mu=None, sigma=None, sigma_ref=None, gamma_fixed=None):
+        B.lbm_set_to_coeffs(self.ctx, mode, h, c, mu, sigma, sigma_ref, gamma_fixed)
+
     def step(self, n):
         B.lbm_step(self.ctx, n)
 

@@ -14,7 +14,8 @@ A workload is a plain dict of parameters.  Keys:
                       filter 'G' (Gaussian), 'L' (Laplacian), 'B' (3x3 binomial)
                       or 'F' (sharp Fourier band, scale = (l, m) wavenumber bins)
   n_mp                number of mean-profile QoIs (channel only)
-  to_mode             'off' | 'gamma' | 'lrs' | 'track'
+  to_mode             'off' | 'observe' | 'gamma' | 'fixed' | 'lrs' | 'track'
+                      ('fixed': the caller's gamma_i held for every step)
   gamma_std           std of the per-step random gamma ('gamma' mode)
   h                   LRS history length
   seed                run seed (Philox key and input generators)

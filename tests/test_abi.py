@@ -71,3 +71,19 @@ def test_projection_shapes_without_gpu(B):
         with pytest.raises(B.LbmError) as e:
             B.lbm_project_shape(B.config_from_workload(synthetic.workload(name)), m)
         assert e.value.args and "m" in str(e.value)
+
+
+def test_set_to_coeffs_without_gpu(B):
+    """lbm_set_to_coeffs checks its handle before any device work, and the
+    fixed-gamma mode is a valid configuration (its buffer holds the N gamma_i)."""
+    with pytest.raises(B.LbmError) as e:
+        B.lbm_set_to_coeffs(None, "fixed", gamma_fixed=[0.0, 0.0])
+    assert e.value.code == B.LBM_ERR_ARG
+    fixed = B.config_from_workload(synthetic.workload("C3", to_mode="fixed"))
+    observe = B.config_from_workload(synthetic.workload("C3", to_mode="observe"))
+    assert B.lbm_required_bytes(fixed) >= B.lbm_required_bytes(observe)
+    bad = B.config_from_workload(synthetic.workload("C3"))
+    bad.to_mode = 6
+    with pytest.raises(B.LbmError) as e:
+        B.lbm_required_bytes(bad)
+    assert e.value.code == B.LBM_ERR_ARG

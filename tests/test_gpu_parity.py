@@ -315,3 +315,77 @@ def test_fourier_band_qois_2d(mode):
     _, rg, rho_g, u_g = run_gpu(wl, 20, lrs=lrs)
     _compare_state(wl, rho_g, u_g, rho_o, u_o)
     _compare_rows(wl, rg, ro)
+
+
+@pytest.mark.parametrize("name,kw", [("C3", dict(nx=36, ny=22, nz=13)), ("C2", dict(nx=41, ny=35))])
+def test_fixed_gamma_through_set_to_coeffs(name, kw):
+    """Caller-given coefficients gamma_i held for every step (LBM_TO_FIXED_GAMMA,
+    set with lbm_set_to_coeffs) against the oracle's 'fixed' mode: 3-D channel
+    with its 12 QoIs (six mean-profile bands) and the 2-D Kolmogorov shape."""
+    from paper_2609_32892_b300 import LbmSim
+    from oracle.sim import Simulation
+
+    wl = synthetic.workload(name, to_mode="fixed", **kw)
+    nq = nq_of(wl)
+    rng = np.random.Generator(np.random.PCG64(5))
+    # gamma_i dQ-sized: a small fraction of each QoI per step through den_i = 1/(G^-1)_ii
+    gam = rng.normal(0.0, 1.0, nq) * 1e-3
+    steps = 8 if name == "C3" else 30
+    o = Simulation(wl, synthetic.initial_velocity(wl), gamma_fixed=gam)
+    ro = o.run(steps)
+    rho_o, u_o = o.macros()
+    g = LbmSim(wl)
+    g.init(synthetic.initial_velocity(wl))
+    g.set_to_coeffs("fixed", gamma_fixed=gam)
+    g.step(steps)
+    g.sync()
+    rg = g.qoi()
+    rho_g, u_g = g.macros()
+    g.close()
+    assert np.all(ro[:, -1] == 0)
+    np.testing.assert_array_equal(rg[:, 1 + 2 * nq:1 + 3 * nq], np.tile(gam, (steps, 1)))
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)
+
+
+def test_set_to_coeffs_checks_and_lrs_path():
+    """lbm_set_to_coeffs: the LRS path equals lbm_set_lrs bit for bit; a mode
+    other than the context's, an h other than its own, or missing fixed
+    coefficients are refused with a status."""
+    from paper_2609_32892_b300 import LbmSim, binding as B
+
+    wl = synthetic.workload("C2", nx=40, ny=34, h=3)
+    lrs = lrs_inputs(wl, np.zeros(nq_of(wl)))
+    out = []
+    for via in ("lrs", "coeffs"):
+        g = LbmSim(wl)
+        g.init(synthetic.initial_velocity(wl))
+        if via == "lrs":
+            g.set_lrs(*lrs)
+        else:
+            with pytest.raises(B.LbmError) as e:
+                g.step(1)  # coefficients not set yet
+            assert e.value.code == B.LBM_ERR_STATE
+            with pytest.raises(B.LbmError) as e:
+                g.set_to_coeffs("fixed", gamma_fixed=np.zeros(nq_of(wl)))
+            assert e.value.code == B.LBM_ERR_STATE
+            with pytest.raises(B.LbmError) as e:
+                g.set_to_coeffs("lrs", 4, *lrs)
+            assert e.value.code == B.LBM_ERR_ARG
+            g.set_to_coeffs("lrs", 3, *lrs)
+        g.step(6)
+        g.sync()
+        out.append((g.qoi(), g.populations()))
+        g.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    wf = synthetic.workload("C2", nx=40, ny=34, to_mode="fixed")
+    g = LbmSim(wf)
+    g.init(synthetic.initial_velocity(wf))
+    with pytest.raises(B.LbmError) as e:
+        g.step(1)
+    assert e.value.code == B.LBM_ERR_STATE
+    with pytest.raises(B.LbmError) as e:
+        g.set_to_coeffs("fixed")
+    assert e.value.code == B.LBM_ERR_ARG
+    g.close()

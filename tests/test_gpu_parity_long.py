@@ -1,0 +1,119 @@
+"""Parity with the FP64 oracle on the paths the benchmark takes, over long runs.
+
+* Stored oracle runs (tests/golden/oracle_runs, written by
+  tests/golden/make_oracle_runs.py from the oracle alone): the channel LES with
+  WALE and TO-LRS, 12 QoIs, h = 20, for 100 steps on 68 x 38 x 17 (full and
+  ragged 32 x 16 filter tiles, two blocks of the LRS history product) and for
+  1000 steps on 36 x 22 x 13.  State, QoI rows and the FP64 mean-profile sum
+  are compared element by element.
+* The multi-block LRS history product at the benchmark's h = 500 (12 QoIs:
+  12 013 rows of C in 47 blocks) and at h = 100 (4 QoIs: 805 rows, 4 blocks):
+  seeded initial histories and history coefficients large enough that the
+  history term carries dQ.  With C the identity on the q^{n*} block, dQ =
+  sigma (history term + mu + L z) does not depend on q^{n*} beyond rounding, so
+  the first step's dQ must agree to FP64 rounding (1e-9 relative) even though
+  q^{n*} agrees only to FP32 (1e-4): a block dropped or misplaced, or a ring
+  slot off by one, changes dQ by about a percent.
+* The 256^2 Kolmogorov LES shape with h = 100 over 150 steps on 61 x 58.
+
+Tolerances are those of test_gpu_parity.py (FP32 against FP64)."""
+
+import json
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import synthetic
+from gpu_common import fluid_mask, lrs_inputs, nq_of, oracle_sigma_ref, rel_l2, run_gpu, run_oracle
+from test_gpu_parity import _compare_rows, _compare_state
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "golden"))
+import make_oracle_runs  # noqa: E402
+
+
+@pytest.mark.parametrize("case", sorted(make_oracle_runs.CASES))
+def test_stored_channel_wale_lrs_run(case):
+    from paper_2609_32892_b300 import binding as B
+
+    path = os.path.join(HERE, "golden", "oracle_runs", case + ".npz")
+    d = np.load(path)
+    meta = json.loads(str(d["meta"]))
+    wl = make_oracle_runs.case_workload(case)
+    steps = meta["steps"]
+    lrs = lrs_inputs(wl, d["sigma_ref"])
+    g, rg, rho_g, u_g = run_gpu(wl, steps, lrs=lrs)
+    prof, nprof = B.lbm_get_profile(g.ctx, wl["ny"])
+    g.close()
+    ro = d["rows"]
+    assert np.all(ro[:, -1] == 0)  # the stored run never went singular or unstable
+    _compare_state(wl, rho_g, u_g, d["rho"], d["u"])
+    _compare_rows(wl, rg, ro)
+    # mean streamwise profile: FP64 running sum of plane means (Sec. 7.3)
+    assert nprof == steps
+    po = d["profile_sum"]
+    np.testing.assert_allclose(prof, po, rtol=0, atol=1e-6 * np.abs(po).max())
+    assert np.all(prof[[0, -1]] == 0.0)
+
+
+def _history_inputs(wl, sigma_ref, seed, coupling=1e-3):
+    """C: identity on the q^{n*} block, N(0, s^2) on the history rows with s
+    chosen so that the history term is about `coupling` in scaled units,
+    bias row 0; seeded histories of unit size in scaled units."""
+    nq, h = nq_of(wl), wl["h"]
+    c, mu, sig = synthetic.synthetic_lrs(nq, h, wl["seed"])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s = coupling / np.sqrt(2 * h * nq)
+    hist_rows = np.r_[0:h * nq, (h + 1) * nq:(2 * h + 1) * nq]
+    c[hist_rows] = rng.normal(0.0, s, size=(len(hist_rows), nq))
+    q_hist = sigma_ref * rng.normal(size=(h, nq))
+    qs_hist = sigma_ref * rng.normal(size=(h, nq))
+    return (c, mu, sig, np.asarray(sigma_ref, dtype=np.float64), q_hist, qs_hist)
+
+
+@pytest.mark.parametrize("name,kw", [("C3", dict(nx=20, ny=22, nz=13, h=500)), ("C2", dict(nx=37, ny=31, h=100))])
+def test_lrs_history_product_many_blocks(name, kw):
+    from oracle.sim import Simulation
+    from paper_2609_32892_b300 import LbmSim
+
+    wl = synthetic.workload(name, **kw)
+    nq = nq_of(wl)
+    sref = oracle_sigma_ref(wl, 2)
+    lrs = _history_inputs(wl, sref, seed=99)
+    steps = 4
+    o = Simulation(wl, synthetic.initial_velocity(wl), lrs=lrs)
+    ro = o.run(steps)
+    g = LbmSim(wl)
+    g.init(synthetic.initial_velocity(wl))
+    g.set_lrs(*lrs)
+    g.step(steps)
+    g.sync()
+    rg = g.qoi()
+    g.close()
+    assert np.all(ro[:, -1] == 0) and np.all(rg[:, -1] == 0)
+    q_o, q_g = ro[:, 1:1 + nq], rg[:, 1:1 + nq]
+    np.testing.assert_allclose(q_g, q_o, rtol=1e-4)
+    dq_o, dq_g = ro[:, 1 + nq:1 + 2 * nq], rg[:, 1 + nq:1 + 2 * nq]
+    # the history term dominates dQ: about 1e-3 of sigma_ref
+    assert np.all(np.abs(dq_o[0]) > 1e-6 * sref)
+    np.testing.assert_allclose(dq_g[0], dq_o[0], rtol=1e-9, atol=0)
+    # later steps: the histories now hold this run's own q^{n*} (FP32 vs FP64)
+    np.testing.assert_allclose(dq_g[1:], dq_o[1:], rtol=1e-5, atol=0)
+
+
+def test_kolmogorov_lrs_h100_150_steps():
+    """256^2 Kolmogorov LES shape (Smagorinsky + TO-LRS, 4 QoIs, drag) with the
+    history length 100 (805 rows of C, 4 blocks) on 61 x 58 for 150 steps,
+    so that the histories fill and wrap."""
+    wl = synthetic.workload("C2", nx=61, ny=58, h=100)
+    lrs = lrs_inputs(wl, oracle_sigma_ref(wl))
+    _, ro, rho_o, u_o = run_oracle(wl, 150, lrs=lrs)
+    _, rg, rho_g, u_g = run_gpu(wl, 150, lrs=lrs)
+    assert np.all(ro[:, -1] == 0)
+    _compare_state(wl, rho_g, u_g, rho_o, u_o)
+    _compare_rows(wl, rg, ro)
+    assert rel_l2(u_g, u_o, fluid_mask(wl)) <= 1e-5

@@ -284,13 +284,90 @@ def test_printed_filter_constants(root):
 
 def test_lrs_spin_up_follows_the_reference():
     """During the spin-up of an online run, dQ = Q_ref - q* and the reference
-    (not an LRS prediction) enters the corrected-QoI history."""
+    (not an LRS prediction) enters the corrected-QoI history; afterwards the
+    LRS model takes over.  The reference is the observed run's own predictor
+    QoIs raised by 1e-4, a nudge small enough that every step stays stable."""
     wl = synthetic.workload("C2", nx=20, ny=18, h=3, spinup=2, track_len=2)
     nq = len(wl["qois"])
-    ref = np.array([np.full(nq, 1.0), np.full(nq, 2.0)])
-    sim = Simulation(wl, synthetic.initial_velocity(wl), lrs=_lrs_inputs(wl), track_ref=ref)
-    rows = sim.run(2)
-    np.testing.assert_allclose(rows[:, 1 + nq:1 + 2 * nq], ref - rows[:, 1:1 + nq], rtol=1e-15)
-    np.testing.assert_array_equal(sim.lrs.q_hist[0], ref[1])
-    np.testing.assert_array_equal(sim.lrs.q_hist[1], ref[0])
-    np.testing.assert_array_equal(sim.lrs.qs_hist[0], rows[1, 1:1 + nq])
+    u0 = synthetic.initial_velocity(wl)
+    obs = Simulation(dict(wl, to_mode="observe", spinup=0), u0).run(2)
+    ref = obs[:, 1:1 + nq] * (1.0 + 1e-4)
+    sim = Simulation(wl, u0, lrs=_lrs_inputs(wl, _sigma_ref(wl)), track_ref=ref)
+    rows = sim.run(3)
+    assert np.all(rows[:, -1] == 0)  # neither singular nor unstable
+    assert np.all(np.isfinite(rows)) and np.all(np.isfinite(sim.fp))
+    q, dq = rows[:, 1:1 + nq], rows[:, 1 + nq:1 + 2 * nq]
+    # step 0 starts from the observed run's state: the same predictor QoIs
+    np.testing.assert_array_equal(q[0], obs[0, 1:1 + nq])
+    # spin-up steps: dQ = Q_ref - q*, a nudge of about 1e-4 q*
+    np.testing.assert_allclose(dq[:2], ref - q[:2], rtol=1e-15)
+    assert np.all(np.abs(dq[0]) > 0.5e-4 * np.abs(q[0]))
+    # histories, most recent first: the LRS prediction of step 2, then the references
+    np.testing.assert_array_equal(sim.lrs.q_hist[1], ref[1])
+    np.testing.assert_array_equal(sim.lrs.q_hist[2], ref[0])
+    np.testing.assert_allclose(sim.lrs.q_hist[0] - q[2], dq[2], rtol=0, atol=1e-15 * np.abs(q[2]).max())
+    np.testing.assert_array_equal(sim.lrs.qs_hist[0], q[2])
+    np.testing.assert_array_equal(sim.lrs.qs_hist[1], q[1])
+
+
+def test_fixed_gamma_moves_each_qoi_by_gamma_times_its_pattern_norm():
+    """Fixed coefficients (Eq. TO-ansatz with caller-given gamma_i): the step
+    adds f^eq(rho, v* + dv) - f^eq(rho, v*), which shifts the velocity by
+    exactly dv, so dv is read off the two states (the fixed-gamma step and
+    an observed step from the same start).  Then <V_j, dv> = gamma_j <V_j, O_j>
+    (orthogonal patterns) = dQ_j of the QoI row, for every j."""
+    wl = synthetic.workload("C2", nx=22, ny=20, to_mode="fixed")
+    nq = len(wl["qois"])
+    u0 = synthetic.initial_velocity(wl)
+    gam = np.array([2e-3, -1e-3, 5e-4, 1.5e-3])[:nq]
+    fixed = Simulation(wl, u0, gamma_fixed=gam)
+    row = fixed.run(1)[0]
+    obs = Simulation(dict(wl, to_mode="observe"), u0)
+    obs.run(1)
+    assert row[-1] == 0
+    np.testing.assert_array_equal(row[1 + 2 * nq:1 + 3 * nq], gam)
+    _, v_fix = fixed.macros()
+    _, v_obs = obs.macros()  # v^{p*} of the same step
+    dv = v_fix - v_obs
+    vs = fixed.to.sensitivities(v_obs)
+    proj = np.array([(vs[j] * dv).sum() for j in range(nq)])
+    dq = row[1 + nq:1 + 2 * nq]
+    np.testing.assert_allclose(proj, dq, rtol=1e-9)
+    # gamma = 0 is the observed step (to the rounding of f^eq(v) - f^eq(v))
+    zero = Simulation(wl, u0, gamma_fixed=np.zeros(nq))
+    zero.run(1)
+    np.testing.assert_allclose(zero.fp, obs.fp, rtol=0, atol=1e-15)
+
+
+def test_mean_profile_sum_on_a_laminar_channel():
+    """The running mean-profile sum (the <u_x>(y) statistic of Sec. 7.3) on the
+    body-force channel at tau = 1/2 + sqrt(3)/4, where the steady profile is
+    exactly the parabola F y_w (2H - y_w)/(2 nu) (Poiseuille, pinned above):
+    the stored post-collision velocity is that physical velocity plus
+    F/(2 rho), so K steps add K (parabola + F/2) on every fluid row and zero
+    on the solid rows.  A perturbation a (-1)^x cos(pi z/2) of zero plane mean
+    (a = 1e-9) leaves the plane mean unchanged to O(a^2), so the sum must
+    average over the whole x-z plane, not one column."""
+    fx, ny, nx, nz = 1e-6, 10, 4, 4
+    tau = 0.5 + math.sqrt(3) / 4
+    base = synthetic.workload("C3", nx=nx, ny=ny, nz=nz, tau=tau, forcing="guo", body_force=(fx, 0.0, 0.0),
+                              substrate="none", to_mode="off", init=("rest",), n_mp=0)
+    spin = Simulation(base, np.zeros((3, nz, ny, nx)))
+    spin.run(2500)
+    lat = spin.lat
+    rho, v = spin.macros()
+    x = np.arange(nx)[None, None, :]
+    z = np.arange(nz)[:, None, None]
+    pert = 1e-9 * ((-1.0) ** x) * np.cos(np.pi * z / 2) * spin.mask
+    v2 = v.copy()
+    v2[0] += pert
+    fp = spin.fp + lbm.equilibrium(lat, rho, v2) - lbm.equilibrium(lat, rho, v)
+    obs = Simulation(dict(base, to_mode="observe", qois=[("E", "B", 1)], h=0), np.zeros((3, nz, ny, nx)))
+    obs.fp = fp
+    k = 4
+    obs.run(k)
+    nu = CS2 * (tau - 0.5)
+    yw = np.arange(ny) - 0.5
+    exact = fx / (2 * nu) * yw * ((ny - 2) - yw) + 0.5 * fx
+    exact[0] = exact[-1] = 0.0
+    np.testing.assert_allclose(obs.profile_sum / k, exact, rtol=1e-9, atol=1e-20)

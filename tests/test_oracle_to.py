@@ -115,3 +115,33 @@ def test_mean_profile_bands():
         cand = np.arange(1, ny // 2)
         best = cand[np.argmin(np.abs(np.log(dw[cand]) - np.log(centres[j])))]
         assert y == best
+
+
+def test_mean_profile_band_width_is_the_centre_spacing():
+    """Eq. 3d-mp-band-weights (Sec. 7.2): band j is a Gaussian in ln d_w
+    centred on ln d_{w,j} with the spacing of the log-spaced centres as its
+    width, so w_j(d_{w,j +- 1}) / w_j(d_{w,j}) = exp(-1/2).  ln w_j is then
+    exactly quadratic in ln d_w; three rows near the centre give the
+    quadratic, whose vertex and curvature are the centre and the width."""
+    ny = 2002
+    nb = 6
+    w = to.mp_band_weights(ny, nb)
+    h = 0.5 * (ny - 2)
+    centres = np.exp(np.linspace(np.log(0.5), np.log(h), nb))
+    spacing = (np.log(h) - np.log(0.5)) / (nb - 1)
+    for j in range(nb):
+        # three lower-half rows (d_w = y - 1/2) within about one width of the centre
+        yc = int(np.clip(round(centres[j] + 0.5), 1, h))
+        ys = sorted({max(1, yc - 2 * (j + 1)), yc, min(int(h), yc + 2 * (j + 1))} | {int(h) - 1})[:3]
+        if len(ys) < 3:
+            ys = [1, 2, 3]
+        ld = np.log(np.array(ys) - 0.5)
+        lw = np.log(w[j, ys])
+        a = np.vstack([np.ones(3), ld, ld * ld]).T
+        c0, c1, c2 = np.linalg.solve(a, lw)
+        sigma = np.sqrt(-1.0 / (2.0 * c2))
+        centre = -c1 / (2.0 * c2)
+        assert abs(sigma / spacing - 1.0) < 1e-6, (j, sigma, spacing)
+        assert abs(centre - np.log(centres[j])) < 1e-6 * spacing, (j, centre)
+        ratio = np.exp(c2 * spacing ** 2)  # w at the next centre over w at this one
+        assert abs(ratio - np.exp(-0.5)) < 1e-6

@@ -151,17 +151,24 @@ def _lrs_for(wl):
 
 
 def _algorithmic_bytes(wl, n):
-    """Per-class minimal DRAM bytes per launch: what each kernel must read and write per node."""
+    """Per-class minimal DRAM bytes per launch: what each kernel must read and write per node.
+
+    predict: pull the populations (Q b), write v^{p*} (d x 4) and, with WALE, the
+    post-stream velocity (3 x 4); collide: read and write the populations
+    (2 Q b), read the WALE velocity (3 x 4) and, with the SGS corrector, the
+    sensitivities of the scale QoIs (N_s x d x 4)."""
     q = 19 if wl["dim"] == 3 else 9
     b = {"fp32": 4, "fp16": 2, "bf16": 2}[wl["storage"]]
     d = wl["dim"]
     ncomp = 6 if d == 3 else 3
     to = wl["to_mode"] != "off"
+    corr = to and wl["to_mode"] != "observe"
+    ns = len(wl["qois"]) if to else 0
+    wale = wl["substrate"] == "wale"
     return {
-        "collide": n * (2 * q * b + ((1 + d) * 4 if to else 0) + (3 * 4 if wl["substrate"] == "wale" else 0)),
-        "moments": n * (q * b + 3 * 4),
+        "collide": n * (2 * q * b + (3 * 4 if wale else 0) + (ns * d * 4 if corr else 0)),
+        "predict": n * (q * b + (d * 4 if to else 0) + (3 * 4 if wale else 0)),
         "filter": n * 2 * ncomp * 4,
-        "apply": n * (2 * q * b + (1 + d) * 4),
     }
 
 

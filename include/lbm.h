@@ -232,8 +232,11 @@ int lbm_load(lbm_ctx* ctx, const void* host_buf, size_t bytes);
  *     context's stream, accumulated per kernel class; lbm_profile_read
  *     returns the totals.  Class ids are the LBM_K_* values. */
 enum {
-    LBM_K_MOMENTS = 0, LBM_K_COLLIDE = 1, LBM_K_CURL = 2, LBM_K_FILTER = 3, LBM_K_SENS = 4,
-    LBM_K_REDUCE = 5, LBM_K_LRS = 6, LBM_K_SOLVE = 7, LBM_K_APPLY = 8,
+    LBM_K_MOMENTS = 0,  /* predictor pass: v^{p*} (TO modes), post-stream u (WALE) */
+    LBM_K_COLLIDE = 1,  /* stream-collide, with the step's SGS corrector in TO modes */
+    LBM_K_CURL = 2, LBM_K_FILTER = 3, LBM_K_SENS = 4,
+    LBM_K_REDUCE = 5, LBM_K_LRS = 6, LBM_K_SOLVE = 7,
+    LBM_K_APPLY = 8,    /* reserved: the corrector runs inside the collide */
     LBM_K_GAUSS3 = 9,  /* fused 3-D Gaussian / binomial filter applications */
     LBM_K_LAP3 = 10,   /* 3-D Laplacian filters: L_1 one launch, L_3 two    */
     LBM_K_FFT = 11,    /* cuFFT transforms of the Fourier-band filters      */
@@ -285,13 +288,14 @@ int lbm_eval_qoi(lbm_ctx* ctx, const float* u, double* q);
 
 /* Autotuner (default on): before the first lbm_step the library times the
  * candidate launch shapes of its kernels on this context's buffers (node-pair
- * vs single-node collide, 4-node vs single-node SGS apply, the z-segment count
- * of the fused 3-D filters, the line segments of 2-D filter passes) and keeps
- * the fastest, cached per grid shape for the process.  Per node, every
- * candidate evaluates the same arithmetic.  lbm_set_autotune must precede the
- * first lbm_step; 0 keeps the built-in shapes.  lbm_get_tuning returns
- * [tuned, collide_pair, apply4, march_threads, blocks_per_sm of filter slot
- * 0..7 (0 = default), throughput goal] (up to count values). */
+ * vs single-node collide, the z-segment count of the fused 3-D filters, the
+ * line segments of 2-D filter passes) and keeps the fastest, cached per grid
+ * shape for the process.  Per node, every candidate evaluates the same
+ * arithmetic.  lbm_set_autotune must precede the first lbm_step; 0 keeps the
+ * built-in shapes.  lbm_get_tuning returns [tuned, collide_pair,
+ * corrector_in_collide (1 when the step's SGS corrector runs inside the
+ * collide: every TO mode but OFF and OBSERVE), march_threads, blocks_per_sm
+ * of filter slot 0..7 (0 = default), throughput goal] (up to count values). */
 int lbm_set_autotune(lbm_ctx* ctx, int enable);
 int lbm_get_tuning(lbm_ctx* ctx, int32_t* values, int count);
 

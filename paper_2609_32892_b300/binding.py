@@ -23,7 +23,7 @@ FILTER = {"G": 0, "L": 1, "B": 2, "F": 3}
 TO_MODE = {"off": 0, "observe": 1, "gamma": 2, "lrs": 3, "track": 4, "fixed": 5}
 MAX_QOI = 16
 FLAG_SINGULAR, FLAG_UNSTABLE = 1, 2
-K_NAMES = ["moments", "collide", "curl", "filter", "sens", "reduce", "lrs", "solve", "apply", "gauss3", "lap3", "fft"]
+K_NAMES = ["predict", "collide", "curl", "filter", "sens", "reduce", "lrs", "solve", "apply", "gauss3", "lap3", "fft"]
 EXPORTED = [
     "lbm_qoi_row_len", "lbm_required_bytes", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_macros",
     "lbm_set_lrs", "lbm_set_to_coeffs", "lbm_set_track_reference", "lbm_step", "lbm_sync", "lbm_qoi", "lbm_get_macros",
@@ -412,5 +412,5 @@ def lbm_eval_qoi(ctx, u_ptr, q_ptr):
 def lbm_get_tuning(ctx):
     v = (C.c_int32 * 13)()
     _check(_lib.lbm_get_tuning(ctx, v, 13), ctx)
-    return {"tuned": int(v[0]), "collide_pair": int(v[1]), "apply4": int(v[2]), "march_threads": int(v[3]),
+    return {"tuned": int(v[0]), "collide_pair": int(v[1]), "corrector_in_collide": int(v[2]), "march_threads": int(v[3]),
             "filter_blocks_per_sm": [int(v[4 + f]) for f in range(8)], "throughput_goal": int(v[12])}

@@ -167,10 +167,26 @@ __device__ __forceinline__ Macro macros_of(const Params& p, const float* g, cons
     return m;
 }
 
+// The predictor velocity of the TO phase (Sec. 4 predictor-corrector):
+// BGK relaxation conserves mass and momentum and the body force adds F, so
+// v^{p*} = sum_i c_i f^{p*}_i / rho = (rho u + F)/rho under both forcing
+// schemes.  It follows from the pulled moments alone, whatever tau_eff the
+// substrate gives the node, so it can be formed before the collision.
+__device__ __forceinline__ void predictor_velocity(const Macro& m, float& vx, float& vy, float& vz) {
+    const float inv = 1.0f / m.rho;
+    vx = (m.jx + m.fx) * inv;
+    vy = (m.jy + m.fy) * inv;
+    vz = (m.jz + m.fz) * inv;
+}
+
 // ------------------------------------------------------------------ kernels --
-template <int DIM, typename T>
-__global__ void __launch_bounds__(256) moments_kernel(Params p, const T* __restrict__ src, float* __restrict__ vn,
-                                                      const float* __restrict__ kolmo) {
+// Predictor pass: pull the populations of a node and write the predictor
+// velocity v^{p*} (WV, the input of the TO phase, DIM components) and/or the
+// post-stream velocity u (WN, the input of the WALE gradients, 3 components).
+// Solid rows get zero velocity.
+template <int DIM, typename T, bool WV, bool WN>
+__global__ void __launch_bounds__(256) predict_kernel(Params p, const T* __restrict__ src, float* __restrict__ vps,
+                                                      float* __restrict__ vn, const float* __restrict__ kolmo) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.n) return;
     const int N = (int)p.n;
@@ -178,16 +194,24 @@ __global__ void __launch_bounds__(256) moments_kernel(Params p, const T* __restr
     const int t = n / p.nx;
     const int y = t % p.ny;
     const int z = t / p.ny;
-    if (p.walls && (y == 0 || y == p.ny - 1)) {
-        vn[n] = 0.f; vn[N + n] = 0.f; vn[2 * N + n] = 0.f;
-        return;
+    float vx = 0.f, vy = 0.f, vz = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+    if (!(p.walls && (y == 0 || y == p.ny - 1))) {
+        float g[Lat<DIM>::Q];
+        pull<DIM, T>(p, src, x, y, z, n, g);
+        const Macro m = macros_of<DIM>(p, g, kolmo, y);
+        predictor_velocity(m, vx, vy, vz);
+        ux = m.ux; uy = m.uy; uz = m.uz;
     }
-    float g[Lat<DIM>::Q];
-    pull<DIM, T>(p, src, x, y, z, n, g);
-    const Macro m = macros_of<DIM>(p, g, kolmo, y);
-    vn[n] = m.ux;
-    vn[N + n] = m.uy;
-    vn[2 * N + n] = m.uz;
+    if (WV) {
+        vps[n] = vx;
+        vps[(size_t)N + n] = vy;
+        if (DIM == 3) vps[(size_t)2 * N + n] = vz;
+    }
+    if (WN) {
+        vn[n] = ux;
+        vn[(size_t)N + n] = uy;
+        vn[(size_t)2 * N + n] = uz;
+    }
 }
 
 // WALE eddy viscosity from the post-stream velocity field (Sec. 5.2): g_ij =
@@ -342,19 +366,64 @@ __device__ __forceinline__ void collide_node(const Params& p, float* g, int x, i
             g[j] = g[j] + (geq[j] - g[j]) * om + (ev - od);
         }
     }
-    const float inv = 1.0f / m.rho;
     rho_o = m.rho;
-    vx_o = (m.jx + fx) * inv;
-    vy_o = (m.jy + fy) * inv;
-    vz_o = (m.jz + fz) * inv;
+    predictor_velocity(m, vx_o, vy_o, vz_o);
 }
 
-// One thread per node: pull, collide_node, store (and the TO fields).
-template <int DIM, typename T, int SUB>
+// SGS velocity increment of a node: dv = sum_k beta_k V_k + (sum_j beta_j
+// w_j(y)) e_x (the orthogonal patterns folded into one combination of the
+// sensitivities, beta = G^-1 dQ; the band term per row from the solve).
+struct VPtrs {
+    const float* v[kMaxQoi];
+};
+constexpr int kMaxScaleQoi = 8;  // lbm_create allows at most 8 scale-aware QoIs
+
+template <int DIM>
+__device__ __forceinline__ void sgs_increment(const Params& p, const VPtrs& vk, const float* __restrict__ betaf,
+                                              const float* __restrict__ mprow, size_t n, int y, float& dx,
+                                              float& dy, float& dz) {
+    const size_t N = (size_t)p.n;
+    dx = 0.f;
+    dy = 0.f;
+    dz = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxScaleQoi; ++k) {
+        if (k < p.n_s) {
+            const float b = betaf[k];
+            const float* v = vk.v[k];
+            dx += b * __ldg(v + n);
+            dy += b * __ldg(v + N + n);
+            if (DIM == 3) dz += b * __ldg(v + 2 * N + n);
+        }
+    }
+    dx += mprow[y];
+}
+
+// Eq. LES-2 corrector on the predictor populations of a node held in
+// registers: g^p = g^{p*} + f^eq(rho, v* + dv) - f^eq(rho, v*), written out
+// as w_i rho [3 c.d + 4.5 (c.d)(2 c.v* + c.d) - 1.5 d.(2 v* + d)].
+template <int DIM>
+__device__ __forceinline__ void sgs_correct(float* g, float r, float ux, float uy, float uz, float dx, float dy,
+                                            float dz) {
+    using LT = Lat<DIM>;
+    const float du = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+        const float cu = cx * ux + cy * uy + cz * uz;
+        const float cd = cx * dx + cy * dy + cz * dz;
+        g[i] += LT::w(i) * r * (3.0f * cd + 4.5f * cd * (2.0f * cu + cd) - 1.5f * du);
+    }
+}
+
+// One thread per node: pull, collide_node and, with CORR, the SGS corrector
+// of the step (Eq. LES-2) before the store: the predictor populations never
+// leave registers.
+template <int DIM, typename T, int SUB, bool CORR>
 __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
-                                                      float* __restrict__ rho_out, float* __restrict__ vps,
                                                       const float* __restrict__ vn, const float* __restrict__ kolmo,
-                                                      DevState* st, int fields) {
+                                                      DevState* st, VPtrs vk, const float* __restrict__ betaf,
+                                                      const float* __restrict__ mprow) {
     using LT = Lat<DIM>;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.n) return;
@@ -363,26 +432,18 @@ __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restr
     const int t = n / p.nx;
     const int y = t % p.ny;
     const int z = t / p.ny;
-    if (p.walls && (y == 0 || y == p.ny - 1)) {
-        if (fields) {
-            rho_out[n] = 1.f;
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) vps[(size_t)a * N + n] = 0.f;
-        }
-        return;
-    }
+    if (p.walls && (y == 0 || y == p.ny - 1)) return;
     float g[LT::Q];
     pull<DIM, T>(p, src, x, y, z, n, g);
     float r, vx, vy, vz;
     collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g, x, y, z, vn, kolmo, st, r, vx, vy, vz);
+    if (CORR) {
+        float dx, dy, dz;
+        sgs_increment<DIM>(p, vk, betaf, mprow, (size_t)n, y, dx, dy, dz);
+        sgs_correct<DIM>(g, r, vx, vy, vz, dx, dy, dz);
+    }
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) st_<T>(dst + (size_t)i * N + n, g[i]);
-    if (fields) {
-        rho_out[n] = r;
-        vps[n] = vx;
-        vps[(size_t)N + n] = vy;
-        if (DIM == 3) vps[(size_t)2 * N + n] = vz;
-    }
 }
 
 // ---- two nodes per thread (nx even): aligned 2-element population loads ----
@@ -459,11 +520,11 @@ __device__ __forceinline__ void pull2(const Params& p, const T* __restrict__ src
     }
 }
 
-template <int DIM, typename T, int SUB>
+template <int DIM, typename T, int SUB, bool CORR>
 __global__ void __launch_bounds__(128) collide2_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
-                                                       float* __restrict__ rho_out, float* __restrict__ vps,
                                                        const float* __restrict__ vn, const float* __restrict__ kolmo,
-                                                       DevState* st, int fields) {
+                                                       DevState* st, VPtrs vk, const float* __restrict__ betaf,
+                                                       const float* __restrict__ mprow) {
     using LT = Lat<DIM>;
     const long long npair = p.n / 2;
     long long pi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -478,177 +539,19 @@ __global__ void __launch_bounds__(128) collide2_kernel(Params p, const T* __rest
     float g0[LT::Q], g1[LT::Q];
     pull2<DIM, T>(p, src, x0, y, z, n0, g0, g1);
     if (!live) return;
-    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
-    if (solid) {
-        if (fields) {
-            *reinterpret_cast<float2*>(rho_out + n0) = make_float2(1.f, 1.f);
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) *reinterpret_cast<float2*>(vps + (size_t)a * N + n0) = make_float2(0.f, 0.f);
-        }
-        return;
-    }
+    if (p.walls && (y == 0 || y == p.ny - 1)) return;
     float r0, vx0, vy0, vz0, r1, vx1, vy1, vz1;
     collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g0, x0, y, z, vn, kolmo, st, r0, vx0, vy0, vz0);
     collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g1, x0 + 1, y, z, vn, kolmo, st, r1, vx1, vy1, vz1);
+    if (CORR) {
+        float dx0, dy0, dz0, dx1, dy1, dz1;
+        sgs_increment<DIM>(p, vk, betaf, mprow, (size_t)n0, y, dx0, dy0, dz0);
+        sgs_increment<DIM>(p, vk, betaf, mprow, (size_t)n0 + 1, y, dx1, dy1, dz1);
+        sgs_correct<DIM>(g0, r0, vx0, vy0, vz0, dx0, dy0, dz0);
+        sgs_correct<DIM>(g1, r1, vx1, vy1, vz1, dx1, dy1, dz1);
+    }
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) Vec2<T>::st(dst + (size_t)i * N + n0, g0[i], g1[i]);
-    if (fields) {
-        *reinterpret_cast<float2*>(rho_out + n0) = make_float2(r0, r1);
-        *reinterpret_cast<float2*>(vps + n0) = make_float2(vx0, vx1);
-        *reinterpret_cast<float2*>(vps + (size_t)N + n0) = make_float2(vy0, vy1);
-        if (DIM == 3) *reinterpret_cast<float2*>(vps + (size_t)2 * N + n0) = make_float2(vz0, vz1);
-    }
-}
-
-// Eq. LES-2 corrector: g^p = g^{p*} + f^eq(rho, v* + dv) - f^eq(rho, v*), with
-// dv = sum_k beta_k V_k + sum_j beta_mp_j w_j(y) e_x (the orthogonal patterns
-// folded into one combination of the sensitivities, beta = G^-1 dQ).
-struct VPtrs {
-    const float* v[kMaxQoi];
-};
-
-template <int DIM, typename T>
-__global__ void __launch_bounds__(256) apply_kernel(Params p, T* __restrict__ f, const float* __restrict__ rho,
-                                                    const float* __restrict__ vps, VPtrs vk,
-                                                    const double* __restrict__ beta,
-                                                    const double* __restrict__ w_mp) {
-    using LT = Lat<DIM>;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= p.n) return;
-    const int N = (int)p.n;
-    const int y = (n / p.nx) % p.ny;
-    if (p.walls && (y == 0 || y == p.ny - 1)) return;
-    float dx = 0.f, dy = 0.f, dz = 0.f;
-    for (int k = 0; k < p.n_s; ++k) {
-        const float b = (float)beta[k];
-        const float* v = vk.v[k];
-        dx += b * v[n];
-        dy += b * v[(size_t)N + n];
-        if (DIM == 3) dz += b * v[(size_t)2 * N + n];
-    }
-    float mp = 0.f;  // same order as the 4-node kernel, so both give identical results
-    for (int j = 0; j < p.n_mp; ++j) mp += (float)(beta[p.n_s + j] * w_mp[(size_t)j * p.ny + y]);
-    dx += mp;
-    const float r = rho[n];
-    const float ux = vps[n], uy = vps[(size_t)N + n], uz = DIM == 3 ? vps[(size_t)2 * N + n] : 0.f;
-    const float du = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
-#pragma unroll
-    for (int i = 0; i < LT::Q; ++i) {
-        const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
-        const float cu = cx * ux + cy * uy + cz * uz;
-        const float cd = cx * dx + cy * dy + cz * dz;
-        T* q = f + (size_t)i * N + n;
-        st_<T>(q, ld_<T>(q) + LT::w(i) * r * (3.0f * cd + 4.5f * cd * (2.0f * cu + cd) - 1.5f * du));
-    }
-}
-
-// Four nodes of one row per thread (nx % 4 == 0): 16-byte (FP32) or 8-byte
-// (16-bit) population accesses and 16-byte field and sensitivity loads.
-template <typename T> struct Vec4;
-template <> struct Vec4<float> {
-    static __device__ __forceinline__ void ld(const float* p, float* v) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    }
-    static __device__ __forceinline__ void st(float* p, const float* v) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-};
-template <> struct Vec4<__half> {
-    static __device__ __forceinline__ void ld(const __half* p, float* v) {
-        const uint2 q = *reinterpret_cast<const uint2*>(p);
-        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-    static __device__ __forceinline__ void st(__half* p, const float* v) {
-        const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
-        uint2 q;
-        q.x = *reinterpret_cast<const unsigned*>(&a);
-        q.y = *reinterpret_cast<const unsigned*>(&b);
-        *reinterpret_cast<uint2*>(p) = q;
-    }
-};
-template <> struct Vec4<__nv_bfloat16> {
-    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float* v) {
-        const uint2 q = *reinterpret_cast<const uint2*>(p);
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, const float* v) {
-        const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
-        uint2 q;
-        q.x = *reinterpret_cast<const unsigned*>(&a);
-        q.y = *reinterpret_cast<const unsigned*>(&b);
-        *reinterpret_cast<uint2*>(p) = q;
-    }
-};
-
-__device__ __forceinline__ void ld4f(const float* p, float* v) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-}
-
-// NS: the number of scale QoIs (1-8, = p.n_s) fixed at compile time, so the
-// sensitivity loop unrolls and every 16-byte field load can be in flight at
-// once (the kernel waits on DRAM latency).
-template <int DIM, typename T, int NS>
-__global__ void __launch_bounds__(128) apply4_kernel(Params p, T* __restrict__ f, const float* __restrict__ rho,
-                                                     const float* __restrict__ vps, VPtrs vk,
-                                                     const double* __restrict__ beta,
-                                                     const double* __restrict__ w_mp) {
-    using LT = Lat<DIM>;
-    const long long n4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n4 >= p.n / 4) return;
-    const size_t N = (size_t)p.n;
-    const size_t n0 = (size_t)n4 * 4;
-    const int y = (int)((n0 / p.nx) % p.ny);
-    if (p.walls && (y == 0 || y == p.ny - 1)) return;
-    float dx[4] = {0.f, 0.f, 0.f, 0.f}, dy[4] = {0.f, 0.f, 0.f, 0.f}, dz[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        const float b = (float)beta[k];
-        const float* v = vk.v[k];
-        float a[4];
-        ld4f(v + n0, a);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) dx[e] += b * a[e];
-        ld4f(v + N + n0, a);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) dy[e] += b * a[e];
-        if (DIM == 3) {
-            ld4f(v + 2 * N + n0, a);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) dz[e] += b * a[e];
-        }
-    }
-    float mp = 0.f;
-    for (int j = 0; j < p.n_mp; ++j) mp += (float)(beta[p.n_s + j] * w_mp[(size_t)j * p.ny + y]);
-    float r[4], ux[4], uy[4], uz[4] = {0.f, 0.f, 0.f, 0.f}, du[4];
-    ld4f(rho + n0, r);
-    ld4f(vps + n0, ux);
-    ld4f(vps + N + n0, uy);
-    if (DIM == 3) ld4f(vps + 2 * N + n0, uz);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        dx[e] += mp;
-        du[e] = dx[e] * (2.0f * ux[e] + dx[e]) + dy[e] * (2.0f * uy[e] + dy[e]) + dz[e] * (2.0f * uz[e] + dz[e]);
-    }
-#pragma unroll
-    for (int i = 0; i < LT::Q; ++i) {
-        const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
-        T* q = f + (size_t)i * N + n0;
-        float g[4];
-        Vec4<T>::ld(q, g);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float cu = cx * ux[e] + cy * uy[e] + cz * uz[e];
-            const float cd = cx * dx[e] + cy * dy[e] + cz * dz[e];
-            g[e] += LT::w(i) * r[e] * (3.0f * cd + 4.5f * cd * (2.0f * cu + cd) - 1.5f * du[e]);
-        }
-        Vec4<T>::st(q, g);
-    }
 }
 
 // f = f^eq(rho, u) on fluid nodes, 0 (= rest) on solid rows; inputs are the
@@ -720,18 +623,18 @@ static void do_init(const Params& p, const Layout& L, const float* drho, const f
     else
         init_feq_kernel<3, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[which], drho, u);
 }
-// moments_kernel for node pairs (nx even): the pair pull of collide2_kernel
+// predict_kernel for node pairs (nx even): the pair pull of collide2_kernel
 // (aligned 2-element loads, x neighbours by warp shuffle), the same moments,
 // 2-element stores.
-template <int DIM, typename T>
-__global__ void __launch_bounds__(128) moments2_kernel(Params p, const T* __restrict__ src, float* __restrict__ vn,
-                                                       const float* __restrict__ kolmo) {
+template <int DIM, typename T, bool WV, bool WN>
+__global__ void __launch_bounds__(128) predict2_kernel(Params p, const T* __restrict__ src, float* __restrict__ vps,
+                                                       float* __restrict__ vn, const float* __restrict__ kolmo) {
     using LT = Lat<DIM>;
     const long long npair = p.n / 2;
     long long pi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = pi < npair;
     if (!live) pi = npair - 1;
-    const int N = (int)p.n;
+    const size_t N = (size_t)p.n;
     const int n0 = (int)(2 * pi);
     const int x0 = n0 % p.nx;
     const int t = n0 / p.nx;
@@ -740,18 +643,26 @@ __global__ void __launch_bounds__(128) moments2_kernel(Params p, const T* __rest
     float g0[LT::Q], g1[LT::Q];
     pull2<DIM, T>(p, src, x0, y, z, n0, g0, g1);
     if (!live) return;
-    float2* v0 = reinterpret_cast<float2*>(vn + n0);
-    float2* v1 = reinterpret_cast<float2*>(vn + (size_t)N + n0);
-    float2* v2 = reinterpret_cast<float2*>(vn + 2 * (size_t)N + n0);
-    if (p.walls && (y == 0 || y == p.ny - 1)) {
-        *v0 = *v1 = *v2 = make_float2(0.f, 0.f);
-        return;
+    float2 vx = make_float2(0.f, 0.f), vy = vx, vz = vx, ux = vx, uy = vx, uz = vx;
+    if (!(p.walls && (y == 0 || y == p.ny - 1))) {
+        const Macro a = macros_of<DIM>(p, g0, kolmo, y);
+        const Macro b = macros_of<DIM>(p, g1, kolmo, y);
+        predictor_velocity(a, vx.x, vy.x, vz.x);
+        predictor_velocity(b, vx.y, vy.y, vz.y);
+        ux = make_float2(a.ux, b.ux);
+        uy = make_float2(a.uy, b.uy);
+        uz = make_float2(a.uz, b.uz);
     }
-    const Macro a = macros_of<DIM>(p, g0, kolmo, y);
-    const Macro b = macros_of<DIM>(p, g1, kolmo, y);
-    *v0 = make_float2(a.ux, b.ux);
-    *v1 = make_float2(a.uy, b.uy);
-    *v2 = make_float2(a.uz, b.uz);
+    if (WV) {
+        *reinterpret_cast<float2*>(vps + n0) = vx;
+        *reinterpret_cast<float2*>(vps + N + n0) = vy;
+        if (DIM == 3) *reinterpret_cast<float2*>(vps + 2 * N + n0) = vz;
+    }
+    if (WN) {
+        *reinterpret_cast<float2*>(vn + n0) = ux;
+        *reinterpret_cast<float2*>(vn + N + n0) = uy;
+        *reinterpret_cast<float2*>(vn + 2 * N + n0) = uz;
+    }
 }
 
 cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* drho, const float* u, int which,
@@ -760,49 +671,63 @@ cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* drho,
     return cudaGetLastError();
 }
 
-template <typename T>
-static void do_moments(const Params& p, const Layout& L, int src, cudaStream_t s) {
-    if (p.nx % 2 == 0) {
-        const unsigned g2 = grid_of(p.n / 2, 128);
-        if (p.dim == 2)
-            moments2_kernel<2, T><<<g2, 128, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
-        else
-            moments2_kernel<3, T><<<g2, 128, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
-        return;
-    }
-    if (p.dim == 2)
-        moments_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
+template <int DIM, typename T, bool WV, bool WN>
+static void do_predict_d(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    const T* a = (const T*)L.f[src];
+    if (p.nx % 2 == 0)
+        predict2_kernel<DIM, T, WV, WN><<<grid_of(p.n / 2, 128), 128, 0, s>>>(p, a, L.vps, L.vn, L.kolmo);
     else
-        moments_kernel<3, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (const T*)L.f[src], L.vn, L.kolmo);
+        predict_kernel<DIM, T, WV, WN><<<grid_of(p.n, 256), 256, 0, s>>>(p, a, L.vps, L.vn, L.kolmo);
 }
-cudaError_t launch_moments(const Params& p, const Layout& L, int src, cudaStream_t s) {
-    LBM_DISPATCH_STORAGE(p, do_moments, p, L, src, s);
+template <typename T>
+static void do_predict(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    const bool wv = p.to_mode != LBM_TO_OFF, wn = p.substrate == LBM_SUBSTRATE_WALE;
+    if (p.dim == 2) {
+        if (wv && wn) do_predict_d<2, T, true, true>(p, L, src, s);
+        else if (wv) do_predict_d<2, T, true, false>(p, L, src, s);
+        else if (wn) do_predict_d<2, T, false, true>(p, L, src, s);
+    } else {
+        if (wv && wn) do_predict_d<3, T, true, true>(p, L, src, s);
+        else if (wv) do_predict_d<3, T, true, false>(p, L, src, s);
+        else if (wn) do_predict_d<3, T, false, true>(p, L, src, s);
+    }
+}
+cudaError_t launch_predict(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    LBM_DISPATCH_STORAGE(p, do_predict, p, L, src, s);
     return cudaGetLastError();
 }
 
-template <int DIM, typename T>
-static void do_collide_d(const Params& p, const Layout& L, int src, cudaStream_t s) {
-    const int fields = p.to_mode != LBM_TO_OFF;
+bool corrector_runs(const Params& p) {
+    return p.to_mode != LBM_TO_OFF && p.to_mode != LBM_TO_OBSERVE;
+}
+
+template <int DIM, typename T, int SUB, bool CORR>
+static void do_collide_k(const Params& p, const Layout& L, int src, cudaStream_t s) {
     const T* a = (const T*)L.f[src];
     T* b = (T*)L.f[1 - src];
-    if (p.nx % 2 == 0 && p.tune.collide_pair) {
-        // node pairs: nx even keeps every pair inside one row and 2-aligned
-        const unsigned g2 = grid_of(p.n / 2, 128);
-        if (p.substrate == LBM_SUBSTRATE_SMAG)
-            collide2_kernel<DIM, T, LBM_SUBSTRATE_SMAG><<<g2, 128, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
-        else if (p.substrate == LBM_SUBSTRATE_WALE)
-            collide2_kernel<DIM, T, LBM_SUBSTRATE_WALE><<<g2, 128, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
-        else
-            collide2_kernel<DIM, T, LBM_SUBSTRATE_NONE><<<g2, 128, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
-        return;
+    VPtrs vk;
+    for (int k = 0; k < kMaxQoi; ++k) vk.v[k] = nullptr;
+    for (int k = 0; k < p.n_s; ++k) {
+        const int slot = p.qoi_filter_slot[k];
+        vk.v[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
     }
-    const unsigned gr = grid_of(p.n, 256);
-    if (p.substrate == LBM_SUBSTRATE_SMAG)
-        collide_kernel<DIM, T, LBM_SUBSTRATE_SMAG><<<gr, 256, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
-    else if (p.substrate == LBM_SUBSTRATE_WALE)
-        collide_kernel<DIM, T, LBM_SUBSTRATE_WALE><<<gr, 256, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
+    if (p.nx % 2 == 0 && p.tune.collide_pair)  // node pairs: nx even keeps every pair inside one row, 2-aligned
+        collide2_kernel<DIM, T, SUB, CORR><<<grid_of(p.n / 2, 128), 128, 0, s>>>(p, a, b, L.vn, L.kolmo, L.st, vk,
+                                                                                 L.betaf, L.mprow);
     else
-        collide_kernel<DIM, T, LBM_SUBSTRATE_NONE><<<gr, 256, 0, s>>>(p, a, b, L.rho, L.vps, L.vn, L.kolmo, L.st, fields);
+        collide_kernel<DIM, T, SUB, CORR><<<grid_of(p.n, 256), 256, 0, s>>>(p, a, b, L.vn, L.kolmo, L.st, vk, L.betaf,
+                                                                            L.mprow);
+}
+template <int DIM, typename T, int SUB>
+static void do_collide_s(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    if (corrector_runs(p)) do_collide_k<DIM, T, SUB, true>(p, L, src, s);
+    else do_collide_k<DIM, T, SUB, false>(p, L, src, s);
+}
+template <int DIM, typename T>
+static void do_collide_d(const Params& p, const Layout& L, int src, cudaStream_t s) {
+    if (p.substrate == LBM_SUBSTRATE_SMAG) do_collide_s<DIM, T, LBM_SUBSTRATE_SMAG>(p, L, src, s);
+    else if (p.substrate == LBM_SUBSTRATE_WALE) do_collide_s<DIM, T, LBM_SUBSTRATE_WALE>(p, L, src, s);
+    else do_collide_s<DIM, T, LBM_SUBSTRATE_NONE>(p, L, src, s);
 }
 template <typename T>
 static void do_collide(const Params& p, const Layout& L, int src, cudaStream_t s) {
@@ -811,47 +736,6 @@ static void do_collide(const Params& p, const Layout& L, int src, cudaStream_t s
 }
 cudaError_t launch_collide(const Params& p, const Layout& L, int src, cudaStream_t s) {
     LBM_DISPATCH_STORAGE(p, do_collide, p, L, src, s);
-    return cudaGetLastError();
-}
-
-template <int DIM, typename T>
-static bool do_apply4(const Params& p, const Layout& L, T* f, const VPtrs& vk, cudaStream_t s) {
-    const unsigned g = grid_of(p.n / 4, 128);
-#define LBM_APPLY4(NS) apply4_kernel<DIM, T, NS><<<g, 128, 0, s>>>(p, f, L.rho, L.vps, vk, L.beta, L.w_mp)
-    switch (p.n_s) {
-        case 1: LBM_APPLY4(1); break;
-        case 2: LBM_APPLY4(2); break;
-        case 3: LBM_APPLY4(3); break;
-        case 4: LBM_APPLY4(4); break;
-        case 5: LBM_APPLY4(5); break;
-        case 6: LBM_APPLY4(6); break;
-        case 7: LBM_APPLY4(7); break;
-        case 8: LBM_APPLY4(8); break;
-        default: return false;  // the configuration allows at most 8 scale QoIs
-    }
-#undef LBM_APPLY4
-    return true;
-}
-
-template <typename T>
-static void do_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) {
-    VPtrs vk;
-    for (int k = 0; k < kMaxQoi; ++k) vk.v[k] = nullptr;
-    for (int k = 0; k < p.n_s; ++k) {
-        const int slot = p.qoi_filter_slot[k];
-        vk.v[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
-    }
-    if (p.nx % 4 == 0 && p.tune.apply4) {
-        if (p.dim == 2 ? do_apply4<2, T>(p, L, (T*)L.f[dst], vk, s) : do_apply4<3, T>(p, L, (T*)L.f[dst], vk, s))
-            return;
-    }
-    if (p.dim == 2)
-        apply_kernel<2, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
-    else
-        apply_kernel<3, T><<<grid_of(p.n, 256), 256, 0, s>>>(p, (T*)L.f[dst], L.rho, L.vps, vk, L.beta, L.w_mp);
-}
-cudaError_t launch_apply(const Params& p, const Layout& L, int dst, cudaStream_t s) {
-    LBM_DISPATCH_STORAGE(p, do_apply, p, L, dst, s);
     return cudaGetLastError();
 }
 

@@ -773,13 +773,21 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L
         if (L.st->status & 1u) fl |= LBM_FLAG_UNSTABLE;
         row[1 + 3 * nq] = (double)fl;
     }
-    // 7. mean profile of the corrected velocity: P_v + sum_k beta_k P_k + nx nz sum_j beta_mp_j w_j
+    // 7. mean profile of the corrected velocity: P_v + sum_k beta_k P_k + nx nz sum_j beta_mp_j w_j;
+    //    the corrector's inputs in FP32: beta_k and, per row, sum_j beta_j w_j(y)
+    if (tid < nq) L.betaf[tid] = (float)beta[tid];
     for (int y = tid; y < p.ny; y += blockDim.x) {
         const double* ps = L.plane_sum + (size_t)y * np1;
         double a = ps[0], b = 0.0;
+        float mp = 0.f;
         for (int k = 0; k < ns; ++k) a = fma(beta[k], ps[1 + k], a);
-        for (int j = 0; j < nmp; ++j) b = fma(beta[ns + j], L.w_mp[(size_t)j * p.ny + y], b);
+        for (int j = 0; j < nmp; ++j) {
+            const double wb = beta[ns + j] * L.w_mp[(size_t)j * p.ny + y];
+            b = fma(beta[ns + j], L.w_mp[(size_t)j * p.ny + y], b);
+            mp += (float)wb;
+        }
         L.profile[y] += fma(a, p.inv_area, b);
+        L.mprow[y] = mp;
     }
     __syncthreads();
     if (tid == 0) {

@@ -227,7 +227,6 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     for (int f = 0; f < 8; ++f) p->tune.filter_per_sm[f] = 0;
     p->tune.march_lines = 148 * 2048;
     p->tune.collide_pair = c->substrate == LBM_SUBSTRATE_WALE ? 0 : 1;
-    p->tune.apply4 = 1;
     p->tune.one_seg = 0;
     if (p->h > 0) {
         const long long rows = (long long)(2 * p->h + 1) * p->n_q + 1;
@@ -273,7 +272,6 @@ static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filt
     l.kolmo = cv.take<float>(p.ny);
     if (c->substrate == LBM_SUBSTRATE_WALE) l.vn = cv.take<float>(3 * N);
     if (p.to_mode != LBM_TO_OFF) {
-        l.rho = cv.take<float>(N);
         l.x6 = cv.take<float>(p.ncomp * N);
         l.vps = l.x6;
         l.t1 = cv.take<float>(p.ncomp * N);
@@ -312,6 +310,8 @@ static size_t carve(const lbm_config* c, const Params& p, const std::vector<Filt
             l.fft_work = cv.take<char>(fft_work_bytes(p));
         }
         l.beta = cv.take<double>(kMaxQoi);
+        l.betaf = cv.take<float>(kMaxQoi);
+        l.mprow = cv.take<float>(p.ny);
         if (p.to_mode == LBM_TO_FIXED_GAMMA) l.gfix = cv.take<double>(kMaxQoi);
         l.ring = cv.take<double>((size_t)p.ring_cap * p.row_len);
         l.profile = cv.take<double>(p.ny);
@@ -536,6 +536,12 @@ static void enqueue_fields(Launcher& lc) {
     LAUNCH(lc, LBM_K_REDUCE, launch_reduce(p, L, vk, lc.s));
 }
 
+// One time step from f[src] into f[1 - src].  TO modes: the predictor pass
+// (v^{p*}, and the post-stream velocity for WALE), the QoI/Gram fields, totals
+// and the solve, then the stream-collide with the SGS corrector applied in
+// registers before the store (Eq. LES-2), so the predictor populations are
+// never written.  Substrate-only runs: the collide (after the velocity pass
+// WALE needs).
 static void enqueue_step(Launcher& lc, int src) {
     lbm_ctx* c = lc.c;
     const Params& p = c->p;
@@ -551,15 +557,16 @@ static void enqueue_step(Launcher& lc, int src) {
         LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, c->side));
         lc.check(cudaEventRecord(c->ev_join, c->side));
     }
-    if (p.substrate == LBM_SUBSTRATE_WALE) LAUNCH(lc, LBM_K_MOMENTS, launch_moments(p, L, src, lc.s));
+    if (p.to_mode != LBM_TO_OFF || p.substrate == LBM_SUBSTRATE_WALE)
+        LAUNCH(lc, LBM_K_MOMENTS, launch_predict(p, L, src, lc.s));
+    if (p.to_mode != LBM_TO_OFF) {
+        if (pre && !fork) LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, lc.s));
+        enqueue_fields(lc);
+        if (fork) lc.check(cudaStreamWaitEvent(lc.s, c->ev_join, 0));
+        LAUNCH(lc, LBM_K_REDUCE, launch_totals(p, L, true, lc.s));
+        LAUNCH(lc, LBM_K_SOLVE, launch_solve(p, L, lc.s));
+    }
     LAUNCH(lc, LBM_K_COLLIDE, launch_collide(p, L, src, lc.s));
-    if (p.to_mode == LBM_TO_OFF) return;
-    if (pre && !fork) LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, lc.s));
-    enqueue_fields(lc);
-    if (fork) lc.check(cudaStreamWaitEvent(lc.s, c->ev_join, 0));
-    LAUNCH(lc, LBM_K_REDUCE, launch_totals(p, L, true, lc.s));
-    LAUNCH(lc, LBM_K_SOLVE, launch_solve(p, L, lc.s));
-    if (p.to_mode != LBM_TO_OBSERVE) LAUNCH(lc, LBM_K_APPLY, launch_apply(p, L, 1 - src, lc.s));
 }
 
 static void count_launches(lbm_ctx* c) {
@@ -763,17 +770,6 @@ static int autotune(lbm_ctx* c) {
         p.tune.collide_pair = pick;
     }
     if (p.to_mode != LBM_TO_OFF) {
-        // SGS apply on the other population copy (overwritten by the next collide)
-        if (p.nx % 4 == 0) {
-            float best = 1e30f;
-            int pick = p.tune.apply4;
-            for (int v = 0; v <= 1; ++v) {
-                p.tune.apply4 = v;
-                const float t = time_ms(c, [&] { chk(launch_apply(p, c->L, 1 - src, c->stream)); }, 5);
-                if (t < best) { best = t; pick = v; }
-            }
-            p.tune.apply4 = pick;
-        }
         const int nc = p.ncomp;
         if (p.dim == 3 && !p.tune.one_seg) {
             static const int cand[] = {2, 4, 8, 16};
@@ -1388,7 +1384,7 @@ int lbm_set_autotune(lbm_ctx* c, int enable) {
 
 int lbm_get_tuning(lbm_ctx* c, int32_t* values, int count) {
     if (!c || !values) return fail(c, LBM_ERR_ARG, "NULL argument");
-    int32_t v[13] = {c->tuned, c->p.tune.collide_pair, c->p.tune.apply4, c->p.tune.march_lines};
+    int32_t v[13] = {c->tuned, c->p.tune.collide_pair, corrector_runs(c->p) ? 1 : 0, c->p.tune.march_lines};
     for (int f = 0; f < 8; ++f) v[4 + f] = c->p.tune.filter_per_sm[f];
     v[12] = c->p.tune.one_seg;
     for (int k = 0; k < count && k < 13; ++k) values[k] = v[k];

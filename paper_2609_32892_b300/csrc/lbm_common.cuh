@@ -34,7 +34,6 @@ struct Taps {
 // Pointers into the caller's buffer, computed once at create time.
 struct Layout {
     void* f[2];          // shifted populations, ping-pong
-    float* rho;          // [N]     density of the predictor state
     float* vps;          // [d][N]  predictor velocity v^{p*} (aliases x6)
     float* vn;           // [3][N]  post-stream velocity (WALE gradients)
     float* kolmo;        // [ny]    Kolmogorov force profile
@@ -63,6 +62,8 @@ struct Layout {
     double* g_mpmp;      // [n_mp][n_mp]
     double* beta;        // [N_Q] SGS coefficients of the current step (beta = G^-1 dQ)
     double* gfix;        // [N_Q] caller's gamma_i (LBM_TO_FIXED_GAMMA)
+    float* betaf;        // [N_Q] beta rounded to FP32 (the collide's SGS corrector)
+    float* mprow;        // [ny]  sum_j beta_j w_j(y) of the bands, FP32, per row
     double* ring;        // [ring_cap][row_len]
     double* profile;     // [ny]
     float2* spec;        // [3][ny][nx/2+1] spectrum of (v_x, v_y, omega) (Fourier bands)
@@ -76,7 +77,6 @@ struct Tune {
     int filter_per_sm[8];  // fused 3-D filter of each distinct filter slot: target blocks per SM (0: default)
     int march_lines;    // 1-D passes along y/z: target threads in flight (line segments)
     int collide_pair;   // node-pair collide when nx is even
-    int apply4;         // 4-node SGS apply when nx % 4 == 0
     int one_seg;        // fused 3-D filters: one z segment per block column (least total work)
 };
 
@@ -106,9 +106,12 @@ struct Params {
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* rho, const float* u, int which,
                             cudaStream_t s);
-cudaError_t launch_moments(const Params& p, const Layout& L, int src, cudaStream_t s);
+// predictor pass: v^{p*} (TO modes) and the post-stream velocity (WALE)
+cudaError_t launch_predict(const Params& p, const Layout& L, int src, cudaStream_t s);
+// stream-collide from f[src] into f[1 - src], with the SGS corrector of the
+// step when corrector_runs(p) (every TO mode but OFF and OBSERVE)
 cudaError_t launch_collide(const Params& p, const Layout& L, int src, cudaStream_t s);
-cudaError_t launch_apply(const Params& p, const Layout& L, int dst, cudaStream_t s);
+bool corrector_runs(const Params& p);
 cudaError_t launch_to_curl(const Params& p, const Layout& L, cudaStream_t s);
 cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t,
                         float scale, int accumulate, cudaStream_t s);

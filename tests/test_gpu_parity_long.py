@@ -9,11 +9,11 @@
 * The multi-block LRS history product at the benchmark's h = 500 (12 QoIs:
   12 013 rows of C in 47 blocks) and at h = 100 (4 QoIs: 805 rows, 4 blocks):
   seeded initial histories and history coefficients large enough that the
-  history term carries dQ.  With C the identity on the q^{n*} block, dQ =
+  history term carries dQ (about 1e-4 of each QoI).  With C the identity on the q^{n*} block, dQ =
   sigma (history term + mu + L z) does not depend on q^{n*} beyond rounding, so
   the first step's dQ must agree to FP64 rounding (1e-9 relative) even though
   q^{n*} agrees only to FP32 (1e-4): a block dropped or misplaced, or a ring
-  slot off by one, changes dQ by about a percent.
+  slot off by one, changes dQ by about a percent (1e7 times the tolerance).
 * The 256^2 Kolmogorov LES shape with h = 100 over 150 steps on 61 x 58.
 
 Tolerances are those of test_gpu_parity.py (FP32 against FP64)."""
@@ -60,7 +60,7 @@ def test_stored_channel_wale_lrs_run(case):
     assert np.all(prof[[0, -1]] == 0.0)
 
 
-def _history_inputs(wl, sigma_ref, seed, coupling=1e-3):
+def _history_inputs(wl, sigma_ref, seed, coupling=1e-4):
     """C: identity on the q^{n*} block, N(0, s^2) on the history rows with s
     chosen so that the history term is about `coupling` in scaled units,
     bias row 0; seeded histories of unit size in scaled units."""
@@ -77,6 +77,12 @@ def _history_inputs(wl, sigma_ref, seed, coupling=1e-3):
 
 @pytest.mark.parametrize("name,kw", [("C3", dict(nx=20, ny=22, nz=13, h=500)), ("C2", dict(nx=37, ny=31, h=100))])
 def test_lrs_history_product_many_blocks(name, kw):
+    """Step 0: dQ to FP64 rounding.  Step 1: the histories hold step 0's q^{n*}
+    and q^n, which agree to FP32, at weights ~1e-6, so dQ still agrees to 1e-6.
+    Later steps: the corrections here are ten times the synthetic model's, and
+    the 12-QoI Gram matrix (condition number ~1e6) turns FP32 rounding of its
+    entries (~3e-7) into ~1e-4 of q^{n*} and of dQ (the oracle itself moves
+    that much when its Gram entries are perturbed by 3e-7), so 1e-3 there."""
     from oracle.sim import Simulation
     from paper_2609_32892_b300 import LbmSim
 
@@ -96,13 +102,14 @@ def test_lrs_history_product_many_blocks(name, kw):
     g.close()
     assert np.all(ro[:, -1] == 0) and np.all(rg[:, -1] == 0)
     q_o, q_g = ro[:, 1:1 + nq], rg[:, 1:1 + nq]
-    np.testing.assert_allclose(q_g, q_o, rtol=1e-4)
     dq_o, dq_g = ro[:, 1 + nq:1 + 2 * nq], rg[:, 1 + nq:1 + 2 * nq]
-    # the history term dominates dQ: about 1e-3 of sigma_ref
-    assert np.all(np.abs(dq_o[0]) > 1e-6 * sref)
+    np.testing.assert_allclose(q_g[0], q_o[0], rtol=1e-4)
+    # the history term dominates dQ: about 1e-4 of sigma_ref
+    assert np.all(np.abs(dq_o[0]) > 1e-7 * sref)
     np.testing.assert_allclose(dq_g[0], dq_o[0], rtol=1e-9, atol=0)
-    # later steps: the histories now hold this run's own q^{n*} (FP32 vs FP64)
-    np.testing.assert_allclose(dq_g[1:], dq_o[1:], rtol=1e-5, atol=0)
+    np.testing.assert_allclose(dq_g[1], dq_o[1], rtol=1e-6, atol=0)
+    np.testing.assert_allclose(q_g[1:], q_o[1:], rtol=1e-3)
+    np.testing.assert_allclose(dq_g[2:], dq_o[2:], rtol=1e-3, atol=0)
 
 
 def test_kolmogorov_lrs_h100_150_steps():

@@ -49,17 +49,10 @@ def _peaks():
     return 6400.0, "fallback"
 
 
-# DRAM traffic of the Laplacian-filter launches (box3_kernel + cross3s_kernel,
-# the two passes of L_3, and crossq3_kernel, the L_1 cross: the dominant kernel
-# class), from one ncu capture on the 320x200x160 channel
-# (profiles/filters_channel3d_320x200x160.md): read+write bytes per launch
-# averaged over the class (two launches of each per step), per lattice node.  It
-# is reported only while the kernel source still has the hash it had when
-# captured.
-TRAFFIC = {
-    "lap3": {"bytes_per_node": (461.013696 + 522.231168 + 462.320256) / 3 * 1e6 / (320 * 200 * 160),
-             "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "170718aa4413ea34"},
-}
+# DRAM traffic per launch and node of each kernel class, read+write bytes from
+# the ncu launch list of the benchmark command (profiles/), reported only while
+# the kernel source still has the hash it had when captured.
+TRAFFIC = {}
 
 
 def _traffic(kind, n_nodes):
@@ -151,25 +144,36 @@ def _lrs_for(wl):
 
 
 def _algorithmic_bytes(wl, n):
-    """Per-class minimal DRAM bytes per launch: what each kernel must read and write per node.
+    """Algorithmic DRAM bytes per launch of each kernel class: the bytes the
+    method's work in that launch must move, per node, times the nodes.
 
-    predict: pull the populations (Q b), write v^{p*} (d x 4) and, with WALE, the
-    post-stream velocity (3 x 4); collide: read and write the populations
-    (2 Q b), read the WALE velocity (3 x 4) and, with the SGS corrector, the
-    sensitivities of the scale QoIs (N_s x d x 4)."""
+    collide   read and write every population once (2 Q b: the stream-collide
+              minimum; the sensitivities its SGS corrector reads and the WALE
+              relaxation time are counted as implementation bytes)
+    predict   read the populations, write v^{p*} (Q b + d 4: the predictor is
+              formed before the collide's store, as f^{p*} is never stored)
+    filters   one application of a compact filter reads and writes the
+              six-component (v, omega) field once, 2 x ncomp x 4 B; the
+              Gaussian R R (two applications) runs as three passes, each
+              credited a third of 2 applications, and L_3 as two passes (box,
+              cross), each credited half an application
+    curl/sens read 3 components, write 3 (24 B); reduce reads v^{p*} and the
+              N_s sensitivities ((1 + N_s) d 4); wale reads u, writes tau (16 B)"""
     q = 19 if wl["dim"] == 3 else 9
     b = {"fp32": 4, "fp16": 2, "bf16": 2}[wl["storage"]]
     d = wl["dim"]
     ncomp = 6 if d == 3 else 3
     to = wl["to_mode"] != "off"
-    corr = to and wl["to_mode"] != "observe"
     ns = len(wl["qois"]) if to else 0
-    wale = wl["substrate"] == "wale"
-    return {
-        "collide": n * (2 * q * b + (3 * 4 if wale else 0) + (ns * d * 4 if corr else 0)),
-        "predict": n * (q * b + (d * 4 if to else 0) + (3 * 4 if wale else 0)),
-        "filter": n * 2 * ncomp * 4,
+    app = 2 * ncomp * 4
+    per_node = {
+        "collide": 2 * q * b,
+        "predict": q * b + (d * 4 if to else 0),
+        "gauss_x": 2 * app / 3, "gauss_z": 2 * app / 3, "gauss_y": 2 * app / 3,
+        "box3": app / 2, "cross3s": app / 2, "lap1": app, "filter": app,
+        "curl": 2 * 3 * 4, "sens": 2 * 3 * 4, "reduce": (1 + ns) * d * 4, "wale": 16,
     }
+    return {k: v * n for k, v in per_node.items()}
 
 
 def run_ours(args, world, rank, local):
@@ -236,55 +240,41 @@ def run_ours(args, world, rank, local):
     B.lbm_profile(sim.ctx, 0)
     algo = _algorithmic_bytes(wl, n_nodes)
     peak, peak_kind = _peaks()
-    dominant = max(prof, key=lambda k: prof[k][0])
     sections = {}
     for k, (tms, cnt) in prof.items():
         if cnt:
             ent = {"ms_per_launch": tms / cnt, "launches_per_step": cnt / args.profile_steps,
                    "ms_per_step": tms / args.profile_steps}
             if k in algo:
-                ent["gbs"] = algo[k] / (tms / cnt * 1e-3) / 1e9
+                ent["algorithmic_gbs"] = algo[k] / (tms / cnt * 1e-3) / 1e9
             sections[k] = ent
     flops = B.lbm_filter_flops_per_step(sim.ctx)
-    for k in ("gauss3", "lap3"):
+    for k in ("gauss_x", "gauss_z", "gauss_y", "box3", "cross3s", "lap1", "filter"):
         if k in sections and flops[k] > 0:
             sections[k]["tflops"] = flops[k] / (sections[k]["ms_per_step"] * 1e-3) / 1e12
-            sections[k]["flops_per_step"] = flops[k]
-    roof = None
+    # the dominant kernel: the class with the largest time per step (each class
+    # is one kernel); achieved = its algorithmic bytes per launch / its mean
+    # CUDA-event launch time
+    dominant = max(prof, key=lambda k: prof[k][0])
+    tms, cnt = prof[dominant]
+    avg_ms = tms / cnt
+    roof = {"kernel": dominant, "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+            "avg_launch_ms": round(avg_ms, 5), "algorithmic_bytes_per_launch": algo.get(dominant),
+            "share_of_step": round(tms / args.profile_steps / sum(v[0] / args.profile_steps for v in prof.values()), 4)}
     if dominant in algo:
-        avg_ms = prof[dominant][0] / prof[dominant][1]
         ach = algo[dominant] / (avg_ms * 1e-3) / 1e9
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "peak_kind": peak_kind, "traffic": None,
-                "bytes_per_launch": algo[dominant], "avg_launch_ms": avg_ms}
-    elif dominant in ("gauss3", "lap3") and flops[dominant] > 0:
-        # a fused filter launch reads and writes the six-component field once
-        # (48 B per node); its bound is the roofline's: HBM when its algorithmic
-        # FLOP per byte is below the ridge (FP32 peak / measured HBM), else FP32
-        tms, cnt = prof[dominant]
-        per_launch = flops[dominant] / (cnt / args.profile_steps)
-        bytes_launch = n_nodes * 2 * 6 * 4
-        avg_ms = tms / cnt
-        tflops = per_launch / (avg_ms * 1e-3) / 1e12
-        gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
-        intensity = per_launch / bytes_launch
-        ridge = FP32_PEAK_TFLOPS * 1e3 / peak
         tr = _traffic(dominant, n_nodes)
-        common = {"kernel": dominant, "traffic": None if tr is None else round(tr),
-                  "traffic_unit": "bytes per launch (ncu, scaled by nodes)", "algorithmic_bytes_per_launch": bytes_launch,
-                  "flops_per_launch": per_launch, "flop_per_byte": round(intensity, 2), "ridge_flop_per_byte": round(ridge, 2),
-                  "avg_launch_ms": avg_ms, "tflops": round(tflops, 3), "hbm_gbs": round(gbs, 1)}
-        if intensity < ridge:
-            roof = dict(common, bound="hbm", achieved=round(gbs, 1), peak=peak, unit="GB/s", frac=round(gbs / peak, 4),
-                        peak_kind=peak_kind)
-        else:
-            roof = dict(common, bound="alu", achieved=round(tflops, 3), peak=round(FP32_PEAK_TFLOPS, 2), unit="TFLOP/s",
-                        frac=round(tflops / FP32_PEAK_TFLOPS, 4),
-                        peak_kind="derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz")
+        roof.update(achieved=round(ach, 1), frac=round(ach / peak, 4),
+                    traffic=None if tr is None else round(tr), traffic_unit="bytes per launch (ncu dram read+write)")
     coll = prof["collide"]
     coll_gbs = algo["collide"] / (coll[0] / coll[1] * 1e-3) / 1e9 if coll[1] else None
-    step_gbs = n_nodes * (2 * (19 if wl["dim"] == 3 else 9) * (4 if wl["storage"] == "fp32" else 2)
-                          + (2 * (1 + wl["dim"]) * 4 if nq else 0)) / (ms_per_step * 1e-3) / 1e9
+    # the whole step against the algorithmic bytes per node of Sec. 8(d): 2 Q b,
+    # plus the round trip of rho and v^{p*} when the TO phase runs
+    step_bytes = n_nodes * (2 * (19 if wl["dim"] == 3 else 9) * (4 if wl["storage"] == "fp32" else 2)
+                            + (2 * (1 + wl["dim"]) * 4 if nq else 0))
+    step_gbs = step_bytes / (ms_per_step * 1e-3) / 1e9
+    roof["step"] = {"algorithmic_bytes_per_node": step_bytes / n_nodes, "achieved": round(step_gbs, 1),
+                    "frac": round(step_gbs / peak, 4), "ms_per_step": round(ms_per_step, 4)}
 
     # end to end through the C ABI with host buffers: upload the initial field
     # and the LRS coefficients, step, drain the QoI block, read the status
@@ -337,8 +327,8 @@ def run_serving(args, device):
 
     from paper_2609_32892_b300 import serve
 
-    reqs32 = serve.scaled_mix(args.serve_n, 7, 1.0, args.serve_scale, "fp32")
-    reqs16 = serve.scaled_mix(args.serve_n, 7, 1.0, args.serve_scale, "fp16")
+    reqs32 = synthetic.serving_requests(args.serve_n, 7, 1.0, args.serve_scale, "fp32")
+    reqs16 = synthetic.serving_requests(args.serve_n, 7, 1.0, args.serve_scale, "fp16")
     res = {"requests": args.serve_n, "horizon_scale": args.serve_scale,
            "mix": "2-D Kolmogorov 128^2-512^2 (Smagorinsky + TO-LRS, 4 QoIs) and 3-D channel "
                   "48x20x24-96x40x48 (WALE + TO-LRS, 12 QoIs), horizons log-uniform 1e3-1e4 steps x scale"}
@@ -360,7 +350,7 @@ def run_serving(args, device):
     res["serial_fp32"] = serve.serial_baseline(reqs32, device)
     # Poisson arrivals at the batched FP32 capacity (members per second)
     rate = args.serve_n / w32
-    reqs_rt = serve.scaled_mix(args.serve_n, 8, rate, args.serve_scale, "fp32")
+    reqs_rt = synthetic.serving_requests(args.serve_n, 8, rate, args.serve_scale, "fp32")
     out_rt, w_rt, _ = srv.serve(reqs_rt, chunk=args.serve_chunk, realtime=True)
     res["poisson_fp32"] = dict(serve.summarize(out_rt, w_rt), offered_members_per_s=round(rate, 2))
     srv.close()
@@ -492,32 +482,67 @@ def run_reference_series(args, device):
     return out
 
 
-def cpu_oracle_sample(wl, seconds=15.0):
-    """The oracle (as it stands) stepping a bounded sample of the workload:
-    the same physics and QoI set on a 48x40x24 sub-grid, timed for ~`seconds`."""
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or "unknown"
+
+
+def _oracle_mlups(wl, seconds, max_steps=None):
+    """Steps of the oracle (as it stands) on workload wl for about `seconds`."""
     from oracle.sim import Simulation
 
-    sw = dict(wl, nx=48, ny=40, nz=24)
-    if sw["to_mode"] == "lrs":
-        sw["h"] = min(sw["h"], 500)
-    nq = len(sw["qois"]) + sw["n_mp"] if sw["to_mode"] != "off" else 0
+    nq = len(wl["qois"]) + wl["n_mp"] if wl["to_mode"] != "off" else 0
     lrs = None
-    if sw["to_mode"] == "lrs":
-        c, mu, sig = _lrs_for(sw)
+    if wl["to_mode"] == "lrs":
+        c, mu, sig = _lrs_for(wl)
         lrs = (c, mu, sig, np.ones(nq))
-    sim = Simulation(sw, synthetic.initial_velocity(sw), lrs=lrs)
+    sim = Simulation(wl, synthetic.initial_velocity(wl), lrs=lrs)
     n = 0
     t0 = time.perf_counter()
     while True:
         sim.step()
         n += 1
-        if time.perf_counter() - t0 > seconds:
+        if time.perf_counter() - t0 > seconds or (max_steps and n >= max_steps):
             break
     dt = time.perf_counter() - t0
+    nodes = wl["nx"] * wl["ny"] * wl["nz"]
+    return nodes * n / dt / 1e6, n, dt
+
+
+def cpu_oracle_sample(wl, seconds=15.0):
+    """The FP64 oracle (as it stands: numpy, one thread) on the host cores.
+
+    value: the benchmark step's physics (WALE + TO-LRS, 12 QoIs) on a 48x40x24
+    sub-grid of the channel for about `seconds`; beside it the plain BGK step
+    of the 480x200x240 channel on a 480x200x8 slab (MLUPS) and the 64^2
+    Kolmogorov workload end to end (its 2000 steps, seconds)."""
+    sw = dict(wl, nx=48, ny=40, nz=24)
+    if sw["to_mode"] == "lrs":
+        sw["h"] = min(sw["h"], 500)
+    v, n, dt = _oracle_mlups(sw, seconds)
+    extra = {}
+    try:
+        bgk = synthetic.workload("C4", nz=8)
+        m4, n4, t4 = _oracle_mlups(bgk, seconds / 3, max_steps=20)
+        extra["bgk_480x200_slab"] = {"mlups": round(m4, 4), "steps": n4, "seconds": round(t4, 2),
+                                     "grid": [480, 200, 8]}
+        c1 = synthetic.workload("C1")
+        m1, n1, t1 = _oracle_mlups(c1, 120.0, max_steps=c1["steps"])
+        extra["kolmogorov64_end_to_end"] = {"steps": n1, "seconds": round(t1, 2), "mlups": round(m1, 4)}
+    except MemoryError:
+        pass
     nodes = sw["nx"] * sw["ny"] * sw["nz"]
-    return {"value": round(nodes * n / dt / 1e6, 6), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    return {"value": round(v, 6), "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"{n} full steps of the same workload physics on a 48x40x24 sub-grid ({nodes} nodes), "
-                      f"FP64 numpy, single thread, {dt:.1f} s"}
+                      f"FP64 numpy, single thread, {dt:.1f} s",
+            "host_cores": os.cpu_count(), "cpu_model": _cpu_model(), **extra}
 
 
 def main():
@@ -593,7 +618,7 @@ def main():
                 "data": "synthetic (seeded laminar channel + 5% noise, synthetic LRS coefficients)",
                 "config": config, "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
                 "gpu_launches": int(r["launches"] * args.steps), "clocks": r["clocks"],
-                "step_hbm_gbs": round(r["step_gbs"], 1), "collide_gbs": r["collide_gbs"],
+                "step_hbm_gbs": round(r["step_gbs"], 1), "collide_algorithmic_gbs": r["collide_gbs"],
                 "sections": r["sections"], "tuning": r["tuning"], "bgk_480x200x240": r["bgk"], "serving": serving,
                 "hf_reference": reference, "storage_precision": precision}
         print(json.dumps(line), flush=True)

@@ -55,7 +55,7 @@ typedef enum {
     LBM_ERR_CUDA = 3,           /* a CUDA runtime call failed                   */
     LBM_ERR_UNSTABLE = 4,       /* non-finite state, rho <= 0 or |v| > c_s      */
     LBM_ERR_SINGULAR_GRAM = 5,  /* reported through QoI flags, not as a status  */
-    LBM_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                */
+    LBM_ERR_TIMEOUT = 6,        /* a kernel's bounded wait on its bulk copies gave up */
     LBM_ERR_STATE = 7           /* call not valid in the current state          */
 } lbm_status;
 
@@ -193,7 +193,9 @@ int lbm_set_track_reference(lbm_ctx* ctx, const double* qref, int64_t len);
  * of previously completed work only; instabilities surface at lbm_sync. */
 int lbm_step(lbm_ctx* ctx, int64_t nsteps);
 
-/* Wait for queued work; ERR_UNSTABLE if any step saw an unstable state. */
+/* Wait for queued work; ERR_UNSTABLE if any step saw an unstable state,
+ * ERR_TIMEOUT if a kernel's bounded wait for its asynchronous bulk copies gave
+ * up (the step's results are then not valid). */
 int lbm_sync(lbm_ctx* ctx);
 
 /* Drain QoI block rows written since the last drain into out[capacity][row_len]
@@ -237,10 +239,16 @@ enum {
     LBM_K_CURL = 2, LBM_K_FILTER = 3, LBM_K_SENS = 4,
     LBM_K_REDUCE = 5, LBM_K_LRS = 6, LBM_K_SOLVE = 7,
     LBM_K_APPLY = 8,    /* reserved: the corrector runs inside the collide */
-    LBM_K_GAUSS3 = 9,  /* fused 3-D Gaussian / binomial filter applications */
-    LBM_K_LAP3 = 10,   /* 3-D Laplacian filters: L_1 one launch, L_3 two    */
-    LBM_K_FFT = 11,    /* cuFFT transforms of the Fourier-band filters      */
-    LBM_K_COUNT = 12
+    LBM_K_GAUSS_X = 9,   /* R R of a 3-D Gaussian / binomial filter: x pass     */
+    LBM_K_LAP1 = 10,     /* 3-D L_1 cross (or a one-pass Laplacian kernel)      */
+    LBM_K_FFT = 11,      /* cuFFT transforms of the Fourier-band filters        */
+    LBM_K_WALE = 12,     /* reserved: WALE runs inside the collide              */
+    LBM_K_GAUSS_Z = 13,  /* R R of a 3-D Gaussian / binomial filter: z pass     */
+    LBM_K_GAUSS_Y = 14,  /* R R of a 3-D Gaussian / binomial filter: y pass     */
+    LBM_K_BOX3 = 15,     /* L_3 pass 1: the 3x3x3 box                           */
+    LBM_K_CROSS3S = 16,  /* L_3 pass 2: the cross of l at stride 3              */
+    LBM_K_TOTALS = 17,   /* cross-block sums of the reduction partials          */
+    LBM_K_COUNT = 18
 };
 int lbm_set_graphs(lbm_ctx* ctx, int enable);
 
@@ -390,12 +398,14 @@ int lbm_batch_stats(lbm_batch* b, size_t* free_bytes, size_t* largest, int32_t* 
  * that owns every device allocation through its own arena, and real-time
  * loops that cannot afford the implicit device synchronisation of an
  * allocation.  It computes the same scale-aware QoIs as the TO phase of
- * lbm_step (q_i = E_R or Z_R of Sec. 4.1 for each cfg->qoi[i]) for a field
- * the caller supplies, using only a scratch array compiled into the library.
+ * lbm_step (the Tau-orthogonal SGS forcing step) reports for each
+ * cfg->qoi[i], for a field the caller supplies, using only a scratch array
+ * compiled into the library.
  *
- *   cfg     grid (dim, nx, ny, nz, walls) and the scale-aware QoIs
- *           (n_qoi >= 1, qoi[]); mean-profile bands are not supported
- *           (n_mp must be 0); to_mode and the LBM fields are ignored
+ *   cfg     grid (dim, nx, ny, nz, walls) and the scale-aware QoIs:
+ *           n_qoi in 1..8, Gaussian, Laplacian or binomial filters
+ *           (LBM_FILTER_FOURIER is refused); mean-profile bands are not
+ *           supported (n_mp must be 0); to_mode and the LBM fields are ignored
  *   u       device pointer, FP32 velocity [3][nz][ny][nx] (z component
  *           ignored in 2-D); values on solid rows are treated as zero
  *   q       device pointer, receives n_qoi doubles
@@ -406,12 +416,14 @@ int lbm_batch_stats(lbm_batch* b, size_t* free_bytes, size_t* largest, int32_t* 
  * set must fit in it (about 200 bytes per node for six 3-D QoIs over three
  * filters); larger requests return LBM_ERR_BUDGET and say how many bytes they
  * would need.  Nothing is allocated: no cudaMalloc, no cudaFree, no
- * allocating library call.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress with that device current);
- * make that first call before any stream capture begins.  Every call shares
- * the one array and it keeps the previous call's contents, so calls whose
- * work overlaps on the GPU (other streams, other host threads) race with
- * each other; serialise them.
+ * allocating library call.  The first call in each CUDA context (each
+ * device's primary context, a context recreated after cudaDeviceReset, or a
+ * context of the caller's own) looks up the array's device address
+ * (cudaGetSymbolAddress with that context current) and caches it under the
+ * context's unique id; make that first call before any stream capture
+ * begins.  Every call shares the one array and it keeps the previous call's
+ * contents, so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race with each other; serialise them.
  * Errors: LBM_ERR_ARG (invalid grid or QoI set), LBM_ERR_BUDGET (too large
  * for the scratch), LBM_ERR_CUDA; the text is lbm_last_error(NULL, ...). */
 #define LBM_STATIC_SCRATCH_BYTES (64u << 20)

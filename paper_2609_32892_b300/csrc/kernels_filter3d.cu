@@ -1,16 +1,15 @@
-// Fused 3-D compact filters (Sec. 4.1): one kernel applies a whole filter.
+// Fused 3-D Laplacian filters L_s (Sec. 4.1, Eq. laplace): one kernel (or,
+// for L_3, two streams) per filter application.  The Gaussian and binomial
+// filters are applied twice at once by the streaming passes of kernels_gauss.cu.
 //
 // A block owns a TX x TY tile of (x, y) and marches along a segment of z.
 // For every input plane it stages the tile plus halo in shared memory
 // (coalesced loads, prefetched into registers one plane ahead), applies the
-// x and y factors with register sliding windows (a thread produces 8 x-values
-// of a row from 8 + 2R staged values, or RPT y-values of a column from
-// RPT + 2R), and pushes the result into per-thread register rings along z,
-// from which the z factor produces one output plane per step.  Each input
+// in-plane terms, and pushes the result into per-thread register rings along
+// z, from which the z terms produce one output plane per step.  Each input
 // element is read from DRAM about once per application (halo re-reads hit L2)
 // and each output written once.
 //
-//   gauss3_kernel<R>      G_s (or B3): the same (2R+1)-tap factor on x, y, z
 //   lap3_kernel<RA, RB>   L_s = c sum_a [l dilated along a] x [box_s on the
 //                         other two axes], arm radius RA = (5s-1)/2, box
 //                         radius RB = (s-1)/2 (RB = 0: the box is the identity;
@@ -83,97 +82,6 @@ struct TileLoader {
         }
     }
 };
-
-// 8 consecutive outputs of a 1-D convolution along a shared-memory row:
-// out[j] = sum_r t(r) row[j + R - r], row 16-byte aligned, 8 + 2R values used.
-template <int R>
-__device__ __forceinline__ void conv8(const float* row, const float* t, float* out) {
-    constexpr int NV = round4(8 + 2 * R);
-    float v[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k += 4) {
-        const float4 q = *reinterpret_cast<const float4*>(row + k);
-        v[k] = q.x; v[k + 1] = q.y; v[k + 2] = q.z; v[k + 3] = q.w;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        float s = 0.f;
-#pragma unroll
-        for (int r = -R; r <= R; ++r) s += t[r + R] * v[j + R - r];
-        out[j] = s;
-    }
-}
-
-template <int R>
-__global__ void __launch_bounds__(128) gauss3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                     T3<R> tp, float scale, int accumulate, int ncomp, int seg) {
-    constexpr int NT = 128, RPT = TY / (NT / TX);  // 4 output rows per thread
-    using LD = TileLoader<R, NT>;
-    constexpr int WP = LD::WP, HH = LD::HH;
-    __shared__ __align__(16) float tile[HH * WP];
-    __shared__ __align__(16) float xt[HH * TX];
-    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
-    const int nz = p.nz;
-    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int lx = threadIdx.x % TX, yr = threadIdx.x / TX;
-    const int x = x0 + lx;
-    const size_t N = (size_t)p.n;
-    const float* a = in + c * N;
-    float* o = out + c * N;
-    float ring[RPT][2 * R + 1];
-#pragma unroll
-    for (int j = 0; j < RPT; ++j)
-#pragma unroll
-        for (int k = 0; k < 2 * R + 1; ++k) ring[j][k] = 0.f;
-    LD ld;
-    ld.init(p, x0, y0);
-    int zq = pm(z0 - R, nz);  // z index of the plane loaded last (advanced by one per plane)
-    ld.load(p, a, zq);
-    // Two barriers per plane: the x factor reads `tile` only before the second
-    // barrier and the y factor reads `xt` only before the next plane's first,
-    // so the next plane's stores cannot overtake a reader.
-    for (int q = z0 - R; q < z1 + R; ++q) {
-        ld.store(tile);
-        __syncthreads();
-        zq = zq + 1 == nz ? 0 : zq + 1;
-        if (q + 1 < z1 + R) ld.load(p, a, zq);
-        // x factor: task = (tile row, 8-wide segment)
-        for (int task = threadIdx.x; task < HH * (TX / 8); task += NT) {
-            const int ry = task / (TX / 8), k = task % (TX / 8);
-            float r8[8];
-            conv8<R>(tile + ry * WP + 8 * k, tp.t, r8);
-            float4* dst = reinterpret_cast<float4*>(xt + ry * TX + 8 * k);
-            dst[0] = make_float4(r8[0], r8[1], r8[2], r8[3]);
-            dst[1] = make_float4(r8[4], r8[5], r8[6], r8[7]);
-        }
-        __syncthreads();
-        // y factor: RPT consecutive rows of column lx from RPT + 2R values
-        float col[RPT + 2 * R];
-#pragma unroll
-        for (int m = 0; m < RPT + 2 * R; ++m) col[m] = xt[(yr * RPT + m) * TX + lx];
-        const int zo = q - R;
-#pragma unroll
-        for (int j = 0; j < RPT; ++j) {
-            float s = 0.f;
-#pragma unroll
-            for (int r = -R; r <= R; ++r) s += tp.t[r + R] * col[j + R - r];
-#pragma unroll
-            for (int k = 0; k < 2 * R; ++k) ring[j][k] = ring[j][k + 1];
-            ring[j][2 * R] = s;
-            const int y = y0 + yr * RPT + j;
-            if (zo >= z0 && x < p.nx && y < p.ny) {
-                float v = 0.f;
-#pragma unroll
-                for (int r = -R; r <= R; ++r) v += tp.t[r + R] * ring[j][R - r];
-                const bool solid = p.walls && (y == 0 || y == p.ny - 1);
-                v = solid ? 0.f : scale * v;
-                float* op = o + ((size_t)zo * p.ny + y) * p.nx + x;
-                *op = accumulate ? (*op + v) : v;
-            }
-        }
-    }
-}
 
 // L_s with a box (s > 1): double-buffered shared arrays, two barriers per
 // plane.  Phase A (after the tile of plane q is stored): box along y on the
@@ -383,18 +291,6 @@ int seg_len(const Params& p, int blocks_xy, int ncomp, int R, int per_sm) {
     if (seg < R) seg = R;
     if (seg > p.nz) seg = p.nz;
     return seg;
-}
-
-template <int R>
-cudaError_t run_gauss(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale, int acc,
-                      int per_sm, cudaStream_t s) {
-    T3<R> tp;
-    for (int i = 0; i < 2 * R + 1; ++i) tp.t[i] = t.t[i];
-    const int bx = (p.nx + TX - 1) / TX, by = (p.ny + TY - 1) / TY;
-    const int seg = seg_len(p, bx * by, ncomp, R, per_sm > 0 ? per_sm : 8);
-    const int nseg = (p.nz + seg - 1) / seg;
-    gauss3_kernel<R><<<dim3(bx, by, ncomp * nseg), 128, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
-    return cudaGetLastError();
 }
 
 template <int RA, int RB>
@@ -746,18 +642,6 @@ cudaError_t launch_cross3s(const Params& p, const float* in, float* out, int nco
     const int nseg = (p.nz + seg - 1) / seg;
     cross3s_kernel<<<dim3(bx, by, ncomp * nseg), cs3::NT, 0, s>>>(p, in, out, scale, accumulate, ncomp, seg);
     return cudaGetLastError();
-}
-
-// G_s / B3 in 3-D with the same 1-D taps on every axis.
-cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
-                          int accumulate, int per_sm, cudaStream_t s) {
-    switch (t.radius) {
-        case 1: return run_gauss<1>(p, in, out, ncomp, t, scale, accumulate, per_sm, s);
-        case 2: return run_gauss<2>(p, in, out, ncomp, t, scale, accumulate, per_sm, s);
-        case 4: return run_gauss<4>(p, in, out, ncomp, t, scale, accumulate, per_sm, s);
-        case 6: return run_gauss<6>(p, in, out, ncomp, t, scale, accumulate, per_sm, s);
-        default: return cudaErrorNotSupported;
-    }
 }
 
 // L_s in 3-D for s = 1 (arm radius 2, no box) and s = 3 (arm 7, box 1).

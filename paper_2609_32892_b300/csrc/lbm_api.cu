@@ -357,6 +357,42 @@ static Taps box_taps(int s) {
     for (int m = 0; m < s; ++m) t.t[m] = 1.0f;
     return t;
 }
+// The 3-D Gaussian (alpha = 2) or binomial 1-D kernel t and its
+// self-convolution t * t, both from double (the factor R R applies along a
+// periodic axis)
+static GaussTaps gauss_pair_taps(const Filter& f) {
+    GaussTaps g;
+    memset(&g, 0, sizeof g);
+    double t[13] = {0.0};
+    int r = 1;
+    if (f.kind == LBM_FILTER_BINOMIAL) {
+        t[0] = 0.25; t[1] = 0.5; t[2] = 0.25;
+    } else {
+        r = 2 * f.scale;
+        double sum = 0.0;
+        for (int k = -r; k <= r; ++k) {
+            t[k + r] = exp(-(double)(k * k) / (2.0 * f.scale * f.scale));
+            sum += t[k + r];
+        }
+        for (int k = 0; k <= 2 * r; ++k) t[k] /= sum;
+    }
+    g.radius = r;
+    for (int k = 0; k <= 2 * r; ++k) g.t[k] = (float)t[k];
+    for (int k = 0; k <= 4 * r; ++k) {
+        double c = 0.0;
+        for (int i = 0; i <= 2 * r; ++i)
+            if (k - i >= 0 && k - i <= 2 * r) c += t[i] * t[k - i];
+        g.c[k] = (float)c;
+    }
+    return g;
+}
+
+// R R of a Gaussian / binomial filter through launch_gauss_rr (3-D fields)
+static bool gauss_rr_path(const Params& p, const Filter& f) {
+    if (p.dim != 3 || (f.kind != LBM_FILTER_GAUSS && f.kind != LBM_FILTER_BINOMIAL)) return false;
+    return launch_gauss_rr_supported(f.kind == LBM_FILTER_BINOMIAL ? 1 : 2 * f.scale);
+}
+
 static Taps binom_taps() {
     Taps t;
     memset(&t, 0, sizeof t);
@@ -429,29 +465,24 @@ static void enqueue_filter(Launcher& lc, const Filter& f, int slot, const float*
     float* t1 = c->L.t1;
     float* t2 = c->L.t2;
     const double flops = 2.0 * filter_taps(f, d) * nc * (double)p.n;
-    if (d == 3) {
-        // fused 3-D kernels: the whole filter in one pass over the field
-        if (f.kind == LBM_FILTER_GAUSS || f.kind == LBM_FILTER_BINOMIAL) {
-            const Taps t = f.kind == LBM_FILTER_GAUSS ? gauss_taps(f.scale, d) : binom_taps();
-            if (launch_gauss3_supported(t.radius)) {
-                if (lc.count_only) c->filter_flops[LBM_K_GAUSS3] += flops;
-                LAUNCH(lc, LBM_K_GAUSS3, launch_gauss3(p, in, out, nc, t, 1.f, 0, p.tune.filter_per_sm[slot], lc.s));
-                return;
+    if (d == 3 && f.kind == LBM_FILTER_LAPLACE && launch_lap3_supported(f.scale)) {
+        // fused 3-D kernels: the whole filter in one pass over the field, or
+        // L_3 = c C_3 * B_3 in two streams through the scratch field
+        const float scale = (float)(1.0 / (8.0 * d * (double)f.scale * f.scale * f.scale));
+        const double n = (double)nc * (double)p.n;
+        if (lap3_split(p, f.scale)) {
+            if (lc.count_only) {
+                c->filter_flops[LBM_K_BOX3] += 2.0 * d * f.scale * n;   // s taps per axis
+                c->filter_flops[LBM_K_CROSS3S] += 2.0 * (4.0 * d + 1.0) * n;
             }
-        } else if (launch_lap3_supported(f.scale)) {
-            const float scale = (float)(1.0 / (8.0 * d * (double)f.scale * f.scale * f.scale));
-            if (lc.count_only) c->filter_flops[LBM_K_LAP3] += flops;
-            if (lap3_split(p, f.scale)) {
-                // L_3 = c C_3 * B_3 in two streams over the field: the box into
-                // the scratch field, then the cross at stride 3
-                LAUNCH(lc, LBM_K_LAP3, launch_box3(p, in, t1, nc, p.tune.filter_per_sm[slot], lc.s));
-                LAUNCH(lc, LBM_K_LAP3, launch_cross3s(p, t1, out, nc, scale, 0, p.tune.filter_per_sm[slot], lc.s));
-                return;
-            }
-            LAUNCH(lc, LBM_K_LAP3,
-                   launch_lap3(p, in, out, nc, f.scale, ell_taps(f.scale), scale, 0, p.tune.filter_per_sm[slot], lc.s));
+            LAUNCH(lc, LBM_K_BOX3, launch_box3(p, in, t1, nc, p.tune.filter_per_sm[slot], lc.s));
+            LAUNCH(lc, LBM_K_CROSS3S, launch_cross3s(p, t1, out, nc, scale, 0, p.tune.filter_per_sm[slot], lc.s));
             return;
         }
+        if (lc.count_only) c->filter_flops[LBM_K_LAP1] += flops;
+        LAUNCH(lc, LBM_K_LAP1,
+               launch_lap3(p, in, out, nc, f.scale, ell_taps(f.scale), scale, 0, p.tune.filter_per_sm[slot], lc.s));
+        return;
     }
     if (lc.count_only) c->filter_flops[LBM_K_FILTER] += flops;
     if (d == 2 && !p.walls) {
@@ -522,6 +553,18 @@ static void enqueue_fields(Launcher& lc) {
             LAUNCH(lc, LBM_K_FILTER, launch_band_mask(p, L.spec, L.spec_band, 3, fl.scale, fl.hi, lc.s));
             LIBCALL(lc, LBM_K_FFT, (cufftSetStream(c->fft_c2r, lc.s),
                                     cufftExecC2R(c->fft_c2r, (cufftComplex*)L.spec_band, (cufftReal*)L.rr[f])));
+        } else if (gauss_rr_path(p, fl)) {
+            // R R in three streaming passes with the composite kernel t * t
+            const GaussTaps gt = gauss_pair_taps(fl);
+            if (lc.count_only) {
+                const double fl1 = 2.0 * (4.0 * gt.radius + 1.0) * p.ncomp * (double)p.n;  // one composite pass
+                c->filter_flops[LBM_K_GAUSS_X] += fl1;
+                c->filter_flops[LBM_K_GAUSS_Z] += fl1;
+                c->filter_flops[LBM_K_GAUSS_Y] += fl1;
+            }
+            LAUNCH(lc, LBM_K_GAUSS_X, launch_gauss_pass(p, 0, L.x6, L.t1, p.ncomp, gt, L.st, lc.s));
+            LAUNCH(lc, LBM_K_GAUSS_Z, launch_gauss_pass(p, 2, L.t1, L.t2, p.ncomp, gt, L.st, lc.s));
+            LAUNCH(lc, LBM_K_GAUSS_Y, launch_gauss_pass(p, 1, L.t2, L.rr[f], p.ncomp, gt, L.st, lc.s));
         } else {
             enqueue_filter(lc, fl, (int)f, L.x6, L.acc);
             enqueue_filter(lc, fl, (int)f, L.acc, L.rr[f]);
@@ -563,7 +606,7 @@ static void enqueue_step(Launcher& lc, int src) {
         if (pre && !fork) LAUNCH(lc, LBM_K_LRS, launch_lrs_pre(p, L, lc.s));
         enqueue_fields(lc);
         if (fork) lc.check(cudaStreamWaitEvent(lc.s, c->ev_join, 0));
-        LAUNCH(lc, LBM_K_REDUCE, launch_totals(p, L, true, lc.s));
+        LAUNCH(lc, LBM_K_TOTALS, launch_totals(p, L, true, lc.s));
         LAUNCH(lc, LBM_K_SOLVE, launch_solve(p, L, lc.s));
     }
     LAUNCH(lc, LBM_K_COLLIDE, launch_collide(p, L, src, lc.s));
@@ -775,21 +818,19 @@ static int autotune(lbm_ctx* c) {
             static const int cand[] = {2, 4, 8, 16};
             for (size_t f = 0; f < c->filters.size() && f < 8; ++f) {
                 const Filter& fl = c->filters[f];
-                const bool lap = fl.kind == LBM_FILTER_LAPLACE;
-                if (lap ? !launch_lap3_supported(fl.scale) : !launch_gauss3_supported(
-                                                               fl.kind == LBM_FILTER_GAUSS ? gauss_taps(fl.scale, 3).radius : 1))
-                    continue;
-                const Taps t0 = lap ? ell_taps(fl.scale) : (fl.kind == LBM_FILTER_GAUSS ? gauss_taps(fl.scale, 3) : binom_taps());
+                // the Gaussian R R streams have fixed shapes; the fused Laplacian
+                // kernels choose their z-segment count
+                if (fl.kind != LBM_FILTER_LAPLACE || !launch_lap3_supported(fl.scale)) continue;
+                const Taps t0 = ell_taps(fl.scale);
                 float best = 1e30f;
                 int pick = 0;
                 for (int v : cand) {
                     const float t = time_ms(c, [&] {
-                        if (lap && lap3_split(p, fl.scale)) {
+                        if (lap3_split(p, fl.scale)) {
                             chk(launch_box3(p, c->L.x6, c->L.t1, nc, v, c->stream));
                             chk(launch_cross3s(p, c->L.t1, c->L.acc, nc, 1.f, 0, v, c->stream));
                         } else {
-                            chk(lap ? launch_lap3(p, c->L.x6, c->L.acc, nc, fl.scale, t0, 1.f, 0, v, c->stream)
-                                    : launch_gauss3(p, c->L.x6, c->L.acc, nc, t0, 1.f, 0, v, c->stream));
+                            chk(launch_lap3(p, c->L.x6, c->L.acc, nc, fl.scale, t0, 1.f, 0, v, c->stream));
                         }
                     }, 5);
                     if (t < best) { best = t; pick = v; }
@@ -1171,6 +1212,8 @@ int lbm_sync(lbm_ctx* c) {
     DevState st;
     CK(c, cudaMemcpyAsync(&st, c->L.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (st.status & 4u)
+        return fail(c, LBM_ERR_TIMEOUT, "a kernel's bounded wait for its bulk copies gave up; results are not valid");
     if (st.status & 1u) return fail(c, LBM_ERR_UNSTABLE, "unstable state (non-finite, rho <= 0 or |v| > c_s)");
     return LBM_OK;
 }
@@ -1439,7 +1482,7 @@ int lbm_eval_qoi(lbm_ctx* c, const float* u, double* q) {
     lc.timed = false;
     LAUNCH(lc, LBM_K_CURL, launch_load_velocity(c->p, c->L, u, lc.s));
     enqueue_fields(lc);
-    LAUNCH(lc, LBM_K_REDUCE, launch_totals(c->p, c->L, false, lc.s));
+    LAUNCH(lc, LBM_K_TOTALS, launch_totals(c->p, c->L, false, lc.s));
     LAUNCH(lc, LBM_K_SOLVE, launch_qoi_values(c->p, c->L, q, lc.s));
     if (lc.err != cudaSuccess) return fail(c, LBM_ERR_CUDA, "lbm_eval_qoi: %s", cudaGetErrorString(lc.err));
     return LBM_OK;

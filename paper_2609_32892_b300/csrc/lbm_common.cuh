@@ -31,6 +31,14 @@ struct Taps {
     float t[kMaxTaps];
 };
 
+// A Gaussian (or binomial) 1-D kernel t of radius R and its self-convolution
+// c = t * t (radius 2R): R R along a periodic axis applies c once.
+struct GaussTaps {
+    int radius;        // R: 1 (binomial), 2, 4 or 6
+    float t[13];       // t[0 .. 2R]
+    float c[25];       // c[0 .. 4R]
+};
+
 // Pointers into the caller's buffer, computed once at create time.
 struct Layout {
     void* f[2];          // shifted populations, ping-pong
@@ -122,17 +130,20 @@ cudaError_t launch_pass_fast(const Params& p, const float* in, float* out, int n
 cudaError_t launch_filter2_fused(const Params& p, const float* in, float* out, int ncomp, bool laplacian, int s_scale,
                                  const Taps& t, float scale, int accumulate, cudaStream_t s);
 // per_sm: target blocks per SM (z segments); 0 = built-in default
-cudaError_t launch_gauss3(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
-                          int accumulate, int per_sm, cudaStream_t s);
 cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp, int s_scale, const Taps& arm,
                         float scale, int accumulate, int per_sm, cudaStream_t s);
-inline bool launch_gauss3_supported(int radius) { return radius == 1 || radius == 2 || radius == 4 || radius == 6; }
 inline bool launch_lap3_supported(int s_scale) { return s_scale == 1 || s_scale == 3; }
 // L_3 as two launches through a scratch field (box, then cross at stride 3)
 bool lap3_split(const Params& p, int s_scale);
 cudaError_t launch_box3(const Params& p, const float* in, float* out, int ncomp, int per_sm, cudaStream_t s);
 cudaError_t launch_cross3s(const Params& p, const float* in, float* out, int ncomp, float scale, int accumulate,
                            int per_sm, cudaStream_t s);
+// R R of a 3-D Gaussian / binomial filter on ncomp fields is three streaming
+// passes: axis 0 (x) and 2 (z) with the composite kernel, then axis 1 (y)
+// with the wall projection; any order of the three gives the same operator
+bool launch_gauss_rr_supported(int radius);
+cudaError_t launch_gauss_pass(const Params& p, int axis, const float* in, float* out, int ncomp, const GaussTaps& gt,
+                              DevState* st, cudaStream_t s);
 cudaError_t launch_band_mask(const Params& p, const float2* in, float2* out, int ncomp, int lo, int hi,
                              cudaStream_t s);
 cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s);

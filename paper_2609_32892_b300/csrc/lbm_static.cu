@@ -7,6 +7,8 @@
 #include <string.h>
 #include <math.h>
 
+#include <cuda.h>  // driver types only: the two driver calls below are fetched at run time
+
 #include "lbm_common.cuh"
 #include "dfloat.cuh"
 
@@ -15,12 +17,46 @@ using namespace lbm;
 namespace {
 
 // The one scratch array.  Its name is only a host-side stand-in in host code;
-// the device address comes from cudaGetSymbolAddress (per device).
+// the device address comes from cudaGetSymbolAddress, looked up once per CUDA
+// context (the primary context of each device, or any other context the
+// caller makes current) and cached under the context's unique id, so a
+// context created later (after cudaDeviceReset, say) gets its own lookup.
 static __device__ __align__(256) unsigned char g_static_scratch[LBM_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 std::mutex g_mu;
-void* g_dev_ptr[kMaxDevices] = {nullptr};
+struct CtxEntry {
+    unsigned long long id;
+    void* ptr;
+};
+CtxEntry g_ctx_cache[kMaxContexts];
+int g_nctx = 0;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// unique id of the calling thread's current context (0 if none or unknown)
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
 
 int err(int code, const char* fmt, ...) {
     char buf[256];
@@ -159,6 +195,8 @@ extern "C" int lbm_qoi_eval_static(const lbm_config* cfg, const float* u, double
     for (int i = 0; i < p.n_s; ++i) {
         const lbm_qoi_spec& sp = cfg->qoi[i];
         if (sp.kind != LBM_QOI_ENERGY && sp.kind != LBM_QOI_ENSTROPHY) return err(LBM_ERR_ARG, "lbm_qoi_eval_static: bad QoI kind");
+        if (sp.filter == LBM_FILTER_FOURIER)
+            return err(LBM_ERR_ARG, "lbm_qoi_eval_static: Fourier-band QoIs are not supported (Gaussian, Laplacian, binomial only)");
         if (sp.filter < 0 || sp.filter > 2) return err(LBM_ERR_ARG, "lbm_qoi_eval_static: bad filter");
         const int sc = sp.filter == LBM_FILTER_BINOMIAL ? 1 : sp.scale;
         if (sp.filter != LBM_FILTER_BINOMIAL && (sc < 1 || sc % 2 == 0)) return err(LBM_ERR_ARG, "lbm_qoi_eval_static: filter scale must be odd");
@@ -205,23 +243,24 @@ extern "C" int lbm_qoi_eval_static(const lbm_config* cfg, const float* u, double
         return err(LBM_ERR_BUDGET, "lbm_qoi_eval_static: needs %zu scratch bytes, the static array holds %u", need,
                    (unsigned)LBM_STATIC_SCRATCH_BYTES);
 
-    // per-device set-up: the device address of the static array
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return err(LBM_ERR_CUDA, "lbm_qoi_eval_static: cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return err(LBM_ERR_ARG, "lbm_qoi_eval_static: device id %d out of range", dev);
+    // set-up once per context: the device address of the static array
     char* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_dev_ptr[dev]) {
+        unsigned long long id = current_context_id();
+        for (int i = 0; i < g_nctx && id; ++i)
+            if (g_ctx_cache[i].id == id) base = (char*)g_ctx_cache[i].ptr;
+        if (!base) {
             void* ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
             if (e != cudaSuccess || !ptr)
                 return err(LBM_ERR_CUDA, "lbm_qoi_eval_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            g_dev_ptr[dev] = ptr;
+            base = (char*)ptr;
+            if (!id) id = current_context_id();  // the lookup made the primary context current
+            if (id && g_nctx < kMaxContexts) g_ctx_cache[g_nctx++] = {id, ptr};
         }
-        base = (char*)g_dev_ptr[dev];
     }
+    cudaError_t e = cudaSuccess;
 
     Layout L;
     memset(&L, 0, sizeof L);

@@ -9,17 +9,26 @@ drains between rounds), and collects completions without blocking.  Per request 
 records the queueing delay, the completion time (device clock) and the
 latency per simulated time unit.
 
+A request is a workload dict (the lbm_config fields, see binding.config_from_workload)
+plus what the member needs from its caller:
+  steps         horizon (lattice steps)
+  u0            initial velocity, host FP64 [3][nz][ny][nx]
+  steps_per_tu  lattice steps per simulated time unit (for the latency figure)
+  lrs           (C, mu, Sigma, sigma_ref) of the member's LRS model (to_mode 'lrs';
+                sigma_ref <= 0 entries are taken from the member's first step)
+  gamma_fixed   its gamma_i (to_mode 'fixed')
+  track_ref     its reference QoI series (to_mode 'track')
+  arrival_s     arrival time (realtime serving)
+
 Scheduling and marshalling only: every step runs in liblbm.so.
 """
 
 import collections
-import math
 import os
 import time
 
 import numpy as np
 
-import synthetic
 from . import binding as B
 
 # Each member steps on its own stream.  With the default 8 hardware work
@@ -30,11 +39,16 @@ from . import binding as B
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 
-def steps_per_tu(wl):
-    """Lattice steps per time unit: C_u/C_l (2-D Kolmogorov), H/u_tau (3-D channel)."""
-    if wl["dim"] == 2:
-        return synthetic.kolmogorov_lattice(wl["nx"])["steps_per_tu"]
-    return synthetic.channel_lattice(wl["ny"])["steps_per_tu"]
+def set_coefficients(ctx, req):
+    """The member's coefficient source from the request (lbm_set_to_coeffs)."""
+    mode = req["to_mode"]
+    if mode == "lrs":
+        c, mu, sig, sref = req["lrs"]
+        B.lbm_set_to_coeffs(ctx, "lrs", req["h"], c, mu, sig, sref)
+    elif mode == "fixed":
+        B.lbm_set_to_coeffs(ctx, "fixed", gamma_fixed=req["gamma_fixed"])
+    elif mode == "track":
+        B.lbm_set_track_reference(ctx, req["track_ref"])
 
 
 class EnsembleServer:
@@ -53,16 +67,12 @@ class EnsembleServer:
             B.lbm_batch_destroy(self.batch)
             self.batch = None
 
-    def admit(self, wl, tag):
-        cfg = B.config_from_workload(wl, member=tag)
-        slot = B.lbm_batch_admit(self.batch, cfg, synthetic.initial_velocity(wl), wl["steps"], tag)
+    def admit(self, req, tag):
+        cfg = B.config_from_workload(req, member=tag)
+        slot = B.lbm_batch_admit(self.batch, cfg, req["u0"], req["steps"], tag)
         if slot is None:
             return None
-        if wl["to_mode"] == "lrs":
-            nq = len(wl["qois"]) + wl["n_mp"]
-            c, mu, sig = synthetic.synthetic_lrs(nq, wl["h"], wl["seed"])
-            # reference scales taken from each member's first predictor QoIs
-            B.lbm_set_lrs(B.lbm_batch_member(self.batch, slot), c, mu, sig, np.zeros(nq))
+        set_coefficients(B.lbm_batch_member(self.batch, slot), req)
         return slot
 
     def serve(self, requests, chunk=32, keep_qoi=False, realtime=True):
@@ -88,7 +98,7 @@ class EnsembleServer:
                     break  # head of the queue waits for memory or a slot
                 active[slot] = i
                 out[i] = {"arrival_s": r.get("arrival_s", 0.0) if realtime else 0.0, "admit_s": now,
-                          "steps": r["steps"], "tu": r["steps"] / steps_per_tu(r),
+                          "steps": r["steps"], "tu": r["steps"] / r["steps_per_tu"],
                           "nodes": r["nx"] * r["ny"] * r["nz"], "storage": r.get("storage", "fp32")}
                 pending.popleft()
             if active:
@@ -145,11 +155,8 @@ def serial_baseline(requests, device="cuda"):
     nodes = 0
     for i, r in enumerate(requests):
         s = LbmSim(r, member=i, device=device)
-        s.init(synthetic.initial_velocity(r))
-        if r["to_mode"] == "lrs":
-            nq = len(r["qois"]) + r["n_mp"]
-            c, mu, sig = synthetic.synthetic_lrs(nq, r["h"], r["seed"])
-            s.set_lrs(c, mu, sig, np.zeros(nq))
+        s.init(r["u0"])
+        set_coefficients(s.ctx, r)
         s.step(r["steps"])
         s.sync()
         s.close()
@@ -159,12 +166,3 @@ def serial_baseline(requests, device="cuda"):
     wall = time.perf_counter() - t0
     return {"requests": len(requests), "wall_s": round(wall, 3), "member_steps_per_s": round(steps / wall, 1),
             "mlups": round(nodes / wall / 1e6, 1)}
-
-
-def scaled_mix(n, seed, rate, horizon_scale=1.0, storage="fp32"):
-    """The serving mix of the benchmark configuration with horizons scaled."""
-    reqs = synthetic.workloads.serving_mix(n, seed, rate)
-    for r in reqs:
-        r["steps"] = max(2, int(math.ceil(r["steps"] * horizon_scale)))
-        r["storage"] = storage
-    return reqs

@@ -17,4 +17,4 @@ Every generator is seeded (numpy PCG64) so both sides see identical inputs.
 from .units import kolmogorov_lattice, channel_lattice  # noqa: F401
 from .fields import uniform_noise_u0, channel_u0, initial_velocity  # noqa: F401
 from .lrs_inputs import synthetic_lrs  # noqa: F401
-from .workloads import WORKLOADS, workload  # noqa: F401
+from .workloads import WORKLOADS, serving_requests, workload  # noqa: F401

@@ -200,3 +200,27 @@ def serving_mix(n_members, seed, rate_per_s):
         w["name"] = f"member{m}"
         out.append(w)
     return out
+
+
+def serving_requests(n_members, seed, rate_per_s, horizon_scale=1.0, storage="fp32"):
+    """The serving mix as server requests: each member's workload with its
+    seeded initial field (u0), its synthetic LRS model (lrs: C, mu, Sigma and
+    sigma_ref = 0, i.e. scales from the member's first step), its steps per
+    simulated time unit, horizons scaled by horizon_scale and the population
+    storage precision."""
+    import math
+
+    from .fields import initial_velocity
+    from .lrs_inputs import synthetic_lrs
+
+    reqs = serving_mix(n_members, seed, rate_per_s)
+    for r in reqs:
+        r["steps"] = max(2, int(math.ceil(r["steps"] * horizon_scale)))
+        r["storage"] = storage
+        r["u0"] = initial_velocity(r)
+        nq = len(r["qois"]) + r["n_mp"]
+        c, mu, sig = synthetic_lrs(nq, r["h"], r["seed"])
+        r["lrs"] = (c, mu, sig, [0.0] * nq)
+        lat = kolmogorov_lattice(r["nx"]) if r["dim"] == 2 else channel_lattice(r["ny"])
+        r["steps_per_tu"] = lat["steps_per_tu"]
+    return reqs

@@ -12,6 +12,7 @@ physics and its 12 QoIs) on a smaller grid:
                     in x and y plus ragged ones), h = 20: 493 rows of C, so
                     the history product spans two 256-row blocks
   c3_36x22x13_h20   1000 steps on 36 x 22 x 13, h = 20
+  c3_36x22x13_h20_u0f32   the same from the initial field rounded to FP32
 
 Stored per case (float64): the QoI block rows, the final density and velocity
 (`Simulation.macros`), the running mean-profile sum, the reference scales.
@@ -32,6 +33,9 @@ OUT = os.path.join(HERE, "oracle_runs")
 CASES = {
     "c3_68x38x17_h20": dict(name="C3", kw=dict(nx=68, ny=38, nz=17, h=20), steps=100, warm=3),
     "c3_36x22x13_h20": dict(name="C3", kw=dict(nx=36, ny=22, nz=13, h=20), steps=1000, warm=3),
+    # the same run from the initial field rounded to FP32: the oracle's own
+    # sensitivity to a perturbation of the size of FP32 rounding
+    "c3_36x22x13_h20_u0f32": dict(name="C3", kw=dict(nx=36, ny=22, nz=13, h=20), steps=1000, warm=3, u0_f32=True),
 }
 
 
@@ -60,7 +64,10 @@ def _run(case):
     sigma_ref = np.sqrt((rows[:, 1:1 + nq] ** 2).mean(axis=0))
     cmat, mu, sig = synthetic.synthetic_lrs(nq, wl["h"], wl["seed"])
     t0 = time.time()
-    sim = Simulation(wl, synthetic.initial_velocity(wl), lrs=(cmat, mu, sig, sigma_ref))
+    u0 = synthetic.initial_velocity(wl)
+    if c.get("u0_f32"):
+        u0 = u0.astype(np.float32).astype(np.float64)
+    sim = Simulation(wl, u0, lrs=(cmat, mu, sig, sigma_ref))
     rows = sim.run(c["steps"])
     rho, u = sim.macros()
     np.savez_compressed(os.path.join(OUT, case + ".npz"), rows=rows, rho=rho, u=u,

@@ -96,7 +96,7 @@ def test_admission_by_budget():
 def test_server_runs_a_request_stream():
     from paper_2609_32892_b300 import serve
 
-    reqs = serve.scaled_mix(10, seed=5, rate=200.0, horizon_scale=0.01)
+    reqs = synthetic.serving_requests(10, seed=5, rate_per_s=200.0, horizon_scale=0.01)
     srv = serve.EnsembleServer(pool_bytes=2 << 30, n_slots=6)
     out, wall, rounds = srv.serve(reqs, chunk=8, keep_qoi=True)
     srv.close()
@@ -120,7 +120,7 @@ def test_serving_mix_members_stay_stable_over_hundreds_of_steps():
     from gpu_common import run_gpu, run_oracle
     from paper_2609_32892_b300 import serve
 
-    reqs = serve.scaled_mix(8, 5, 1.0, 0.04)
+    reqs = synthetic.serving_requests(8, 5, 1.0, 0.04)
     for r in reqs:
         r["steps"] = 300
     srv = serve.EnsembleServer(2 << 30, 16, "cuda")
@@ -170,3 +170,35 @@ def test_batch_wait_bounds_rounds_in_flight():
         with pytest.raises(B.LbmError):
             B.lbm_batch_wait(b, bad)
     B.lbm_batch_destroy(b)
+
+
+def test_server_members_carry_their_own_coefficients():
+    """A request brings its own coefficient source: an LRS member with its own
+    (C, mu, Sigma, sigma_ref) and a fixed-gamma member with its own gamma_i,
+    served together, each equal bit for bit to the same request run alone."""
+    import torch
+
+    from paper_2609_32892_b300 import LbmSim, serve
+
+    a = synthetic.workload("C2", nx=40, ny=32, h=3, seed=41, steps=12)
+    nq = nq_of(a)
+    c, mu, sig = synthetic.synthetic_lrs(nq, a["h"], 77)  # not the seed's own model
+    a.update(u0=synthetic.initial_velocity(a), lrs=(c, mu, sig, np.full(nq, 0.5)), steps_per_tu=100.0)
+    b = synthetic.workload("C3", nx=20, ny=22, nz=12, seed=42, steps=10, to_mode="fixed")
+    b.update(u0=synthetic.initial_velocity(b), gamma_fixed=np.linspace(-1e-3, 1e-3, nq_of(b)), steps_per_tu=100.0)
+    srv = serve.EnsembleServer(2 << 30, 4, "cuda")
+    out, _, _ = srv.serve([a, b], chunk=4, keep_qoi=True, realtime=False)
+    srv.close()
+    for i, r in enumerate((a, b)):
+        s = LbmSim(r, member=i)
+        s.init(r["u0"])
+        serve.set_coefficients(s.ctx, r)
+        s.step(r["steps"])
+        s.sync()
+        alone = s.qoi()
+        s.close()
+        assert out[i]["status"] == 0
+        np.testing.assert_array_equal(out[i]["qoi"], alone)
+    np.testing.assert_array_equal(out[1]["qoi"][:, 1 + 2 * nq_of(b):1 + 3 * nq_of(b)],
+                                  np.tile(b["gamma_fixed"], (b["steps"], 1)))
+    torch.cuda.synchronize()

@@ -4,8 +4,11 @@
   tests/golden/make_oracle_runs.py from the oracle alone): the channel LES with
   WALE and TO-LRS, 12 QoIs, h = 20, for 100 steps on 68 x 38 x 17 (full and
   ragged 32 x 16 filter tiles, two blocks of the LRS history product) and for
-  1000 steps on 36 x 22 x 13.  State, QoI rows and the FP64 mean-profile sum
-  are compared element by element.
+  1000 steps on 36 x 22 x 13 (with a copy started from the FP32-rounded
+  initial field, which measures the flow's own sensitivity).  State, QoI rows
+  and the FP64 mean-profile sum are compared element by element over 100
+  steps; over 1000 steps the first 10 rows element by element and the rest
+  through QoI statistics.
 * The multi-block LRS history product at the benchmark's h = 500 (12 QoIs:
   12 013 rows of C in 47 blocks) and at h = 100 (4 QoIs: 805 rows, 4 blocks):
   seeded initial histories and history coefficients large enough that the
@@ -36,7 +39,7 @@ sys.path.insert(0, os.path.join(HERE, "golden"))
 import make_oracle_runs  # noqa: E402
 
 
-@pytest.mark.parametrize("case", sorted(make_oracle_runs.CASES))
+@pytest.mark.parametrize("case", ["c3_68x38x17_h20"])
 def test_stored_channel_wale_lrs_run(case):
     from paper_2609_32892_b300 import binding as B
 
@@ -51,13 +54,59 @@ def test_stored_channel_wale_lrs_run(case):
     g.close()
     ro = d["rows"]
     assert np.all(ro[:, -1] == 0)  # the stored run never went singular or unstable
-    _compare_state(wl, rho_g, u_g, d["rho"], d["u"])
+    # rho ~ 1 +- 3e-3 here: FP32 rounding of rho (half-ulp 6e-8 per step) walks
+    # ~6e-7 rms over 100 steps, ~2e-6 at the worst of 4e4 nodes
+    _compare_state(wl, rho_g, u_g, d["rho"], d["u"], rho_abs=5e-6)
     _compare_rows(wl, rg, ro)
-    # mean streamwise profile: FP64 running sum of plane means (Sec. 7.3)
+    # mean streamwise profile: FP64 running sum of plane means (Sec. 7.3); the
+    # plane means inherit the FP32 state's error (rel-L2(u) <= 1e-5 above), so
+    # each entry is held to 1e-5 of the profile's scale
     assert nprof == steps
     po = d["profile_sum"]
-    np.testing.assert_allclose(prof, po, rtol=0, atol=1e-6 * np.abs(po).max())
+    np.testing.assert_allclose(prof, po, rtol=0, atol=1e-5 * np.abs(po).max())
     assert np.all(prof[[0, -1]] == 0.0)
+
+
+def test_stored_run_1000_steps_statistics():
+    """1000 steps of the 12-QoI channel LES on 36 x 22 x 13.  This flow
+    amplifies perturbations: the oracle itself, started from the initial
+    field rounded to FP32 (a one-time 1e-7 perturbation), drifts to 1.7e-6
+    in q* after 1000 steps, a growth of ~600; an FP32 run adds rounding of
+    that size every step, so pointwise agreement after the first ~50 steps
+    is not a property FP32 can have here, and the long-run comparison of
+    these chaotic LES runs is statistical.  Checked: the first 10 QoI rows at
+    the standard tolerances, then over all 1000 steps each QoI's time mean
+    within 1 % and the FP64 mean-profile sum within 1 %, and over the first
+    500 steps each QoI's two-sample KS distance within 0.05."""
+    from scipy.stats import ks_2samp
+
+    from paper_2609_32892_b300 import binding as B
+
+    case = "c3_36x22x13_h20"
+    d = np.load(os.path.join(HERE, "golden", "oracle_runs", case + ".npz"))
+    pert = np.load(os.path.join(HERE, "golden", "oracle_runs", case + "_u0f32.npz"))
+    wl = make_oracle_runs.case_workload(case)
+    nq = nq_of(wl)
+    g, rg, _, _ = run_gpu(wl, 1000, lrs=lrs_inputs(wl, d["sigma_ref"]))
+    prof, nprof = B.lbm_get_profile(g.ctx, wl["ny"])
+    g.close()
+    ro = d["rows"]
+    assert np.all(ro[:, -1] == 0) and np.all(rg[:, -1] == 0)
+    # the oracle's own sensitivity: small, but growing ~600x over the run
+    dq = np.abs(pert["rows"][:, 1:1 + nq] / ro[:, 1:1 + nq] - 1).max(axis=1)
+    assert dq[999] > 100 * dq[0]
+    _compare_rows(wl, rg[:10], ro[:10])
+    qg, qo = rg[:, 1:1 + nq], ro[:, 1:1 + nq]
+    mean_rel = np.abs(qg.mean(axis=0) / qo.mean(axis=0) - 1)
+    assert np.all(mean_rel <= 1e-2), mean_rel
+    # the run is a decaying transient, not a stationary state, so the KS
+    # distance is taken over the first half, before the FP32 trajectory's
+    # drift (4e-3 of q* by step 500) shifts the late values
+    ks = np.array([ks_2samp(qg[:500, i], qo[:500, i]).statistic for i in range(nq)])
+    assert np.all(ks <= 0.05), ks
+    po = d["profile_sum"]
+    assert nprof == 1000
+    np.testing.assert_allclose(prof, po, rtol=0, atol=1e-2 * np.abs(po).max())
 
 
 def _history_inputs(wl, sigma_ref, seed, coupling=1e-4):
@@ -106,7 +155,8 @@ def test_lrs_history_product_many_blocks(name, kw):
     np.testing.assert_allclose(q_g[0], q_o[0], rtol=1e-4)
     # the history term dominates dQ: about 1e-4 of sigma_ref
     assert np.all(np.abs(dq_o[0]) > 1e-7 * sref)
-    np.testing.assert_allclose(dq_g[0], dq_o[0], rtol=1e-9, atol=0)
+    # FP64 cancellation in dQ = sigma (q*/sigma + H) - q* leaves a few ulps of q*
+    np.testing.assert_allclose(dq_g[0], dq_o[0], rtol=1e-9, atol=1e-14 * np.abs(q_o[0]).max())
     np.testing.assert_allclose(dq_g[1], dq_o[1], rtol=1e-6, atol=0)
     np.testing.assert_allclose(q_g[1:], q_o[1:], rtol=1e-3)
     np.testing.assert_allclose(dq_g[2:], dq_o[2:], rtol=1e-3, atol=0)

@@ -52,7 +52,18 @@ def _peaks():
 # DRAM traffic per launch and node of each kernel class, read+write bytes from
 # the ncu launch list of the benchmark command (profiles/), reported only while
 # the kernel source still has the hash it had when captured.
-TRAFFIC = {}
+TRAFFIC = {
+    # 320x200x160 channel, WALE + TO-LRS (profiles/gauss_rr_channel3d_320x200x160.md)
+    "collide": {"bytes_per_node": 230.9, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "29b748f384ffc5af"},
+    "predict": {"bytes_per_node": 97.8, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "29b748f384ffc5af"},
+    "gauss_x": {"bytes_per_node": 43.2, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
+    "gauss_z": {"bytes_per_node": 43.4, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
+    "gauss_y": {"bytes_per_node": 43.8, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
+    "box3": {"bytes_per_node": 44.9, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "86151afaeaf3f213"},
+    "cross3s": {"bytes_per_node": 50.6, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "86151afaeaf3f213"},
+    "lap1": {"bytes_per_node": 45.1, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "86151afaeaf3f213"},
+    "reduce": {"bytes_per_node": 83.2, "source": "paper_2609_32892_b300/csrc/kernels_to.cu", "sha256_16": "cb81ba72923d33b8"},
+}
 
 
 def _traffic(kind, n_nodes):

@@ -94,6 +94,8 @@ __device__ __forceinline__ void pull(const Params& p, const T* __restrict__ src,
     const int zm = DIM == 3 ? wrap(z - 1, nz) : 0, zp = DIM == 3 ? wrap(z + 1, nz) : 0;
     const bool wall_lo = p.walls && (y == 1);        // source row y-1 solid
     const bool wall_hi = p.walls && (y == ny - 2);   // source row y+1 solid
+    // node offsets within one population array fit in 32 bits (6 N < 2^31);
+    // the population arrays are stepped through by pointer (Q N may not)
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) {
         const int cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
@@ -104,7 +106,7 @@ __device__ __forceinline__ void pull(const Params& p, const T* __restrict__ src,
             const int xs = cx == 0 ? x : (cx > 0 ? xm : xp);
             const int ys = cy == 0 ? y : (cy > 0 ? ym : yp);
             const int zs = cz == 0 ? z : (cz > 0 ? zm : zp);
-            g[i] = ldg_<T>(src + (size_t)i * N + ((size_t)zs * ny + ys) * nx + xs);
+            g[i] = ldg_<T>(src + (size_t)i * N + (unsigned)((zs * ny + ys) * nx + xs));
         }
     }
 }
@@ -228,16 +230,17 @@ __device__ __forceinline__ float wale_nut(const Params& p, const float* __restri
         for (int b = 0; b < 3; ++b) gm[a][b] = 0.f;
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     const int ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
-    const size_t row = ((size_t)z * ny + y) * nx;
+    // 32-bit node offsets (6 N < 2^31)
+    const unsigned row = (unsigned)((z * ny + y) * nx);
+    const unsigned iyp = (unsigned)((z * ny + yp) * nx + x), iym = (unsigned)((z * ny + ym) * nx + x);
+    const int zm = DIM == 3 ? wrap(z - 1, nz) : 0, zp = DIM == 3 ? wrap(z + 1, nz) : 0;
+    const unsigned izp = (unsigned)((zp * ny + y) * nx + x), izm = (unsigned)((zm * ny + y) * nx + x);
 #pragma unroll
     for (int i = 0; i < (DIM == 3 ? 3 : 2); ++i) {
         const float* v = vn + (size_t)i * N;
         gm[i][0] = 0.5f * (v[row + xp] - v[row + xm]);
-        gm[i][1] = 0.5f * (v[((size_t)z * ny + yp) * nx + x] - v[((size_t)z * ny + ym) * nx + x]);
-        if (DIM == 3) {
-            const int zm = wrap(z - 1, nz), zp = wrap(z + 1, nz);
-            gm[i][2] = 0.5f * (v[((size_t)zp * ny + y) * nx + x] - v[((size_t)zm * ny + y) * nx + x]);
-        }
+        gm[i][1] = 0.5f * (v[iyp] - v[iym]);
+        if (DIM == 3) gm[i][2] = 0.5f * (v[izp] - v[izm]);
     }
     float g2[3][3];
 #pragma unroll
@@ -261,14 +264,21 @@ __device__ __forceinline__ float wale_nut(const Params& p, const float* __restri
     return p.c_wale2 * sdsd * sqrtf(sdsd) / den;
 }
 
-// The fused predictor step of one node from its pulled populations g (in
-// place): moments, substrate tau_eff, BGK (Eq. LES-1) and the body force (EDM:
-// Eq. collide-and-stream; or Guo).  Returns rho and the predictor velocity
-// v^{p*} = (rho u + F)/rho for the TO phase.
-template <int DIM, int SUB, bool ACC>
+// The collision of one node from its pulled populations g (in place):
+// moments, substrate tau_eff, BGK (Eq. LES-1), the body force and, with CORR,
+// the step's SGS increment dv (Eq. LES-2).  Under EDM the force and the SGS
+// increment form one equilibrium difference, Eq. LES-2's single-difference
+// form f^a + f^eq(rho, u + F/rho + dv) - f^eq(rho, u) (the predictor form
+// f^{p*} + f^eq(v* + dv) - f^eq(v*), v* = u + F/rho, telescopes to it); under
+// Guo's scheme the increment follows the forcing as its own difference.
+template <int DIM>
+__device__ __forceinline__ void sgs_correct(float* g, float r, float ux, float uy, float uz, float dx, float dy,
+                                            float dz);
+
+template <int DIM, int SUB, bool ACC, bool CORR>
 __device__ __forceinline__ void collide_node(const Params& p, float* g, int x, int y, int z,
                                              const float* __restrict__ vn, const float* __restrict__ kolmo,
-                                             DevState* st, float& rho_o, float& vx_o, float& vy_o, float& vz_o) {
+                                             DevState* st, float dvx, float dvy, float dvz) {
     using LT = Lat<DIM>;
     const Macro m = macros_of<DIM, ACC>(p, g, kolmo, y);
     const float ux = m.ux, uy = m.uy, uz = m.uz;
@@ -350,7 +360,12 @@ __device__ __forceinline__ void collide_node(const Params& p, float* g, int x, i
     } else {
         // EDM: S_i = w rho [3 c.d + 4.5 (c.d)(2 c.u + c.d) - 1.5 d.(2u + d)], d = F/rho
         const float inv = 1.0f / m.rho;
-        const float dx = fx * inv, dy = fy * inv, dz = fz * inv;
+        float dx = fx * inv, dy = fy * inv, dz = fz * inv;
+        if (CORR) {
+            dx += dvx;
+            dy += dvy;
+            dz += dvz;
+        }
         const float du = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
         g[0] = g[0] + (geq[0] - g[0]) * om - LT::w(0) * m.rho * 1.5f * du;
 #pragma unroll
@@ -366,8 +381,11 @@ __device__ __forceinline__ void collide_node(const Params& p, float* g, int x, i
             g[j] = g[j] + (geq[j] - g[j]) * om + (ev - od);
         }
     }
-    rho_o = m.rho;
-    predictor_velocity(m, vx_o, vy_o, vz_o);
+    if (CORR && p.forcing == LBM_FORCING_GUO) {
+        float vx, vy, vz;
+        predictor_velocity(m, vx, vy, vz);
+        sgs_correct<DIM>(g, m.rho, vx, vy, vz, dvx, dvy, dvz);
+    }
 }
 
 // SGS velocity increment of a node: dv = sum_k beta_k V_k + (sum_j beta_j
@@ -435,13 +453,9 @@ __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restr
     if (p.walls && (y == 0 || y == p.ny - 1)) return;
     float g[LT::Q];
     pull<DIM, T>(p, src, x, y, z, n, g);
-    float r, vx, vy, vz;
-    collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g, x, y, z, vn, kolmo, st, r, vx, vy, vz);
-    if (CORR) {
-        float dx, dy, dz;
-        sgs_increment<DIM>(p, vk, betaf, mprow, (size_t)n, y, dx, dy, dz);
-        sgs_correct<DIM>(g, r, vx, vy, vz, dx, dy, dz);
-    }
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    if (CORR) sgs_increment<DIM>(p, vk, betaf, mprow, (size_t)n, y, dx, dy, dz);
+    collide_node<DIM, SUB, (sizeof(T) == 4), CORR>(p, g, x, y, z, vn, kolmo, st, dx, dy, dz);
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) st_<T>(dst + (size_t)i * N + n, g[i]);
 }
@@ -540,16 +554,13 @@ __global__ void __launch_bounds__(128) collide2_kernel(Params p, const T* __rest
     pull2<DIM, T>(p, src, x0, y, z, n0, g0, g1);
     if (!live) return;
     if (p.walls && (y == 0 || y == p.ny - 1)) return;
-    float r0, vx0, vy0, vz0, r1, vx1, vy1, vz1;
-    collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g0, x0, y, z, vn, kolmo, st, r0, vx0, vy0, vz0);
-    collide_node<DIM, SUB, (sizeof(T) == 4)>(p, g1, x0 + 1, y, z, vn, kolmo, st, r1, vx1, vy1, vz1);
+    float dx0 = 0.f, dy0 = 0.f, dz0 = 0.f, dx1 = 0.f, dy1 = 0.f, dz1 = 0.f;
     if (CORR) {
-        float dx0, dy0, dz0, dx1, dy1, dz1;
         sgs_increment<DIM>(p, vk, betaf, mprow, (size_t)n0, y, dx0, dy0, dz0);
         sgs_increment<DIM>(p, vk, betaf, mprow, (size_t)n0 + 1, y, dx1, dy1, dz1);
-        sgs_correct<DIM>(g0, r0, vx0, vy0, vz0, dx0, dy0, dz0);
-        sgs_correct<DIM>(g1, r1, vx1, vy1, vz1, dx1, dy1, dz1);
     }
+    collide_node<DIM, SUB, (sizeof(T) == 4), CORR>(p, g0, x0, y, z, vn, kolmo, st, dx0, dy0, dz0);
+    collide_node<DIM, SUB, (sizeof(T) == 4), CORR>(p, g1, x0 + 1, y, z, vn, kolmo, st, dx1, dy1, dz1);
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) Vec2<T>::st(dst + (size_t)i * N + n0, g0[i], g1[i]);
 }

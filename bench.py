@@ -54,8 +54,8 @@ def _peaks():
 # the kernel source still has the hash it had when captured.
 TRAFFIC = {
     # 320x200x160 channel, WALE + TO-LRS (profiles/gauss_rr_channel3d_320x200x160.md)
-    "collide": {"bytes_per_node": 230.9, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "29b748f384ffc5af"},
-    "predict": {"bytes_per_node": 97.8, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "29b748f384ffc5af"},
+    "collide": {"bytes_per_node": 230.8, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "4319d70a25bab072"},
+    "predict": {"bytes_per_node": 98.0, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "4319d70a25bab072"},
     "gauss_x": {"bytes_per_node": 43.2, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
     "gauss_z": {"bytes_per_node": 43.4, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
     "gauss_y": {"bytes_per_node": 43.8, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
@@ -372,59 +372,68 @@ def run_serving(args, device):
 
 
 def run_precision(args, device):
-    """Reduced-precision population storage against FP32 over long runs: the
-    configured 256^2 Kolmogorov LES (Smagorinsky) and 96x40x48 channel LES
-    (WALE), 2e4 steps each in FP32, shifted FP16 and BF16 storage from the
-    same initial field, with every QoI evaluated each step (observe mode: the
-    synthetic LRS coefficients are not a trained model and random-walk over
-    such horizons).  The trajectories decorrelate (the flows are chaotic), so
-    the comparison is statistical: per QoI, the relative difference of the
-    time-means and the two-sample Kolmogorov-Smirnov distance over the second
-    half of the run, next to the same figures for FP32 started from another
-    seeded field (the statistical noise floor).  FP32 itself is pinned to the
-    FP64 oracle by the parity tests."""
+    """Reduced-precision population storage against FP32, as ensemble
+    statistics (the QoI accuracy targets: time means within 1 %, two-sample
+    KS distance of the QoI distributions within 0.05).
+
+    For the configured 256^2 Kolmogorov LES (Smagorinsky, --prec-steps-2d
+    steps) and 96x40x48 channel LES (WALE, --prec-steps steps), an ensemble of
+    --prec-members members with different seeded initial fields runs in each
+    storage precision (FP32,
+    shifted FP16, shifted BF16) through the batch server, every QoI evaluated
+    each step (observe mode: the synthetic LRS coefficients are not a trained
+    model and random-walk over such horizons).  Per QoI, the samples of the
+    second half of every member's run are pooled; the reduced-precision pool is
+    compared with the FP32 pool.  The noise floor of the comparison is the same
+    statistic between the two halves of the FP32 ensemble (members 0..M/2-1
+    against M/2..M-1): a difference below the floor is not resolved.  The
+    precision meets a target when its difference is within the target, or
+    within the floor where the floor itself exceeds the target (then the
+    ensemble is too small to resolve it, stated as `resolved: false`)."""
     from scipy.stats import ks_2samp
 
-    from paper_2609_32892_b300 import LbmSim, binding as B
+    from paper_2609_32892_b300 import serve
 
-    out = {}
+    m = args.prec_members
+    out = {"members": m, "to_mode": "observe", "statistic_window": "second half of each run"}
     for name in ("C2", "C3"):
-        series = {}
-        # fp32_reseeded: FP32 from another seeded initial field, the noise floor
-        # of the statistics (finite, correlated samples of a chaotic flow)
-        for st in ("fp32", "fp16", "bf16", "fp32_reseeded"):
-            base = synthetic.workload(name)
-            wl = synthetic.workload(name, storage=st.split("_")[0], to_mode="observe",
-                                    seed=base["seed"] + (1 if st == "fp32_reseeded" else 0))
-            nq = len(wl["qois"]) + wl["n_mp"]
-            sim = LbmSim(wl, device=device)
-            sim.init(synthetic.initial_velocity(wl))
-            rows, status = [], "stable"
-            try:
-                for _ in range(args.prec_steps // 2000):
-                    sim.step(2000)
-                    sim.sync()
-                    rows.append(sim.qoi())  # drains the device ring (4096 rows)
-            except B.LbmError as e:
-                status = f"unstable after {sum(len(r) for r in rows)} steps: {e}"
-            sim.close()
-            r = np.concatenate(rows) if rows else np.zeros((0, 2 + 3 * nq))
-            series[st] = {"q": r[:, 1:1 + nq], "status": status}
-        res = {"grid": [synthetic.workload(name)[k] for k in ("nx", "ny", "nz")], "to_mode": "observe",
-               "status": {st: series[st]["status"] for st in series}}
-        n = min(series[st]["q"].shape[0] for st in series)
-        res["steps"] = int(n)
-        if n >= 200:
-            half = n // 2
-            ref = series["fp32"]["q"][half:n]
-            for st in ("fp16", "bf16", "fp32_reseeded"):
-                q = series[st]["q"][half:n]
-                mean_rel = np.abs(q.mean(axis=0) - ref.mean(axis=0)) / np.abs(ref.mean(axis=0))
-                ks = [float(ks_2samp(q[:, i], ref[:, i]).statistic) for i in range(ref.shape[1])]
-                res[st] = {"time_mean_rel_diff_max": float(np.max(mean_rel)),
-                           "time_mean_rel_diff_median": float(np.median(mean_rel)),
-                           "ks_max": max(ks), "ks_median": float(np.median(ks))}
-        out[synthetic.workload(name)["name"]] = res
+        # the 2-D flow is cheap per step and needs longer to settle into its statistics
+        steps = args.prec_steps_2d if name == "C2" else args.prec_steps
+        base = synthetic.workload(name)
+        nq = len(base["qois"]) + base["n_mp"]
+        pools = {}
+        status = {}
+        for st in ("fp32", "fp16", "bf16"):
+            reqs = []
+            for i in range(m):
+                w = synthetic.workload(name, storage=st, to_mode="observe", seed=base["seed"] + 1000 + i, steps=steps,
+                                       qoi_ring=steps + 8)
+                w["u0"] = synthetic.initial_velocity(w)
+                lat = synthetic.kolmogorov_lattice(w["nx"]) if w["dim"] == 2 else synthetic.channel_lattice(w["ny"])
+                w["steps_per_tu"] = lat["steps_per_tu"]
+                reqs.append(w)
+            srv = serve.EnsembleServer(args.serve_pool_gb << 30, max(m, 1), device)
+            res, wall, _ = srv.serve(reqs, chunk=250, keep_qoi=True, realtime=False)
+            srv.close()
+            status[st] = {"unstable_members": int(sum(1 for r in res.values() if r.get("status", 0) != 0)),
+                          "wall_s": round(wall, 2)}
+            pools[st] = [res[i]["qoi"][steps // 2:, 1:1 + nq] for i in range(m)]
+        def compare(a, b):
+            a, b = np.concatenate(a), np.concatenate(b)
+            mean_rel = np.abs(a.mean(axis=0) / b.mean(axis=0) - 1.0)
+            ks = np.array([ks_2samp(a[:, i], b[:, i]).statistic for i in range(nq)])
+            return mean_rel, ks
+        fm, fk = compare(pools["fp32"][: m // 2], pools["fp32"][m // 2:])
+        rec = {"grid": [base["nx"], base["ny"], base["nz"]], "steps": steps, "status": status,
+               "floor_fp32_halves": {"time_mean_rel_diff_max": float(fm.max()), "ks_max": float(fk.max())}}
+        for st in ("fp16", "bf16"):
+            dm, dk = compare(pools[st], pools["fp32"])
+            rec[st] = {"time_mean_rel_diff_max": float(dm.max()), "time_mean_rel_diff_median": float(np.median(dm)),
+                       "ks_max": float(dk.max()), "ks_median": float(np.median(dk)),
+                       "meets_time_mean_1pct": bool(np.all(dm <= np.maximum(1e-2, fm))),
+                       "meets_ks_0.05": bool(np.all(dk <= np.maximum(0.05, fk))),
+                       "resolved": bool(fm.max() <= 1e-2 and fk.max() <= 0.05)}
+        out[base["name"]] = rec
     return out
 
 
@@ -576,6 +585,8 @@ def main():
     ap.add_argument("--no-ref", dest="ref", action="store_false")
     ap.add_argument("--no-precision", dest="precision", action="store_false")
     ap.add_argument("--prec-steps", type=int, default=20000)
+    ap.add_argument("--prec-steps-2d", type=int, default=100000)
+    ap.add_argument("--prec-members", type=int, default=16)
     ap.add_argument("--ref-rows", type=int, default=10)
     args = ap.parse_args()
     world, rank, local = _dist()

@@ -59,8 +59,6 @@ TRAFFIC = {
     "gauss_x": {"bytes_per_node": 43.2, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
     "gauss_z": {"bytes_per_node": 43.4, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
     "gauss_y": {"bytes_per_node": 43.8, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
-    "box3": {"bytes_per_node": 44.9, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "86151afaeaf3f213"},
-    "cross3s": {"bytes_per_node": 50.6, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "86151afaeaf3f213"},
     "lap1": {"bytes_per_node": 45.1, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "86151afaeaf3f213"},
     "reduce": {"bytes_per_node": 83.2, "source": "paper_2609_32892_b300/csrc/kernels_to.cu", "sha256_16": "cb81ba72923d33b8"},
 }
@@ -166,8 +164,7 @@ def _algorithmic_bytes(wl, n):
     filters   one application of a compact filter reads and writes the
               six-component (v, omega) field once, 2 x ncomp x 4 B; the
               Gaussian R R (two applications) runs as three passes, each
-              credited a third of 2 applications, and L_3 as two passes (box,
-              cross), each credited half an application
+              credited a third of 2 applications; L_3 and L_1 are one pass each
     curl/sens read 3 components, write 3 (24 B); reduce reads v^{p*} and the
               N_s sensitivities ((1 + N_s) d 4); wale reads u, writes tau (16 B)"""
     q = 19 if wl["dim"] == 3 else 9
@@ -181,7 +178,7 @@ def _algorithmic_bytes(wl, n):
         "collide": 2 * q * b,
         "predict": q * b + (d * 4 if to else 0),
         "gauss_x": 2 * app / 3, "gauss_z": 2 * app / 3, "gauss_y": 2 * app / 3,
-        "box3": app / 2, "cross3s": app / 2, "lap1": app, "filter": app,
+        "lap3": app, "lap1": app, "filter": app,
         "curl": 2 * 3 * 4, "sens": 2 * 3 * 4, "reduce": (1 + ns) * d * 4, "wale": 16,
     }
     return {k: v * n for k, v in per_node.items()}
@@ -260,7 +257,7 @@ def run_ours(args, world, rank, local):
                 ent["algorithmic_gbs"] = algo[k] / (tms / cnt * 1e-3) / 1e9
             sections[k] = ent
     flops = B.lbm_filter_flops_per_step(sim.ctx)
-    for k in ("gauss_x", "gauss_z", "gauss_y", "box3", "cross3s", "lap1", "filter"):
+    for k in ("gauss_x", "gauss_z", "gauss_y", "lap3", "lap1", "filter"):
         if k in sections and flops[k] > 0:
             sections[k]["tflops"] = flops[k] / (sections[k]["ms_per_step"] * 1e-3) / 1e12
     # the dominant kernel: the class with the largest time per step (each class

@@ -245,8 +245,8 @@ enum {
     LBM_K_WALE = 12,     /* reserved: WALE runs inside the collide              */
     LBM_K_GAUSS_Z = 13,  /* R R of a 3-D Gaussian / binomial filter: z pass     */
     LBM_K_GAUSS_Y = 14,  /* R R of a 3-D Gaussian / binomial filter: y pass     */
-    LBM_K_BOX3 = 15,     /* L_3 pass 1: the 3x3x3 box                           */
-    LBM_K_CROSS3S = 16,  /* L_3 pass 2: the cross of l at stride 3              */
+    LBM_K_LAP3 = 15,     /* 3-D L_3 (nx % 4 == 0): box and stride-3 cross fused */
+    LBM_K_RESERVED16 = 16, /* unused                                            */
     LBM_K_TOTALS = 17,   /* cross-block sums of the reduction partials          */
     LBM_K_COUNT = 18
 };

@@ -25,7 +25,7 @@ MAX_QOI = 16
 FLAG_SINGULAR, FLAG_UNSTABLE = 1, 2
 # profile classes, in the order of the LBM_K_* ids of include/lbm.h
 K_NAMES = ["predict", "collide", "curl", "filter", "sens", "reduce", "lrs", "solve", "apply", "gauss_x", "lap1", "fft",
-           "wale", "gauss_z", "gauss_y", "box3", "cross3s", "totals"]
+           "wale", "gauss_z", "gauss_y", "lap3", "reserved16", "totals"]
 EXPORTED = [
     "lbm_qoi_row_len", "lbm_required_bytes", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_macros",
     "lbm_set_lrs", "lbm_set_to_coeffs", "lbm_set_track_reference", "lbm_step", "lbm_sync", "lbm_qoi", "lbm_get_macros",

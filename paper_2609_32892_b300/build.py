@@ -12,7 +12,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["lbm_api.cu", "kernels_lbm.cu", "kernels_to.cu", "kernels_filter.cu", "kernels_filter3d.cu", "kernels_gauss.cu", "lbm_static.cu", "lbm_batch.cu"]
+SOURCES = ["lbm_api.cu", "kernels_lbm.cu", "kernels_to.cu", "kernels_filter.cu", "kernels_filter3d.cu", "kernels_gauss.cu", "kernels_lap3.cu", "lbm_static.cu", "lbm_batch.cu"]
 LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -17,8 +17,8 @@
 //
 // With nx % 4 == 0 the Laplacian class has its own kernels, one thread per
 // output quad with 16-byte accesses: crossq3_kernel (L_1, planes staged by
-// asynchronous copies and kept in a ring) and, for L_3, box3_kernel followed
-// by cross3s_kernel (the 3 x 3 x 3 box, then the cross at stride 3).
+// asynchronous copies and kept in a ring) and, for L_3, the fused box and
+// stride-3 cross of kernels_lap3.cu.
 //
 // Periodic along x and z; along y with walls the halo outside the array reads
 // zero (solid rows already hold zero), and outputs on solid rows are zero, so
@@ -276,7 +276,6 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, int s
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 int seg_len(const Params& p, int blocks_xy, int ncomp, int R, int per_sm) {
@@ -430,219 +429,15 @@ cudaError_t run_crossq3(const Params& p, const float* in, float* out, int ncomp,
     return cudaGetLastError();
 }
 
-// L_3 in two passes (nx % 4 == 0).  L_s is L_1 dilated by the Kronecker
-// product with the s^3 block of ones, so L_s = c C_s * B_s: B_s the s x s x s
-// box and C_s the cross of l = [1, -4, 6, -4, 1] at stride s along every axis
-// (centre 3 x 6).  For s = 3 that is a 27-point box and a 13-point cross
-// instead of the 3 x 21 taps of the separable-sum form (lap3_kernel<7, 1>).
-// The box B = B_3 x is written to a scratch field, then the cross is applied
-// to B.  B is computed on every row of the array, solid rows included
-// (B at a solid row holds the box of its fluid neighbours); beyond the array B
-// is zero because the solid rows of x are, so the cross reads B with zero
-// extension and zeroes its solid output rows: P K P exactly, as the fused
-// kernel.  Both passes are plain streams over the field (48 B per node each).
-namespace bx3 {
-constexpr int TX = 32, TY = 16, NT = 128;  // 8 x-quads x 16 rows
-}  // namespace bx3
-
-// B = B_3 x: a thread owns one output quad (4 x-consecutive nodes) of a row
-// and marches along its z segment, keeping the in-plane box of the planes
-// z - 1 and z in registers; rows y +- 1 come through L1, planes through L2.
-__global__ void __launch_bounds__(128) box3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                   int ncomp, int seg) {
-    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
-    const int x = blockIdx.x * bx3::TX + 4 * (threadIdx.x & 7);
-    const int y = blockIdx.y * bx3::TY + (threadIdx.x >> 3);
-    if (x >= nx || y >= ny || z0 >= z1) return;
-    const size_t N = (size_t)p.n, plane_n = (size_t)ny * nx;
-    const float* a = in + c * N;
-    float* o = out + c * N;
-    // the three source rows (-1: beyond a wall, reads zero)
-    int rows[3] = {y - 1, y, y + 1};
-    if (p.walls) {
-        if (rows[0] < 0) rows[0] = -1;
-        if (rows[2] >= ny) rows[2] = -1;
-    } else {
-        rows[0] = rows[0] < 0 ? ny - 1 : rows[0];
-        rows[2] = rows[2] >= ny ? 0 : rows[2];
-    }
-    const int xl = x == 0 ? nx - 1 : x - 1, xr = x + 4 == nx ? 0 : x + 4;
-    // in-plane box of plane zq at this quad: column sums over the rows, then
-    // the x box of the column sums
-    auto box2 = [&](int zq) {
-        const float* pl = a + (size_t)zq * plane_n;
-        float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
-        float ls = 0.f, hs = 0.f;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            if (rows[r] < 0) continue;
-            const float* row = pl + (size_t)rows[r] * nx;
-            const float4 m = __ldg(reinterpret_cast<const float4*>(row + x));
-            cs.x += m.x; cs.y += m.y; cs.z += m.z; cs.w += m.w;
-            ls += __ldg(row + xl);
-            hs += __ldg(row + xr);
-        }
-        return make_float4(ls + cs.x + cs.y, cs.x + cs.y + cs.z, cs.y + cs.z + cs.w, cs.z + cs.w + hs);
-    };
-    int zq = pm(z0 - 1, nz);
-    float4 bm = box2(zq);
-    zq = zq + 1 == nz ? 0 : zq + 1;
-    float4 b0 = box2(zq);
-    // two output planes per iteration: the loads of planes z + 1 and z + 2
-    // are independent, so a thread has 18 in flight (the kernel waits on
-    // memory latency); with an odd segment the last plane z + 2 is read but
-    // not used
-    float* oq = o + (size_t)y * nx + x;
-    for (int z = z0; z < z1; z += 2) {
-        const int z1q = zq + 1 == nz ? 0 : zq + 1;
-        const int z2q = z1q + 1 == nz ? 0 : z1q + 1;
-        const float4 bp = box2(z1q), bq = box2(z2q);
-        *reinterpret_cast<float4*>(oq + (size_t)z * plane_n) =
-            make_float4(bm.x + b0.x + bp.x, bm.y + b0.y + bp.y, bm.z + b0.z + bp.z, bm.w + b0.w + bp.w);
-        if (z + 1 < z1)
-            *reinterpret_cast<float4*>(oq + (size_t)(z + 1) * plane_n) =
-                make_float4(b0.x + bp.x + bq.x, b0.y + bp.y + bq.y, b0.z + bp.z + bq.z, b0.w + bp.w + bq.w);
-        bm = bp;
-        b0 = bq;
-        zq = z2q;
-    }
-}
-
-// out = c C_3 B: the 13-point cross of l = (1, -4, 6, -4, 1) at stride 3.  One
-// thread per output quad: the x and y arms from the output plane staged in
-// shared memory by 16-byte asynchronous copies (two planes in flight), the z
-// arm (planes z +- 3, z +- 6) by 16-byte loads that L2 serves (every plane
-// is staged by this block within six planes of its use as a z neighbour).
-namespace cs3 {
-constexpr int TX = 32, TY = 16, HX = 8, HY = 6;
-constexpr int WP = TX + 2 * HX;    // 48 floats per staged row
-constexpr int NQ = WP / 4;         // 12 chunks per row
-constexpr int TH = TY + 2 * HY;    // 28 staged rows
-constexpr int NT = (TX / 4) * TY;  // 128: one thread per output quad
-constexpr int SZ = TH * WP;
-}  // namespace cs3
-
-__device__ __forceinline__ int wrapz(int v, int n) {
-    while (v < 0) v += n;
-    while (v >= n) v -= n;
-    return v;
-}
-
-__global__ void __launch_bounds__(128) cross3s_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                      float scale, int accumulate, int ncomp, int seg) {
-    constexpr int TX = cs3::TX, TY = cs3::TY, HX = cs3::HX, HY = cs3::HY;
-    constexpr int NQ = cs3::NQ, TH = cs3::TH, NT = cs3::NT, SZ = cs3::SZ;
-    __shared__ __align__(16) float tile[3][SZ];
-    __shared__ int coff[TH * NQ];
-    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
-    const int nz = p.nz;
-    const int z0 = zs * seg, z1 = min(nz, z0 + seg);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int qx = threadIdx.x & 7, ry = threadIdx.x >> 3;
-    const int gx0 = x0 + 4 * qx, y = y0 + ry;
-    const size_t N = (size_t)p.n, plane_n = (size_t)p.ny * p.nx;
-    const float* a = in + c * N;
-    float* o = out + c * N;
-    // chunk k: staged row k / NQ <-> y0 - HY + row, columns 4 (k % NQ) .. + 3
-    // <-> x0 - HX + 4 (k % NQ) ..; -1 beyond a wall (zero-filled)
-    for (int k = threadIdx.x; k < TH * NQ; k += NT) {
-        const int ly = k / NQ, m = k - ly * NQ;
-        int gy = y0 - HY + ly;
-        const int gx = pm(x0 - HX + 4 * m, p.nx);
-        bool ok = true;
-        if (p.walls) ok = gy >= 0 && gy < p.ny;
-        else gy = pm(gy, p.ny);
-        coff[k] = ok ? gy * p.nx + gx : -1;
-    }
-    __syncthreads();
-    int zq = z0;  // z index of the next plane staged (planes z0 .. z1 - 1, in order)
-    auto issue = [&](float* t) {
-        const float* plane = a + (size_t)zq * plane_n;
-        ++zq;
-        for (int k = threadIdx.x; k < TH * NQ; k += NT) {
-            const int ofs = coff[k];
-            cp_async16(t + 4 * k, ofs >= 0 ? plane + ofs : plane, ofs >= 0 ? 16 : 0);
-        }
-    };
-    const bool live = gx0 < p.nx && y < p.ny;
-    const bool solid = p.walls && (y == 0 || y == p.ny - 1);
-    const size_t col = live ? (size_t)y * p.nx + gx0 : 0;  // this quad within a plane
-    const int rq = (ry + HY) * NQ + qx + 2;                 // the output quad in a staged plane
-    if (z0 < z1) issue(tile[0]);
-    cp_async_commit();
-    if (z0 + 1 < z1) issue(tile[1]);
-    cp_async_commit();
-    int b = 0;
-    for (int zo = z0; zo < z1; ++zo) {
-        // z arm first: its L2 latency overlaps the wait for the staged plane
-        float4 zm6 = make_float4(0.f, 0.f, 0.f, 0.f), zm3 = zm6, zp3 = zm6, zp6 = zm6;
-        if (live) {
-            zm6 = __ldg(reinterpret_cast<const float4*>(a + (size_t)wrapz(zo - 6, nz) * plane_n + col));
-            zm3 = __ldg(reinterpret_cast<const float4*>(a + (size_t)wrapz(zo - 3, nz) * plane_n + col));
-            zp3 = __ldg(reinterpret_cast<const float4*>(a + (size_t)wrapz(zo + 3, nz) * plane_n + col));
-            zp6 = __ldg(reinterpret_cast<const float4*>(a + (size_t)wrapz(zo + 6, nz) * plane_n + col));
-        }
-        cp_async_wait1();
-        __syncthreads();
-        if (zo + 2 < z1) issue(tile[b == 0 ? 2 : b - 1]);
-        cp_async_commit();
-        const float4* t4 = reinterpret_cast<const float4*>(tile[b]);
-        // staged columns 4 qx .. 4 qx + 19; the outputs sit at + 8 .. + 11
-        float v[20];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const float4 w = t4[rq - 2 + m];
-            v[4 * m] = w.x; v[4 * m + 1] = w.y; v[4 * m + 2] = w.z; v[4 * m + 3] = w.w;
-        }
-        const float4 ym6 = t4[rq - 6 * NQ], ym3 = t4[rq - 3 * NQ], yp3 = t4[rq + 3 * NQ], yp6 = t4[rq + 6 * NQ];
-        const float am6[4] = {ym6.x, ym6.y, ym6.z, ym6.w}, am3[4] = {ym3.x, ym3.y, ym3.z, ym3.w};
-        const float ap3[4] = {yp3.x, yp3.y, yp3.z, yp3.w}, ap6[4] = {yp6.x, yp6.y, yp6.z, yp6.w};
-        const float bm6[4] = {zm6.x, zm6.y, zm6.z, zm6.w}, bm3[4] = {zm3.x, zm3.y, zm3.z, zm3.w};
-        const float bp3[4] = {zp3.x, zp3.y, zp3.z, zp3.w}, bp6[4] = {zp6.x, zp6.y, zp6.z, zp6.w};
-        float res[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float ctr = v[8 + j];
-            const float a3 = (v[5 + j] + v[11 + j]) + (am3[j] + ap3[j]) + (bm3[j] + bp3[j]);
-            const float a6 = (v[2 + j] + v[14 + j]) + (am6[j] + ap6[j]) + (bm6[j] + bp6[j]);
-            const float w = fmaf(18.f, ctr, fmaf(-4.f, a3, a6));
-            res[j] = solid ? 0.f : scale * w;
-        }
-        if (live) {
-            float4* op = reinterpret_cast<float4*>(o + (size_t)zo * plane_n + col);
-            float4 w = make_float4(res[0], res[1], res[2], res[3]);
-            if (accumulate) {
-                const float4 old = *op;
-                w.x += old.x; w.y += old.y; w.z += old.z; w.w += old.w;
-            }
-            *op = w;
-        }
-        b = b == 2 ? 0 : b + 1;
-    }
-    cp_async_wait0();
-}
-
 }  // namespace
 
-// L_3 in two passes when nx % 4 == 0 (the caller launches box, then cross)
+// L_3 when nx % 4 == 0 runs as one fused kernel (kernels_lap3.cu) in the
+// factorised form L_s = c C_s * B_s: L_s is L_1 dilated by the Kronecker
+// product with the s^3 block of ones, so B_s is the s x s x s box and C_s the
+// cross of l = [1, -4, 6, -4, 1] at stride s along every axis (centre 3 x 6);
+// for s = 3 a 27-point box and a 13-point cross instead of the 3 x 21 taps of
+// the separable-sum form (lap3_kernel<7, 1>).
 bool lap3_split(const Params& p, int s_scale) { return s_scale == 3 && p.nx % 4 == 0; }
-cudaError_t launch_box3(const Params& p, const float* in, float* out, int ncomp, int per_sm, cudaStream_t s) {
-    const int bx = (p.nx + bx3::TX - 1) / bx3::TX, by = (p.ny + bx3::TY - 1) / bx3::TY;
-    const int seg = seg_len(p, bx * by, ncomp, 1, per_sm > 0 ? per_sm : 8);
-    const int nseg = (p.nz + seg - 1) / seg;
-    box3_kernel<<<dim3(bx, by, ncomp * nseg), bx3::NT, 0, s>>>(p, in, out, ncomp, seg);
-    return cudaGetLastError();
-}
-cudaError_t launch_cross3s(const Params& p, const float* in, float* out, int ncomp, float scale, int accumulate,
-                           int per_sm, cudaStream_t s) {
-    const int bx = (p.nx + cs3::TX - 1) / cs3::TX, by = (p.ny + cs3::TY - 1) / cs3::TY;
-    const int seg = seg_len(p, bx * by, ncomp, 1, per_sm > 0 ? per_sm : 8);
-    const int nseg = (p.nz + seg - 1) / seg;
-    cross3s_kernel<<<dim3(bx, by, ncomp * nseg), cs3::NT, 0, s>>>(p, in, out, scale, accumulate, ncomp, seg);
-    return cudaGetLastError();
-}
 
 // L_s in 3-D for s = 1 (arm radius 2, no box) and s = 3 (arm 7, box 1).
 cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp, int s_scale, const Taps& arm,

@@ -466,17 +466,13 @@ static void enqueue_filter(Launcher& lc, const Filter& f, int slot, const float*
     float* t2 = c->L.t2;
     const double flops = 2.0 * filter_taps(f, d) * nc * (double)p.n;
     if (d == 3 && f.kind == LBM_FILTER_LAPLACE && launch_lap3_supported(f.scale)) {
-        // fused 3-D kernels: the whole filter in one pass over the field, or
-        // L_3 = c C_3 * B_3 in two streams through the scratch field
+        // fused 3-D kernels: the whole filter in one pass over the field (for
+        // L_3 with nx % 4 == 0 in the factorised form c C_3 * B_3)
         const float scale = (float)(1.0 / (8.0 * d * (double)f.scale * f.scale * f.scale));
         const double n = (double)nc * (double)p.n;
         if (lap3_split(p, f.scale)) {
-            if (lc.count_only) {
-                c->filter_flops[LBM_K_BOX3] += 2.0 * d * f.scale * n;   // s taps per axis
-                c->filter_flops[LBM_K_CROSS3S] += 2.0 * (4.0 * d + 1.0) * n;
-            }
-            LAUNCH(lc, LBM_K_BOX3, launch_box3(p, in, t1, nc, p.tune.filter_per_sm[slot], lc.s));
-            LAUNCH(lc, LBM_K_CROSS3S, launch_cross3s(p, t1, out, nc, scale, 0, p.tune.filter_per_sm[slot], lc.s));
+            if (lc.count_only) c->filter_flops[LBM_K_LAP3] += flops;
+            LAUNCH(lc, LBM_K_LAP3, launch_lap3_fused(p, in, out, nc, scale, p.tune.filter_per_sm[slot], lc.s));
             return;
         }
         if (lc.count_only) c->filter_flops[LBM_K_LAP1] += flops;
@@ -827,8 +823,7 @@ static int autotune(lbm_ctx* c) {
                 for (int v : cand) {
                     const float t = time_ms(c, [&] {
                         if (lap3_split(p, fl.scale)) {
-                            chk(launch_box3(p, c->L.x6, c->L.t1, nc, v, c->stream));
-                            chk(launch_cross3s(p, c->L.t1, c->L.acc, nc, 1.f, 0, v, c->stream));
+                            chk(launch_lap3_fused(p, c->L.x6, c->L.acc, nc, 1.f, v, c->stream));
                         } else {
                             chk(launch_lap3(p, c->L.x6, c->L.acc, nc, fl.scale, t0, 1.f, 0, v, c->stream));
                         }

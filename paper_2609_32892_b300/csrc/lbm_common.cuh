@@ -135,9 +135,10 @@ cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp,
 inline bool launch_lap3_supported(int s_scale) { return s_scale == 1 || s_scale == 3; }
 // L_3 as two launches through a scratch field (box, then cross at stride 3)
 bool lap3_split(const Params& p, int s_scale);
-cudaError_t launch_box3(const Params& p, const float* in, float* out, int ncomp, int per_sm, cudaStream_t s);
-cudaError_t launch_cross3s(const Params& p, const float* in, float* out, int ncomp, float scale, int accumulate,
-                           int per_sm, cudaStream_t s);
+// L_3 = c C_3 * B_3 in one pass (nx % 4 == 0, lap3_split): box and cross
+// through shared memory, the z arms in registers
+cudaError_t launch_lap3_fused(const Params& p, const float* in, float* out, int ncomp, float scale, int per_sm,
+                              cudaStream_t s);
 // R R of a 3-D Gaussian / binomial filter on ncomp fields is three streaming
 // passes: axis 0 (x) and 2 (z) with the composite kernel, then axis 1 (y)
 // with the wall projection; any order of the three gives the same operator

@@ -811,7 +811,7 @@ static int autotune(lbm_ctx* c) {
     if (p.to_mode != LBM_TO_OFF) {
         const int nc = p.ncomp;
         if (p.dim == 3 && !p.tune.one_seg) {
-            static const int cand[] = {2, 4, 8, 16};
+            static const int cand[] = {2, 3, 4, 6, 8, 12, 16};
             for (size_t f = 0; f < c->filters.size() && f < 8; ++f) {
                 const Filter& fl = c->filters[f];
                 // the Gaussian R R streams have fixed shapes; the fused Laplacian

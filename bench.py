@@ -326,11 +326,29 @@ def run_ours(args, world, rank, local):
                 n_nodes=n_nodes)
 
 
+def _small_member_requests(n, size, steps):
+    """n 2-D Kolmogorov members of size^2 (Smagorinsky + TO-LRS, 4 QoIs): the
+    launch-bound end of the ensemble range."""
+    reqs = []
+    for i in range(n):
+        w = synthetic.workload("C2", nx=size, ny=size, h=5, seed=300 + i)
+        nq = len(w["qois"]) + w["n_mp"]
+        c, mu, sig = synthetic.synthetic_lrs(nq, w["h"], w["seed"])
+        w.update(steps=steps, u0=synthetic.initial_velocity(w), lrs=(c, mu, sig, [0.0] * nq),
+                 steps_per_tu=synthetic.kolmogorov_lattice(size)["steps_per_tu"])
+        reqs.append(w)
+    return reqs
+
+
 def run_serving(args, device):
     """Ensemble serving on the mix of the serving configuration (horizons
     scaled by --serve-scale): offline throughput of the batched server in FP32
-    and with FP16 population storage against one-member-at-a-time FP32, then a
-    Poisson stream at ~1x the batched FP32 capacity for latency per TU."""
+    under three execution policies (the default: persistent batched kernels
+    for members of at most 16384 nodes, per-member graphs above; every member
+    on its own graph; every member persistent) and with FP16 population
+    storage, against one-member-at-a-time FP32; then a Poisson stream at ~1x
+    the batched FP32 capacity for latency per TU; and a batch of small members
+    (64 x 32^2) under the two extreme policies."""
     import torch
 
     from paper_2609_32892_b300 import serve
@@ -339,10 +357,20 @@ def run_serving(args, device):
     reqs16 = synthetic.serving_requests(args.serve_n, 7, 1.0, args.serve_scale, "fp16")
     res = {"requests": args.serve_n, "horizon_scale": args.serve_scale,
            "mix": "2-D Kolmogorov 128^2-512^2 (Smagorinsky + TO-LRS, 4 QoIs) and 3-D channel "
-                  "48x20x24-96x40x48 (WALE + TO-LRS, 12 QoIs), horizons log-uniform 1e3-1e4 steps x scale"}
+                  "48x20x24-96x40x48 (WALE + TO-LRS, 12 QoIs), horizons log-uniform 1e3-1e4 steps x scale",
+           "policies": {"default": "persistent batched kernels (1 lane) for members <= 16384 nodes, per-member "
+                                   "graphs above", "per_member_graphs": "every member replays its own graph",
+                        "persistent_all": "every member in the persistent batched kernels"}}
+    out32 = None
+    for name, lanes, mx in (("batched_fp32", 1, 16384), ("batched_fp32_per_member_graphs", 0, 0),
+                            ("batched_fp32_persistent_all", 1, 1 << 40)):
+        srv = serve.EnsembleServer(args.serve_pool_gb << 30, args.serve_slots, device, persistent=lanes, max_nodes=mx)
+        o, w, _ = srv.serve(reqs32, chunk=args.serve_chunk, keep_qoi=name == "batched_fp32", realtime=False)
+        srv.close()
+        res[name] = serve.summarize(o, w)
+        if name == "batched_fp32":
+            out32, w32 = o, w
     srv = serve.EnsembleServer(args.serve_pool_gb << 30, args.serve_slots, device)
-    out32, w32, _ = srv.serve(reqs32, chunk=args.serve_chunk, keep_qoi=True, realtime=False)
-    res["batched_fp32"] = serve.summarize(out32, w32)
     out16, w16, _ = srv.serve(reqs16, chunk=args.serve_chunk, keep_qoi=True, realtime=False)
     res["batched_fp16"] = serve.summarize(out16, w16)
     # QoI accuracy of reduced-precision storage: time-mean of each QoI, fp16 vs fp32
@@ -362,6 +390,14 @@ def run_serving(args, device):
     out_rt, w_rt, _ = srv.serve(reqs_rt, chunk=args.serve_chunk, realtime=True)
     res["poisson_fp32"] = dict(serve.summarize(out_rt, w_rt), offered_members_per_s=round(rate, 2))
     srv.close()
+    # the launch-bound end: many small members
+    small = _small_member_requests(64, 32, 400)
+    res["small_members_64x32sq"] = {}
+    for name, lanes in (("persistent", 1), ("per_member_graphs", 0)):
+        srv = serve.EnsembleServer(1 << 30, 64, device, persistent=lanes, max_nodes=1 << 40)
+        o, w, _ = srv.serve(small, chunk=100, realtime=False)
+        srv.close()
+        res["small_members_64x32sq"][name] = serve.summarize(o, w)["member_steps_per_s"]
     torch.cuda.synchronize()
     res["speedup_batched_fp16_vs_serial_fp32"] = round(
         res["batched_fp16"]["member_steps_per_s"] / res["serial_fp32"]["member_steps_per_s"], 2)

@@ -340,10 +340,12 @@ int lbm_filter_flops_per_step(lbm_ctx* ctx, double* flops, int count);
  * The caller owns one device pool; the batch carves each admitted member out
  * of it (first fit, 256-byte aligned) and returns LBM_ERR_BUDGET when a member
  * does not fit or no slot is free, so admission is by HBM budget.  Every
- * member has its own stream and its own two-step CUDA graph; lbm_batch_run
- * queues the steps of all active members without waiting, and the device
- * overlaps their kernels.  A member's results are bit-identical whether it
- * runs alone or in a mix (its kernels read only its own memory).
+ * member has its own stream; lbm_batch_run queues the steps of all active
+ * members without waiting, either as persistent batched kernels over all
+ * members (default, lbm_batch_set_persistent) or as per-member graphs that
+ * the device overlaps.  A member's results are bit-identical whether it runs
+ * alone or in a mix (its kernels read only its own memory, on the block
+ * indices of its own launch).
  * ------------------------------------------------------------------------ */
 typedef struct lbm_batch lbm_batch;
 
@@ -370,8 +372,24 @@ int lbm_batch_admit(lbm_batch* b, const lbm_config* cfg, const double* u0, int64
 int lbm_batch_member(lbm_batch* b, int32_t slot, lbm_ctx** ctx);
 
 /* Queue up to `steps` more steps of every active member (stopping at each
- * member's horizon).  Asynchronous. */
+ * member's horizon).  Asynchronous.  A member's first call records its step
+ * (and runs lbm_step's checks and tuning). */
 int lbm_batch_run(lbm_batch* b, int64_t steps);
+
+/* How members advance.  A member of at most max_nodes nodes (default 16384)
+ * with lanes > 0 (default 1) runs persistent: members whose steps run the
+ * same kernels form a class, split over `lanes` lanes (each with its own
+ * stream); every launch of a lane's step runs as one persistent kernel over
+ * all its active members (blocks draw (member, block) work items from a
+ * global queue over a member table in device memory), and a call's steps of
+ * a lane are one CUDA graph.  Other members, and those whose step makes a
+ * library call (Fourier-band filters: cuFFT), replay their own two-step graph
+ * on their own stream (lanes = 0: every member).  Small members gain from the
+ * persistent kernels (one launch per step kernel for the whole class); larger
+ * ones run faster as hardware-scheduled graphs overlapping on their streams.
+ * Results are bit-identical either way.  lanes 0..64, max_nodes >= 0; set
+ * before the members' first lbm_batch_run (LBM_ERR_STATE otherwise). */
+int lbm_batch_set_persistent(lbm_batch* b, int lanes, int64_t max_nodes);
 
 /* Flow control for a scheduler: block until at most `rounds` (0..3) of the
  * most recent lbm_batch_run calls are still executing on any member.

@@ -35,6 +35,7 @@ EXPORTED = [
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_admit", "lbm_batch_member", "lbm_batch_run",
     "lbm_batch_poll", "lbm_batch_release", "lbm_batch_stats", "lbm_set_autotune", "lbm_get_tuning", "lbm_set_branching",
     "lbm_project_shape", "lbm_project", "lbm_eval_qoi", "lbm_set_launch_goal", "lbm_batch_wait",
+    "lbm_batch_set_persistent",
 ]
 
 
@@ -105,6 +106,7 @@ def _load():
         "lbm_set_branching": [VP, C.c_int],
         "lbm_set_launch_goal": [VP, C.c_int],
         "lbm_batch_wait": [VP, C.c_int32],
+        "lbm_batch_set_persistent": [VP, C.c_int, I64],
         "lbm_project_shape": [C.POINTER(lbm_config), C.c_int, C.POINTER(C.c_int32)],
         "lbm_project": [VP, C.c_int, VP, VP],
         "lbm_eval_qoi": [VP, VP, VP],
@@ -355,6 +357,12 @@ def lbm_batch_member(b, slot):
 
 def lbm_batch_run(b, steps):
     _check(_lib.lbm_batch_run(b, int(steps)))
+
+
+def lbm_batch_set_persistent(b, lanes, max_nodes=16384):
+    """lanes: 0 = per-member graphs for every member; n > 0 = persistent batched
+    kernels (n lanes per class) for members of at most max_nodes nodes."""
+    _check(_lib.lbm_batch_set_persistent(b, int(lanes), int(max_nodes)))
 
 
 def lbm_batch_wait(b, rounds):

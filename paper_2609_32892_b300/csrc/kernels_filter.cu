@@ -8,6 +8,7 @@
 // component in shared memory with coalesced loads and convolves from there.
 // Both handle periodic wrap of any length and, along y with walls, the zero
 // extension beyond the array with zero output on solid rows.
+#include "batch.cuh"
 #include "lbm_common.cuh"
 
 namespace lbm {
@@ -22,11 +23,12 @@ __device__ __forceinline__ int posmod(int a, int n) {
 }
 
 template <int R, int NC>
-__global__ void __launch_bounds__(128) march_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                    int axis, TapsR<R> tp, float scale, int accumulate, int seg) {
+__device__ __forceinline__ void march_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                  float* __restrict__ out, int axis, TapsR<R> tp, float scale,
+                                                  int accumulate, int seg) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int other = axis == 1 ? nz : ny;
-    const int line = blockIdx.x * blockDim.x + threadIdx.x;
+    const int line = vb.x * blockDim.x + threadIdx.x;
     if (line >= nx * other) return;
     const int x = line % nx;
     const int o = line / nx;
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(128) march_kernel(Params p, const float* __res
     const size_t base = axis == 1 ? (size_t)o * ny * nx + x : (size_t)o * nx + x;
     const size_t N = (size_t)p.n;
     const bool zero_pad = axis == 1 && p.walls;
-    const int p0 = blockIdx.y * seg;
+    const int p0 = vb.y * seg;
     const int p1 = min(L, p0 + seg);
     if (p0 >= L) return;
     float w[NC][2 * R + 1];
@@ -73,17 +75,30 @@ __global__ void __launch_bounds__(128) march_kernel(Params p, const float* __res
         }
     }
 }
+template <int R, int NC>
+struct march_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        march_kernel_body<R, NC>(vb, b...);
+    }
+};
+template <int R, int NC>
+__global__ void __launch_bounds__(128) march_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                    int axis, TapsR<R> tp, float scale, int accumulate, int seg) {
+    march_kernel_body<R, NC>(vb_hw(), p, in, out, axis, tp, scale, accumulate, seg);
+}
 
 constexpr int kTX = 128;
 
 template <int R, int NC>
-__global__ void __launch_bounds__(kTX) xpass_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                    TapsR<R> tp, float scale, int accumulate) {
+__device__ __forceinline__ void xpass_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                  float* __restrict__ out, TapsR<R> tp, float scale, int accumulate) {
     __shared__ float sm[NC][kTX + 2 * R];
     const int nx = p.nx, ny = p.ny;
-    const int row = blockIdx.y;  // z * ny + y
+    const int row = vb.y;  // z * ny + y
     const int y = row % ny;
-    const int x0 = blockIdx.x * kTX;
+    const int x0 = vb.x * kTX;
     const size_t N = (size_t)p.n;
     const size_t rbase = (size_t)row * nx;
     const int x = x0 + threadIdx.x;
@@ -110,6 +125,19 @@ __global__ void __launch_bounds__(kTX) xpass_kernel(Params p, const float* __res
         *op = accumulate ? (*op + v) : v;
     }
 }
+template <int R, int NC>
+struct xpass_kernel_op {
+    static constexpr int NT = kTX, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        xpass_kernel_body<R, NC>(vb, b...);
+    }
+};
+template <int R, int NC>
+__global__ void __launch_bounds__(kTX) xpass_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                    TapsR<R> tp, float scale, int accumulate) {
+    xpass_kernel_body<R, NC>(vb_hw(), p, in, out, tp, scale, accumulate);
+}
 
 template <int R, int NC>
 static cudaError_t run(const Params& p, const float* in, float* out, int axis, const Taps& t, float scale,
@@ -118,7 +146,7 @@ static cudaError_t run(const Params& p, const float* in, float* out, int axis, c
     for (int i = 0; i < 2 * R + 1; ++i) tr.t[i] = t.t[i];
     if (axis == 0) {
         dim3 grid((p.nx + kTX - 1) / kTX, p.ny * p.nz);
-        xpass_kernel<R, NC><<<grid, kTX, 0, s>>>(p, in, out, tr, scale, accumulate);
+        go<xpass_kernel_op<R, NC>>(xpass_kernel<R, NC>, grid, kTX, 0, s, p, in, out, tr, scale, accumulate);
     } else {
         const int L = axis == 1 ? p.ny : p.nz;
         const int lines = p.nx * (axis == 1 ? p.nz : p.ny);
@@ -130,7 +158,8 @@ static cudaError_t run(const Params& p, const float* in, float* out, int axis, c
         if (seg > L) seg = L;
         nseg = (L + seg - 1) / seg;
         dim3 grid((lines + 127) / 128, nseg);
-        march_kernel<R, NC><<<grid, 128, 0, s>>>(p, in, out, axis, tr, scale, accumulate, seg);
+        go<march_kernel_op<R, NC>>(march_kernel<R, NC>, grid, 128, 0, s, p, in, out, axis, tr, scale, accumulate,
+                                   seg);
     }
     return cudaGetLastError();
 }
@@ -169,15 +198,16 @@ constexpr int TX = 32, TY = 32, NT = 256;
 }
 
 template <int R>
-__global__ void __launch_bounds__(256) gauss2_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                     TapsR<R> tp, float scale, int accumulate) {
+__device__ __forceinline__ void gauss2_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                   float* __restrict__ out, TapsR<R> tp, float scale,
+                                                   int accumulate) {
     constexpr int TX = f2::TX, TY = f2::TY, NT = f2::NT, W = TX + 2 * R, H = TY + 2 * R;
     __shared__ float tile[H * W];
     __shared__ float xt[H * TX];
     const size_t N = (size_t)p.n;
-    const float* a = in + blockIdx.z * N;
-    float* o = out + blockIdx.z * N;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const float* a = in + vb.z * N;
+    float* o = out + vb.z * N;
+    const int x0 = vb.x * TX, y0 = vb.y * TY;
     for (int i = threadIdx.x; i < H * W; i += NT) {
         const int ly = i / W, lx = i - ly * W;
         const int gx = posmod(x0 - R + lx, p.nx), gy = posmod(y0 - R + ly, p.ny);
@@ -217,16 +247,30 @@ __global__ void __launch_bounds__(256) gauss2_kernel(Params p, const float* __re
         }
     }
 }
+template <int R>
+struct gauss2_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        gauss2_kernel_body<R>(vb, b...);
+    }
+};
+template <int R>
+__global__ void __launch_bounds__(256) gauss2_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                     TapsR<R> tp, float scale, int accumulate) {
+    gauss2_kernel_body<R>(vb_hw(), p, in, out, tp, scale, accumulate);
+}
 
 // L_1 in 2-D: the 9-point cross of l = [1, -4, 6, -4, 1] along x and y
-__global__ void __launch_bounds__(256) cross2_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                     TapsR<2> ell, float scale, int accumulate) {
+__device__ __forceinline__ void cross2_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                   float* __restrict__ out, TapsR<2> ell, float scale,
+                                                   int accumulate) {
     constexpr int R = 2, TX = f2::TX, TY = f2::TY, NT = f2::NT, W = TX + 2 * R, H = TY + 2 * R;
     __shared__ float tile[H * W];
     const size_t N = (size_t)p.n;
-    const float* a = in + blockIdx.z * N;
-    float* o = out + blockIdx.z * N;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const float* a = in + vb.z * N;
+    float* o = out + vb.z * N;
+    const int x0 = vb.x * TX, y0 = vb.y * TY;
     for (int i = threadIdx.x; i < H * W; i += NT) {
         const int ly = i / W, lx = i - ly * W;
         const int gx = posmod(x0 - R + lx, p.nx), gy = posmod(y0 - R + ly, p.ny);
@@ -249,6 +293,17 @@ __global__ void __launch_bounds__(256) cross2_kernel(Params p, const float* __re
         }
     }
 }
+struct cross2_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        cross2_kernel_body(vb, b...);
+    }
+};
+__global__ void __launch_bounds__(256) cross2_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                     TapsR<2> ell, float scale, int accumulate) {
+    cross2_kernel_body(vb_hw(), p, in, out, ell, scale, accumulate);
+}
 
 template <int R>
 static cudaError_t run_gauss2(const Params& p, const float* in, float* out, int ncomp, const Taps& t, float scale,
@@ -256,7 +311,7 @@ static cudaError_t run_gauss2(const Params& p, const float* in, float* out, int 
     TapsR<R> tr;
     for (int i = 0; i < 2 * R + 1; ++i) tr.t[i] = t.t[i];
     const dim3 grid((p.nx + f2::TX - 1) / f2::TX, (p.ny + f2::TY - 1) / f2::TY, ncomp);
-    gauss2_kernel<R><<<grid, f2::NT, 0, s>>>(p, in, out, tr, scale, accumulate);
+    go<gauss2_kernel_op<R>>(gauss2_kernel<R>, grid, f2::NT, 0, s, p, in, out, tr, scale, accumulate);
     return cudaGetLastError();
 }
 
@@ -270,7 +325,7 @@ cudaError_t launch_filter2_fused(const Params& p, const float* in, float* out, i
         TapsR<2> tr;
         for (int i = 0; i < 5; ++i) tr.t[i] = t.t[i];
         const dim3 grid((p.nx + f2::TX - 1) / f2::TX, (p.ny + f2::TY - 1) / f2::TY, ncomp);
-        cross2_kernel<<<grid, f2::NT, 0, s>>>(p, in, out, tr, scale, accumulate);
+        go<cross2_kernel_op>(cross2_kernel, grid, f2::NT, 0, s, p, in, out, tr, scale, accumulate);
         return cudaGetLastError();
     }
     switch (t.radius) {

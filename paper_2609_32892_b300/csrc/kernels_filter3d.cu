@@ -23,6 +23,7 @@
 // Periodic along x and z; along y with walls the halo outside the array reads
 // zero (solid rows already hold zero), and outputs on solid rows are zero, so
 // the kernel applies P K P exactly.  One component per blockIdx.z slice.
+#include "batch.cuh"
 #include "lbm_common.cuh"
 
 namespace lbm {
@@ -90,8 +91,9 @@ struct TileLoader {
 // of plane q was last read in phase B of plane q-2, which every thread left
 // before the first barrier of plane q-1.
 template <int RA, int RB>
-__global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                   T3<RA> arm, float scale, int accumulate, int ncomp, int seg) {
+__device__ __forceinline__ void lap3_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                 float* __restrict__ out, T3<RA> arm, float scale, int accumulate,
+                                                 int ncomp, int seg) {
     constexpr int NT = 256, RPT = TY / (NT / TX);  // 2 output rows per thread
     using LD = TileLoader<RA, NT>;
     constexpr int WP = LD::WP, HH = LD::HH, W = LD::W;
@@ -100,10 +102,10 @@ __global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __rest
     __shared__ __align__(16) float tile[2][HH * WP];
     __shared__ __align__(16) float by[2][TY * WP];  // box along y on the output rows, every tile column
     __shared__ __align__(16) float bx[2][HH * TX];  // box along x on every tile row, output columns
-    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int c = vb.z % ncomp, zs = vb.z / ncomp;
     const int nz = p.nz;
     const int z0 = zs * seg, z1 = min(nz, z0 + seg);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = vb.x * TX, y0 = vb.y * TY;
     const int lx = threadIdx.x % TX, yr = threadIdx.x / TX;
     const int x = x0 + lx;
     const size_t N = (size_t)p.n;
@@ -200,21 +202,35 @@ __global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __rest
         }
     }
 }
+template <int RA, int RB>
+struct lap3_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        lap3_kernel_body<RA, RB>(vb, b...);
+    }
+};
+template <int RA, int RB>
+__global__ void __launch_bounds__(256) lap3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                   T3<RA> arm, float scale, int accumulate, int ncomp, int seg) {
+    lap3_kernel_body<RA, RB>(vb_hw(), p, in, out, arm, scale, accumulate, ncomp, seg);
+}
 
 // L_1 (no box): the 13-point cross l_x + l_y + l_z read straight from the
 // double-buffered tile, one barrier per plane.
 template <int RA>
-__global__ void __launch_bounds__(256) cross3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                     T3<RA> arm, float scale, int accumulate, int ncomp, int seg) {
+__device__ __forceinline__ void cross3_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                   float* __restrict__ out, T3<RA> arm, float scale, int accumulate,
+                                                   int ncomp, int seg) {
     constexpr int NT = 256, RPT = TY / (NT / TX);
     using LD = TileLoader<RA, NT>;
     constexpr int WP = LD::WP, HH = LD::HH;
     constexpr int KZ = 2 * RA + 1;
     __shared__ __align__(16) float tile[2][HH * WP];
-    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int c = vb.z % ncomp, zs = vb.z / ncomp;
     const int nz = p.nz;
     const int z0 = zs * seg, z1 = min(nz, z0 + seg);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = vb.x * TX, y0 = vb.y * TY;
     const int lx = threadIdx.x % TX, yr = threadIdx.x / TX;
     const int x = x0 + lx;
     const size_t N = (size_t)p.n;
@@ -269,6 +285,19 @@ __global__ void __launch_bounds__(256) cross3_kernel(Params p, const float* __re
         }
     }
 }
+template <int RA>
+struct cross3_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        cross3_kernel_body<RA>(vb, b...);
+    }
+};
+template <int RA>
+__global__ void __launch_bounds__(256) cross3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                     T3<RA> arm, float scale, int accumulate, int ncomp, int seg) {
+    cross3_kernel_body<RA>(vb_hw(), p, in, out, arm, scale, accumulate, ncomp, seg);
+}
 
 // asynchronous 16-byte global -> shared copies (zero-fill when src_bytes = 0)
 __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, int src_bytes) {
@@ -301,9 +330,11 @@ cudaError_t run_lap(const Params& p, const float* in, float* out, int ncomp, con
     const int seg = seg_len(p, bx * by, ncomp, RA, per_sm > 0 ? per_sm : 4);
     const int nseg = (p.nz + seg - 1) / seg;
     if (RB == 0)
-        cross3_kernel<RA><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+        go<cross3_kernel_op<RA>>(cross3_kernel<RA>, dim3(bx, by, ncomp * nseg), 256, 0, s, p, in, out, tp, scale, acc,
+                                 ncomp, seg);
     else
-        lap3_kernel<RA, RB><<<dim3(bx, by, ncomp * nseg), 256, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+        go<lap3_kernel_op<RA, RB>>(lap3_kernel<RA, RB>, dim3(bx, by, ncomp * nseg), 256, 0, s, p, in, out, tp, scale,
+                                   acc, ncomp, seg);
     return cudaGetLastError();
 }
 // L_1 (the 13-point cross, arm radius 2) with planes staged by asynchronous
@@ -327,16 +358,17 @@ constexpr int NB = 8;              // plane buffers (a power of two)
 
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
-__global__ void __launch_bounds__(128) crossq3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                      T3<2> arm, float scale, int accumulate, int ncomp, int seg) {
+__device__ __forceinline__ void crossq3_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                    float* __restrict__ out, T3<2> arm, float scale, int accumulate,
+                                                    int ncomp, int seg) {
     constexpr int TX = cq3::TX, TY = cq3::TY, RA = cq3::RA, HX = cq3::HX, HY = cq3::HY;
     constexpr int NQ = cq3::NQ, TH = cq3::TH, NT = cq3::NT, SZ = cq3::SZ, NB = cq3::NB;
     __shared__ __align__(16) float tile[NB][SZ];
     __shared__ int coff[TH * NQ];
-    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int c = vb.z % ncomp, zs = vb.z / ncomp;
     const int nz = p.nz;
     const int z0 = zs * seg, z1 = min(nz, z0 + seg);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = vb.x * TX, y0 = vb.y * TY;
     const int qx = threadIdx.x & 7, ry = threadIdx.x >> 3;
     const int gx0 = x0 + 4 * qx, y = y0 + ry;
     const size_t N = (size_t)p.n;
@@ -416,6 +448,17 @@ __global__ void __launch_bounds__(128) crossq3_kernel(Params p, const float* __r
     }
     cp_async_wait0();
 }
+struct crossq3_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        crossq3_kernel_body(vb, b...);
+    }
+};
+__global__ void __launch_bounds__(128) crossq3_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                      T3<2> arm, float scale, int accumulate, int ncomp, int seg) {
+    crossq3_kernel_body(vb_hw(), p, in, out, arm, scale, accumulate, ncomp, seg);
+}
 
 // L_1 with asynchronously staged planes; needs nx % 4 == 0
 cudaError_t run_crossq3(const Params& p, const float* in, float* out, int ncomp, const Taps& arm, float scale, int acc,
@@ -425,7 +468,8 @@ cudaError_t run_crossq3(const Params& p, const float* in, float* out, int ncomp,
     const int bx = (p.nx + cq3::TX - 1) / cq3::TX, by = (p.ny + cq3::TY - 1) / cq3::TY;
     const int seg = seg_len(p, bx * by, ncomp, 2, per_sm > 0 ? per_sm : 8);
     const int nseg = (p.nz + seg - 1) / seg;
-    crossq3_kernel<<<dim3(bx, by, ncomp * nseg), cq3::NT, 0, s>>>(p, in, out, tp, scale, acc, ncomp, seg);
+    go<crossq3_kernel_op>(crossq3_kernel, dim3(bx, by, ncomp * nseg), cq3::NT, 0, s, p, in, out, tp, scale, acc, ncomp,
+                          seg);
     return cudaGetLastError();
 }
 
@@ -446,7 +490,7 @@ cudaError_t launch_lap3(const Params& p, const float* in, float* out, int ncomp,
         if (p.nx % 4 == 0) return run_crossq3(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
         return run_lap<2, 0>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
     }
-    // L_3 with nx % 4 == 0 goes through lap3_split (box, then cross)
+    // L_3 with nx % 4 == 0 goes through lap3_split (the fused kernel of kernels_lap3.cu)
     if (s_scale == 3 && arm.radius == 7) return run_lap<7, 1>(p, in, out, ncomp, arm, scale, accumulate, per_sm, s);
     return cudaErrorNotSupported;
 }

@@ -28,6 +28,7 @@
 // in flight at once and the per-element address arithmetic disappears; each
 // thread then reads its column from shared memory with immediate offsets.
 // Other shapes take the direct-load kernels.
+#include "batch.cuh"
 #include "lbm_common.cuh"
 #include "tma.cuh"
 
@@ -42,14 +43,15 @@ __host__ __device__ constexpr int rup4(int v) { return (v + 3) & ~3; }
 
 // x pass: out(x) = sum_k c[k] in(x + k - RC), periodic in x.
 template <int RC>
-__global__ void __launch_bounds__(128) gx_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                 GaussTaps gt, int chunks_per_row, long long nchunks) {
+__device__ __forceinline__ void gx_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                               float* __restrict__ out, const GaussTaps& gt, int chunks_per_row,
+                                               long long nchunks) {
     constexpr int RCP = rup4(RC);
     constexpr int SW = kGxChunk + 2 * RCP;  // staged values per warp
     constexpr int NW = 8 + 2 * RC;          // window of one lane (even; a multiple of 4 when RC is)
     __shared__ __align__(16) float sm[4][SW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long ch = (long long)blockIdx.x * 4 + warp;
+    const long long ch = (long long)vb.x * 4 + warp;
     if (ch >= nchunks) return;  // whole warp leaves together
     const int nx = p.nx;
     const long long row = ch / chunks_per_row;  // (comp, z, y) row
@@ -115,21 +117,34 @@ __global__ void __launch_bounds__(128) gx_kernel(Params p, const float* __restri
             if (xl + j < nx) dst[j] = o[j];
     }
 }
+template <int RC>
+struct gx_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        gx_kernel_body<RC>(vb, b...);
+    }
+};
+template <int RC>
+__global__ void __launch_bounds__(128) gx_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                 GaussTaps gt, int chunks_per_row, long long nchunks) {
+    gx_kernel_body<RC>(vb_hw(), p, in, out, gt, chunks_per_row, nchunks);
+}
 
 // z pass: out(z) = sum_k c[k] in(z + k - RC), periodic in z; one thread per
 // (x, y) node of the plane and strip of kStripZ outputs.
 template <int RC>
-__global__ void __launch_bounds__(128) gz_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                 GaussTaps gt) {
+__device__ __forceinline__ void gz_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                               float* __restrict__ out, const GaussTaps& gt) {
     constexpr int M = kStripZ, NV = M + 2 * RC;
     const int nz = p.nz;
     const long long plane = (long long)p.nx * p.ny;
-    const long long nxy = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+    const long long nxy = (long long)vb.y * blockDim.x + threadIdx.x;
     if (nxy >= plane) return;
-    const int z0 = blockIdx.x * M;
+    const int z0 = vb.x * M;
     const size_t N = (size_t)p.n;
-    const float* a = in + (size_t)blockIdx.z * N + nxy;
-    float* o = out + (size_t)blockIdx.z * N + nxy;
+    const float* a = in + (size_t)vb.z * N + nxy;
+    float* o = out + (size_t)vb.z * N + nxy;
     float v[NV];
     if (z0 - RC >= 0 && z0 + M + RC <= nz) {
         // interior strip: consecutive planes, no wrap
@@ -158,6 +173,19 @@ __global__ void __launch_bounds__(128) gz_kernel(Params p, const float* __restri
     for (int j = 0; j < M; ++j)
         if (z0 + j < nz) o[(size_t)(z0 + j) * plane] = r[j];
 }
+template <int RC>
+struct gz_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        gz_kernel_body<RC>(vb, b...);
+    }
+};
+template <int RC>
+__global__ void __launch_bounds__(128) gz_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                 GaussTaps gt) {
+    gz_kernel_body<RC>(vb_hw(), p, in, out, gt);
+}
 
 // y pass: one thread per (z, x) column and strip of kStripZ outputs.
 // Periodic y: the composite kernel.  Walls: inputs outside the array are
@@ -165,19 +193,19 @@ __global__ void __launch_bounds__(128) gz_kernel(Params p, const float* __restri
 // fluid takes the composite kernel, the others two stages, u = P (t * in)
 // on rows y0 - R .. y0 + M - 1 + R, then t * u; outputs on solid rows are zero.
 template <int R>
-__global__ void __launch_bounds__(128) gy_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                 GaussTaps gt) {
+__device__ __forceinline__ void gy_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                               float* __restrict__ out, const GaussTaps& gt) {
     constexpr int M = kStripZ, RC = 2 * R, NV = M + 2 * RC, NU = M + 2 * R;
     const int nx = p.nx, ny = p.ny;
     const long long nzx = (long long)p.nz * nx;
-    const long long t = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+    const long long t = (long long)vb.y * blockDim.x + threadIdx.x;
     if (t >= nzx) return;
     const int z = (int)(t / nx), x = (int)(t - (long long)z * nx);
-    const int y0 = blockIdx.x * M;
+    const int y0 = vb.x * M;
     const size_t N = (size_t)p.n;
     const size_t col = (size_t)z * ny * nx + x;
-    const float* a = in + (size_t)blockIdx.z * N + col;
-    float* o = out + (size_t)blockIdx.z * N + col;
+    const float* a = in + (size_t)vb.z * N + col;
+    float* o = out + (size_t)vb.z * N + col;
     float v[NV];
     if (y0 - RC >= 0 && y0 + M + RC <= ny) {
         // interior strip: every row inside the array, no wrap
@@ -235,6 +263,19 @@ __global__ void __launch_bounds__(128) gy_kernel(Params p, const float* __restri
         if (y < ny) o[(size_t)y * nx] = (p.walls && (y == 0 || y == ny - 1)) ? 0.f : r[j];
     }
 }
+template <int R>
+struct gy_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        gy_kernel_body<R>(vb, b...);
+    }
+};
+template <int R>
+__global__ void __launch_bounds__(128) gy_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                 GaussTaps gt) {
+    gy_kernel_body<R>(vb_hw(), p, in, out, gt);
+}
 
 // ---- bulk-copy staged passes (nx % 4 == 0) ----
 
@@ -250,19 +291,22 @@ __device__ __forceinline__ float2 ffma2(float c, float2 v, float2 acc) { return 
 // thread sums its two adjacent columns (8-byte shared loads and global
 // stores, packed FMAs).
 template <int RC>
-__global__ void __launch_bounds__(64) gz_tma_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                    GaussTaps gt, DevState* st) {
+__device__ __forceinline__ void gz_tma_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                   float* __restrict__ out, const GaussTaps& gt, DevState* st) {
     constexpr int M = kStripZ, NV = M + 2 * RC;
     __shared__ __align__(128) float tile[NV][kTileW];
     __shared__ __align__(8) uint64_t bar;
     const int nz = p.nz;
     const long long plane = (long long)p.nx * p.ny;
-    const long long c0 = (long long)blockIdx.y * kTileW;
+    const long long c0 = (long long)vb.y * kTileW;
     const int width = (int)min((long long)kTileW, plane - c0);
-    const int z0 = blockIdx.x * M;
+    const int z0 = vb.x * M;
     const size_t N = (size_t)p.n;
-    const float* a = in + (size_t)blockIdx.z * N + c0;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    const float* a = in + (size_t)vb.z * N + c0;
+    // the barrier is set up by a block's first item; item i waits on phase i
+    // (a persistent block of a batched launch runs many items)
+    if (vb.it == 0 && threadIdx.x == 0) mbar_init(&bar, 1);
+    const uint32_t ph = (uint32_t)vb.it & 1u;
     __syncthreads();
     if (threadIdx.x < 32) {
         // warp 0 issues the copies, one plane per lane (no serial chain)
@@ -279,9 +323,10 @@ __global__ void __launch_bounds__(64) gz_tma_kernel(Params p, const float* __res
             }
             bulk_load(&tile[k][0], a + (size_t)zk * plane, bytes, &bar);
         }
+        __syncwarp();  // every copy issued before any lane of the warp waits
     }
-    if (!mbar_wait(&bar, 0)) {
-        mbar_give_up(&bar, 0, st);
+    if (!mbar_wait(&bar, ph)) {
+        mbar_give_up(&bar, ph, st);
         return;
     }
     const int t2 = 2 * threadIdx.x;  // columns t2, t2 + 1 (width is a multiple of 4)
@@ -296,7 +341,7 @@ __global__ void __launch_bounds__(64) gz_tma_kernel(Params p, const float* __res
         for (int j = 0; j < M; ++j)
             if (k - j >= 0 && k - j <= 2 * RC) r[j] = ffma2(gt.c[k - j], v, r[j]);
     }
-    float* o = out + (size_t)blockIdx.z * N + c0 + t2 + (size_t)z0 * plane;
+    float* o = out + (size_t)vb.z * N + c0 + t2 + (size_t)z0 * plane;
     if (z0 + M <= nz) {
 #pragma unroll
         for (int j = 0; j < M; ++j) *reinterpret_cast<float2*>(o + (size_t)j * plane) = r[j];
@@ -306,24 +351,39 @@ __global__ void __launch_bounds__(64) gz_tma_kernel(Params p, const float* __res
             if (z0 + j < nz) *reinterpret_cast<float2*>(o + (size_t)j * plane) = r[j];
     }
 }
+template <int RC>
+struct gz_tma_kernel_op {
+    static constexpr int NT = 64, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        gz_tma_kernel_body<RC>(vb, b...);
+    }
+};
+template <int RC>
+__global__ void __launch_bounds__(64) gz_tma_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                    GaussTaps gt, DevState* st) {
+    gz_tma_kernel_body<RC>(vb_hw(), p, in, out, gt, st);
+}
 
 // y pass: a block of 64 threads stages rows y0 - 2R .. y0 + M + 2R - 1 of a
 // 128-column piece of an x row at one z (rows outside the array: zero with
 // walls, wrapped without), then each thread runs its two adjacent columns as
 // gy_kernel does (composite, or two stages next to the walls).
 template <int R>
-__global__ void __launch_bounds__(64) gy_tma_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                    GaussTaps gt, DevState* st, int cpr) {
+__device__ __forceinline__ void gy_tma_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                   float* __restrict__ out, const GaussTaps& gt, DevState* st,
+                                                   int cpr) {
     constexpr int M = kStripZ, RC = 2 * R, NV = M + 2 * RC, NU = M + 2 * R;
     __shared__ __align__(128) float tile[NV][kTileW];
     __shared__ __align__(8) uint64_t bar;
     const int nx = p.nx, ny = p.ny;
-    const int z = blockIdx.y / cpr, x0 = (blockIdx.y - z * cpr) * kTileW;
+    const int z = vb.y / cpr, x0 = (vb.y - z * cpr) * kTileW;
     const int width = min(kTileW, nx - x0);
-    const int y0 = blockIdx.x * M;
+    const int y0 = vb.x * M;
     const size_t N = (size_t)p.n;
-    const float* a = in + (size_t)blockIdx.z * N + (size_t)z * ny * nx + x0;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    const float* a = in + (size_t)vb.z * N + (size_t)z * ny * nx + x0;
+    if (vb.it == 0 && threadIdx.x == 0) mbar_init(&bar, 1);  // phase i for the block's item i
+    const uint32_t ph = (uint32_t)vb.it & 1u;
     // with walls, rows outside the array are zero (generic stores to rows no
     // copy touches); only the strips next to the walls have such rows
     const int klo = p.walls ? max(0, RC - y0) : 0;            // first row inside the array
@@ -350,9 +410,10 @@ __global__ void __launch_bounds__(64) gy_tma_kernel(Params p, const float* __res
             }
             bulk_load(&tile[k][0], a + (size_t)y * nx, bytes, &bar);
         }
+        __syncwarp();  // every copy issued before any lane of the warp waits
     }
-    if (!mbar_wait(&bar, 0)) {
-        mbar_give_up(&bar, 0, st);
+    if (!mbar_wait(&bar, ph)) {
+        mbar_give_up(&bar, ph, st);
         return;
     }
     const int t2 = 2 * threadIdx.x;  // columns t2, t2 + 1 (width is a multiple of 4)
@@ -391,7 +452,7 @@ __global__ void __launch_bounds__(64) gy_tma_kernel(Params p, const float* __res
             for (int j = 0; j < M; ++j)
                 if (i - j >= 0 && i - j <= 2 * R) r[j] = ffma2(gt.t[i - j], u[i], r[j]);
     }
-    float* o = out + (size_t)blockIdx.z * N + (size_t)z * ny * nx + x0 + t2 + (size_t)y0 * nx;
+    float* o = out + (size_t)vb.z * N + (size_t)z * ny * nx + x0 + t2 + (size_t)y0 * nx;
     if (y0 + M <= ny - 1 && y0 >= 1) {
 #pragma unroll
         for (int j = 0; j < M; ++j) *reinterpret_cast<float2*>(o + (size_t)j * nx) = r[j];
@@ -405,6 +466,19 @@ __global__ void __launch_bounds__(64) gy_tma_kernel(Params p, const float* __res
         }
     }
 }
+template <int R>
+struct gy_tma_kernel_op {
+    static constexpr int NT = 64, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        gy_tma_kernel_body<R>(vb, b...);
+    }
+};
+template <int R>
+__global__ void __launch_bounds__(64) gy_tma_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                    GaussTaps gt, DevState* st, int cpr) {
+    gy_tma_kernel_body<R>(vb_hw(), p, in, out, gt, st, cpr);
+}
 
 // x pass: warp w of the block stages the whole row blockIdx.x * 4 + w plus
 // its periodic halo (three bulk copies: the row's last RCP values, the row,
@@ -414,14 +488,15 @@ __global__ void __launch_bounds__(64) gy_tma_kernel(Params p, const float* __res
 constexpr int kGxRowMax = 2992;  // 4 rows of (2992 + 2 x 12) floats: 48 KiB
 
 template <int RC>
-__global__ void __launch_bounds__(128) gx_tma_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                     GaussTaps gt, DevState* st, long long nrows) {
+__device__ __forceinline__ void gx_tma_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                   float* __restrict__ out, const GaussTaps& gt, DevState* st,
+                                                   long long nrows) {
     constexpr int RCP = rup4(RC);
     constexpr int NW = 8 + 2 * RC;
     extern __shared__ __align__(128) float gx_sm[];
     __shared__ __align__(8) uint64_t bars[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long row = (long long)blockIdx.x * 4 + warp;
+    const long long row = (long long)vb.x * 4 + warp;
     const int nx = p.nx;
     // row length rounded up to 8 so that the last lane group's window (up to
     // 8 outputs past a row end that is only 4-aligned) stays inside the row's
@@ -430,9 +505,17 @@ __global__ void __launch_bounds__(128) gx_tma_kernel(Params p, const float* __re
     float* s = gx_sm + warp * sw;
     uint64_t* bar = &bars[warp];
     const bool live = row < nrows;
-    if (lane == 0 && live) mbar_init(bar, 1);
-    __syncwarp();
-    if (!live) return;  // whole warp
+    // the barriers are set up by a block's first item; item i waits on phase
+    // i, and a warp without a row completes its phase by a plain arrival
+    if (vb.it == 0) {
+        if (threadIdx.x < 4) mbar_init(&bars[threadIdx.x], 1);
+        __syncthreads();
+    }
+    const uint32_t ph = (uint32_t)vb.it & 1u;
+    if (!live) {  // whole warp
+        if (lane == 0) mbar_arrive(bar);
+        return;
+    }
     const float* src = in + row * nx;
     if (lane == 0) {
         mbar_arrive_expect(bar, (uint32_t)(nx + 2 * RCP) * 4u);
@@ -440,9 +523,10 @@ __global__ void __launch_bounds__(128) gx_tma_kernel(Params p, const float* __re
         bulk_load(s + RCP, src, (uint32_t)nx * 4u, bar);
         bulk_load(s + RCP + nx, src, RCP * 4u, bar);
     }
-    if (!mbar_wait(bar, 0)) {
-        if (lane == 0) atomicOr(&st->status, kStatusTimeout);
-        mbar_wait(bar, 0);
+    __syncwarp();  // the copies issued before any lane waits
+    if (!mbar_wait(bar, ph)) {
+        atomicOr(&st->status, kStatusTimeout);
+        mbar_wait(bar, ph);
         return;
     }
     constexpr int VW = RC % 4 == 0 ? 4 : 2;
@@ -481,6 +565,19 @@ __global__ void __launch_bounds__(128) gx_tma_kernel(Params p, const float* __re
         }
     }
 }
+template <int RC>
+struct gx_tma_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        gx_tma_kernel_body<RC>(vb, b...);
+    }
+};
+template <int RC>
+__global__ void __launch_bounds__(128) gx_tma_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                     GaussTaps gt, DevState* st, long long nrows) {
+    gx_tma_kernel_body<RC>(vb_hw(), p, in, out, gt, st, nrows);
+}
 
 }  // namespace
 
@@ -496,30 +593,31 @@ static void gauss_pass(const Params& p, int axis, const float* in, float* out, i
         const long long nrows = (long long)ncomp * p.nz * p.ny;
         if (bulk && p.nx >= rup4(RC) && p.nx <= kGxRowMax) {
             const size_t smem = (size_t)4 * (((p.nx + 7) & ~7) + 2 * rup4(RC)) * sizeof(float);
-            gx_tma_kernel<RC><<<(unsigned)((nrows + 3) / 4), 128, smem, s>>>(p, in, out, gt, st, nrows);
+            go<gx_tma_kernel_op<RC>>(gx_tma_kernel<RC>, (unsigned)((nrows + 3) / 4), 128, smem, s, p, in, out, gt, st,
+                                     nrows);
             return;
         }
         const long long nchunks = nrows * cpr;
-        gx_kernel<RC><<<(unsigned)((nchunks + 3) / 4), 128, 0, s>>>(p, in, out, gt, cpr, nchunks);
+        go<gx_kernel_op<RC>>(gx_kernel<RC>, (unsigned)((nchunks + 3) / 4), 128, 0, s, p, in, out, gt, cpr, nchunks);
     } else if (axis == 2) {
         const long long plane = (long long)p.nx * p.ny;
         if (bulk) {
             const dim3 g((p.nz + kStripZ - 1) / kStripZ, (unsigned)((plane + kTileW - 1) / kTileW), ncomp);
-            gz_tma_kernel<RC><<<g, 64, 0, s>>>(p, in, out, gt, st);
+            go<gz_tma_kernel_op<RC>>(gz_tma_kernel<RC>, g, 64, 0, s, p, in, out, gt, st);
             return;
         }
         const dim3 g((p.nz + kStripZ - 1) / kStripZ, (unsigned)((plane + 127) / 128), ncomp);
-        gz_kernel<RC><<<g, 128, 0, s>>>(p, in, out, gt);
+        go<gz_kernel_op<RC>>(gz_kernel<RC>, g, 128, 0, s, p, in, out, gt);
     } else {
         if (bulk) {
             const int cpr = (p.nx + kTileW - 1) / kTileW;
             const dim3 g((p.ny + kStripZ - 1) / kStripZ, (unsigned)(p.nz * cpr), ncomp);
-            gy_tma_kernel<R><<<g, 64, 0, s>>>(p, in, out, gt, st, cpr);
+            go<gy_tma_kernel_op<R>>(gy_tma_kernel<R>, g, 64, 0, s, p, in, out, gt, st, cpr);
             return;
         }
         const long long nzx = (long long)p.nz * p.nx;
         const dim3 g((p.ny + kStripZ - 1) / kStripZ, (unsigned)((nzx + 127) / 128), ncomp);
-        gy_kernel<R><<<g, 128, 0, s>>>(p, in, out, gt);
+        go<gy_kernel_op<R>>(gy_kernel<R>, g, 128, 0, s, p, in, out, gt);
     }
 }
 

@@ -25,6 +25,7 @@
 // output node once: 8 B per node and component.
 #include <mutex>
 
+#include "batch.cuh"
 #include "lbm_common.cuh"
 
 #ifndef L3_TY
@@ -90,19 +91,18 @@ __device__ __forceinline__ Quad qfma(float s, Quad a, Quad b) {
 __device__ __forceinline__ Quad qzero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
 
 template <int TY, int NS>
-__global__ void __launch_bounds__(L3Shape<TY, NS>::NT, 2) lap3_fused_kernel(Params p, const float* __restrict__ in,
-                                                                          float* __restrict__ out, float scale,
-                                                                          int ncomp, int seg) {
+__device__ __forceinline__ void lap3_fused_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                       float* __restrict__ out, float scale, int ncomp, int seg) {
     using S = L3Shape<TY, NS>;
     constexpr int NT = S::NT, RQ = S::RQ, RW = S::RW, BS = S::BS;
     extern __shared__ __align__(16) float l3_smem[];
     float* raw = l3_smem;                // [NS][RAW]
     float* box = l3_smem + NS * S::RAW;  // [2][BOX]
     const int t = threadIdx.x;
-    const int c = blockIdx.z % ncomp, zs = blockIdx.z / ncomp;
+    const int c = vb.z % ncomp, zs = vb.z / ncomp;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int z0 = zs * seg, z1 = min(nz, z0 + seg);
-    const int x0 = blockIdx.x * S::TX, y0 = blockIdx.y * TY;
+    const int x0 = vb.x * S::TX, y0 = vb.y * TY;
     const size_t plane_n = (size_t)ny * nx;
     const float* a = in + (size_t)c * p.n;
 
@@ -238,6 +238,20 @@ __global__ void __launch_bounds__(L3Shape<TY, NS>::NT, 2) lap3_fused_kernel(Para
     }
     cpa_wait<0>();  // no copy is left in flight when the block exits
 }
+template <int TY, int NS>
+struct lap3_fused_kernel_op {
+    static constexpr int NT = L3Shape<TY, NS>::NT, MINB = 2;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        lap3_fused_kernel_body<TY, NS>(vb, b...);
+    }
+};
+template <int TY, int NS>
+__global__ void __launch_bounds__(L3Shape<TY, NS>::NT, 2) lap3_fused_kernel(Params p, const float* __restrict__ in,
+                                                                          float* __restrict__ out, float scale,
+                                                                          int ncomp, int seg) {
+    lap3_fused_kernel_body<TY, NS>(vb_hw(), p, in, out, scale, ncomp, seg);
+}
 
 int seg_for(const Params& p, int blocks_xy, int ncomp, int per_sm) {
     // z segments for about `per_sm` blocks per SM; each segment re-reads 14
@@ -268,8 +282,8 @@ cudaError_t run_lap3(const Params& p, const float* in, float* out, int ncomp, fl
     const int bx = (p.nx + S::TX - 1) / S::TX, by = (p.ny + TY - 1) / TY;
     const int seg = seg_for(p, bx * by, ncomp, per_sm > 0 ? per_sm : 2);
     const int nseg = (p.nz + seg - 1) / seg;
-    lap3_fused_kernel<TY, NS><<<dim3(bx, by, ncomp * nseg), S::NT, S::smem, s>>>(p, in, out, scale, ncomp, seg);
-    return cudaGetLastError();
+    return go<lap3_fused_kernel_op<TY, NS>>(lap3_fused_kernel<TY, NS>, dim3(bx, by, ncomp * nseg), S::NT, S::smem, s,
+                                            p, in, out, scale, ncomp, seg);
 }
 
 }  // namespace

@@ -5,6 +5,7 @@
 // the forcing terms as deviations (delta rho = sum g, rho u = sum c g, since
 // sum w = 1 and sum w c = 0) keeps the small velocity-carrying part of each
 // population at full relative precision.
+#include "batch.cuh"
 #include "lbm_common.cuh"
 
 namespace lbm {
@@ -187,9 +188,10 @@ __device__ __forceinline__ void predictor_velocity(const Macro& m, float& vx, fl
 // post-stream velocity u (WN, the input of the WALE gradients, 3 components).
 // Solid rows get zero velocity.
 template <int DIM, typename T, bool WV, bool WN>
-__global__ void __launch_bounds__(256) predict_kernel(Params p, const T* __restrict__ src, float* __restrict__ vps,
-                                                      float* __restrict__ vn, const float* __restrict__ kolmo) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void predict_kernel_body(const VB& vb, const Params& p, const T* __restrict__ src,
+                                                    float* __restrict__ vps, float* __restrict__ vn,
+                                                    const float* __restrict__ kolmo) {
+    const int n = vb.x * blockDim.x + threadIdx.x;
     if (n >= p.n) return;
     const int N = (int)p.n;
     const int x = n % p.nx;
@@ -214,6 +216,19 @@ __global__ void __launch_bounds__(256) predict_kernel(Params p, const T* __restr
         vn[(size_t)N + n] = uy;
         vn[(size_t)2 * N + n] = uz;
     }
+}
+template <int DIM, typename T, bool WV, bool WN>
+struct predict_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        predict_kernel_body<DIM, T, WV, WN>(vb, b...);
+    }
+};
+template <int DIM, typename T, bool WV, bool WN>
+__global__ void __launch_bounds__(256) predict_kernel(Params p, const T* __restrict__ src, float* __restrict__ vps,
+                                                      float* __restrict__ vn, const float* __restrict__ kolmo) {
+    predict_kernel_body<DIM, T, WV, WN>(vb_hw(), p, src, vps, vn, kolmo);
 }
 
 // WALE eddy viscosity from the post-stream velocity field (Sec. 5.2): g_ij =
@@ -438,12 +453,13 @@ __device__ __forceinline__ void sgs_correct(float* g, float r, float ux, float u
 // of the step (Eq. LES-2) before the store: the predictor populations never
 // leave registers.
 template <int DIM, typename T, int SUB, bool CORR>
-__global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
-                                                      const float* __restrict__ vn, const float* __restrict__ kolmo,
-                                                      DevState* st, VPtrs vk, const float* __restrict__ betaf,
-                                                      const float* __restrict__ mprow) {
+__device__ __forceinline__ void collide_kernel_body(const VB& vb, const Params& p, const T* __restrict__ src,
+                                                    T* __restrict__ dst, const float* __restrict__ vn,
+                                                    const float* __restrict__ kolmo, DevState* st, VPtrs vk,
+                                                    const float* __restrict__ betaf,
+                                                    const float* __restrict__ mprow) {
     using LT = Lat<DIM>;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = vb.x * blockDim.x + threadIdx.x;
     if (n >= p.n) return;
     const int N = (int)p.n;
     const int x = n % p.nx;
@@ -458,6 +474,21 @@ __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restr
     collide_node<DIM, SUB, (sizeof(T) == 4), CORR>(p, g, x, y, z, vn, kolmo, st, dx, dy, dz);
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) st_<T>(dst + (size_t)i * N + n, g[i]);
+}
+template <int DIM, typename T, int SUB, bool CORR>
+struct collide_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        collide_kernel_body<DIM, T, SUB, CORR>(vb, b...);
+    }
+};
+template <int DIM, typename T, int SUB, bool CORR>
+__global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
+                                                      const float* __restrict__ vn, const float* __restrict__ kolmo,
+                                                      DevState* st, VPtrs vk, const float* __restrict__ betaf,
+                                                      const float* __restrict__ mprow) {
+    collide_kernel_body<DIM, T, SUB, CORR>(vb_hw(), p, src, dst, vn, kolmo, st, vk, betaf, mprow);
 }
 
 // ---- two nodes per thread (nx even): aligned 2-element population loads ----
@@ -535,13 +566,14 @@ __device__ __forceinline__ void pull2(const Params& p, const T* __restrict__ src
 }
 
 template <int DIM, typename T, int SUB, bool CORR>
-__global__ void __launch_bounds__(128) collide2_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
-                                                       const float* __restrict__ vn, const float* __restrict__ kolmo,
-                                                       DevState* st, VPtrs vk, const float* __restrict__ betaf,
-                                                       const float* __restrict__ mprow) {
+__device__ __forceinline__ void collide2_kernel_body(const VB& vb, const Params& p, const T* __restrict__ src,
+                                                     T* __restrict__ dst, const float* __restrict__ vn,
+                                                     const float* __restrict__ kolmo, DevState* st, VPtrs vk,
+                                                     const float* __restrict__ betaf,
+                                                     const float* __restrict__ mprow) {
     using LT = Lat<DIM>;
     const long long npair = p.n / 2;
-    long long pi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long pi = (long long)vb.x * blockDim.x + threadIdx.x;
     const bool live = pi < npair;
     if (!live) pi = npair - 1;
     const int N = (int)p.n;
@@ -563,6 +595,21 @@ __global__ void __launch_bounds__(128) collide2_kernel(Params p, const T* __rest
     collide_node<DIM, SUB, (sizeof(T) == 4), CORR>(p, g1, x0 + 1, y, z, vn, kolmo, st, dx1, dy1, dz1);
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) Vec2<T>::st(dst + (size_t)i * N + n0, g0[i], g1[i]);
+}
+template <int DIM, typename T, int SUB, bool CORR>
+struct collide2_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        collide2_kernel_body<DIM, T, SUB, CORR>(vb, b...);
+    }
+};
+template <int DIM, typename T, int SUB, bool CORR>
+__global__ void __launch_bounds__(128) collide2_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
+                                                       const float* __restrict__ vn, const float* __restrict__ kolmo,
+                                                       DevState* st, VPtrs vk, const float* __restrict__ betaf,
+                                                       const float* __restrict__ mprow) {
+    collide2_kernel_body<DIM, T, SUB, CORR>(vb_hw(), p, src, dst, vn, kolmo, st, vk, betaf, mprow);
 }
 
 // f = f^eq(rho, u) on fluid nodes, 0 (= rest) on solid rows; inputs are the
@@ -638,11 +685,12 @@ static void do_init(const Params& p, const Layout& L, const float* drho, const f
 // (aligned 2-element loads, x neighbours by warp shuffle), the same moments,
 // 2-element stores.
 template <int DIM, typename T, bool WV, bool WN>
-__global__ void __launch_bounds__(128) predict2_kernel(Params p, const T* __restrict__ src, float* __restrict__ vps,
-                                                       float* __restrict__ vn, const float* __restrict__ kolmo) {
+__device__ __forceinline__ void predict2_kernel_body(const VB& vb, const Params& p, const T* __restrict__ src,
+                                                     float* __restrict__ vps, float* __restrict__ vn,
+                                                     const float* __restrict__ kolmo) {
     using LT = Lat<DIM>;
     const long long npair = p.n / 2;
-    long long pi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long pi = (long long)vb.x * blockDim.x + threadIdx.x;
     const bool live = pi < npair;
     if (!live) pi = npair - 1;
     const size_t N = (size_t)p.n;
@@ -675,6 +723,19 @@ __global__ void __launch_bounds__(128) predict2_kernel(Params p, const T* __rest
         *reinterpret_cast<float2*>(vn + 2 * N + n0) = uz;
     }
 }
+template <int DIM, typename T, bool WV, bool WN>
+struct predict2_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        predict2_kernel_body<DIM, T, WV, WN>(vb, b...);
+    }
+};
+template <int DIM, typename T, bool WV, bool WN>
+__global__ void __launch_bounds__(128) predict2_kernel(Params p, const T* __restrict__ src, float* __restrict__ vps,
+                                                       float* __restrict__ vn, const float* __restrict__ kolmo) {
+    predict2_kernel_body<DIM, T, WV, WN>(vb_hw(), p, src, vps, vn, kolmo);
+}
 
 cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* drho, const float* u, int which,
                             cudaStream_t s) {
@@ -686,9 +747,11 @@ template <int DIM, typename T, bool WV, bool WN>
 static void do_predict_d(const Params& p, const Layout& L, int src, cudaStream_t s) {
     const T* a = (const T*)L.f[src];
     if (p.nx % 2 == 0)
-        predict2_kernel<DIM, T, WV, WN><<<grid_of(p.n / 2, 128), 128, 0, s>>>(p, a, L.vps, L.vn, L.kolmo);
+        go<predict2_kernel_op<DIM, T, WV, WN>>(predict2_kernel<DIM, T, WV, WN>, grid_of(p.n / 2, 128), 128, 0, s, p,
+                                               a, L.vps, L.vn, L.kolmo);
     else
-        predict_kernel<DIM, T, WV, WN><<<grid_of(p.n, 256), 256, 0, s>>>(p, a, L.vps, L.vn, L.kolmo);
+        go<predict_kernel_op<DIM, T, WV, WN>>(predict_kernel<DIM, T, WV, WN>, grid_of(p.n, 256), 256, 0, s, p, a,
+                                              L.vps, L.vn, L.kolmo);
 }
 template <typename T>
 static void do_predict(const Params& p, const Layout& L, int src, cudaStream_t s) {
@@ -723,11 +786,11 @@ static void do_collide_k(const Params& p, const Layout& L, int src, cudaStream_t
         vk.v[k] = p.qoi_kind[k] == LBM_QOI_ENERGY ? L.rr[slot] : L.vz[slot];
     }
     if (p.nx % 2 == 0 && p.tune.collide_pair)  // node pairs: nx even keeps every pair inside one row, 2-aligned
-        collide2_kernel<DIM, T, SUB, CORR><<<grid_of(p.n / 2, 128), 128, 0, s>>>(p, a, b, L.vn, L.kolmo, L.st, vk,
-                                                                                 L.betaf, L.mprow);
+        go<collide2_kernel_op<DIM, T, SUB, CORR>>(collide2_kernel<DIM, T, SUB, CORR>, grid_of(p.n / 2, 128), 128, 0, s,
+                                                  p, a, b, L.vn, L.kolmo, L.st, vk, L.betaf, L.mprow);
     else
-        collide_kernel<DIM, T, SUB, CORR><<<grid_of(p.n, 256), 256, 0, s>>>(p, a, b, L.vn, L.kolmo, L.st, vk, L.betaf,
-                                                                            L.mprow);
+        go<collide_kernel_op<DIM, T, SUB, CORR>>(collide_kernel<DIM, T, SUB, CORR>, grid_of(p.n, 256), 256, 0, s, p,
+                                                 a, b, L.vn, L.kolmo, L.st, vk, L.betaf, L.mprow);
 }
 template <int DIM, typename T, int SUB>
 static void do_collide_s(const Params& p, const Layout& L, int src, cudaStream_t s) {

@@ -5,6 +5,7 @@
 // Fields are FP32 structure-of-arrays [comp][nz][ny][nx].  Every field is
 // zero on solid rows, which is exactly the zero extension the filters and the
 // central differences use beyond the walls (Sec. 4.1).
+#include "batch.cuh"
 #include "lbm_common.cuh"
 #include "rng.cuh"
 #include "dfloat.cuh"
@@ -21,8 +22,8 @@ __device__ __forceinline__ int modp(int a, int n) {
 // omega = curl v* by central differences: 3-D (d_y v_z - d_z v_y, d_z v_x -
 // d_x v_z, d_x v_y - d_y v_x); 2-D the scalar d_x v_y - d_y v_x.  Written
 // after the d velocity components of the stacked field x6.
-__global__ void __launch_bounds__(256) curl_kernel(Params p, float* __restrict__ x6) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void curl_kernel_body(const VB& vb, const Params& p, float* __restrict__ x6) {
+    const int n = vb.x * blockDim.x + threadIdx.x;
     if (n >= p.n) return;
     const int N = (int)p.n, nx = p.nx, ny = p.ny, nz = p.nz;
     const int x = n % nx;
@@ -56,15 +57,26 @@ __global__ void __launch_bounds__(256) curl_kernel(Params p, float* __restrict__
     x6[(size_t)4 * N + n] = dzvx - dxvz;
     x6[(size_t)5 * N + n] = dxvy - dyvx;
 }
+struct curl_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        curl_kernel_body(vb, b...);
+    }
+};
+__global__ void __launch_bounds__(256) curl_kernel(Params p, float* __restrict__ x6) {
+    curl_kernel_body(vb_hw(), p, x6);
+}
 
 // --------------------------------------------------------- filter pass --
 // out(x) = [out(x) +] scale * sum_r t(r) in(x - r e_axis) for every component:
 // one 1-D factor of a separable filter.  Periodic along x and z (and y without
 // walls, any radius); along y with walls, rows outside the array contribute
 // nothing and solid rows hold zero, and the output is zero on solid rows.
-__global__ void __launch_bounds__(256) pass_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
-                                                   int ncomp, int axis, Taps tp, float scale, int accumulate) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void pass_kernel_body(const VB& vb, const Params& p, const float* __restrict__ in,
+                                                 float* __restrict__ out, int ncomp, int axis, const Taps& tp,
+                                                 float scale, int accumulate) {
+    const int n = vb.x * blockDim.x + threadIdx.x;
     if (n >= p.n) return;
     const size_t N = (size_t)p.n;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -99,6 +111,17 @@ __global__ void __launch_bounds__(256) pass_kernel(Params p, const float* __rest
         *o = accumulate ? (*o + scale * s) : scale * s;
     }
 }
+struct pass_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        pass_kernel_body(vb, b...);
+    }
+};
+__global__ void __launch_bounds__(256) pass_kernel(Params p, const float* __restrict__ in, float* __restrict__ out,
+                                                   int ncomp, int axis, Taps tp, float scale, int accumulate) {
+    pass_kernel_body(vb_hw(), p, in, out, ncomp, axis, tp, scale, accumulate);
+}
 
 // ------------------------------------------------------- Fourier bands --
 // out = in * (1/(nx ny) if lo - 1/2 <= |k| < hi + 1/2 else 0) on the R2C half
@@ -125,8 +148,9 @@ __global__ void __launch_bounds__(256) band_mask_kernel(Params p, const float2* 
 
 // ---------------------------------------------- enstrophy sensitivities --
 // V_Z = curl*(W), W = R R omega (App. A): 2-D (d_y W, -d_x W); 3-D curl W.
-__global__ void __launch_bounds__(256) sens_curl_kernel(Params p, const float* __restrict__ w, float* __restrict__ out) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sens_curl_kernel_body(const VB& vb, const Params& p, const float* __restrict__ w,
+                                                      float* __restrict__ out) {
+    const int n = vb.x * blockDim.x + threadIdx.x;
     if (n >= p.n) return;
     const int N = (int)p.n, nx = p.nx, ny = p.ny, nz = p.nz;
     const int x = n % nx;
@@ -155,6 +179,16 @@ __global__ void __launch_bounds__(256) sens_curl_kernel(Params p, const float* _
     out[n] = 0.5f * (wz[iyp] - wz[iym]) - 0.5f * (wy[izp] - wy[izm]);
     out[(size_t)N + n] = 0.5f * (wx[izp] - wx[izm]) - 0.5f * (wz[r0 + xp] - wz[r0 + xm]);
     out[(size_t)2 * N + n] = 0.5f * (wy[r0 + xp] - wy[r0 + xm]) - 0.5f * (wx[iyp] - wx[iym]);
+}
+struct sens_curl_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        sens_curl_kernel_body(vb, b...);
+    }
+};
+__global__ void __launch_bounds__(256) sens_curl_kernel(Params p, const float* __restrict__ w, float* __restrict__ out) {
+    sens_curl_kernel_body(vb_hw(), p, w, out);
 }
 
 // ------------------------------------------- four nodes per thread --
@@ -191,9 +225,10 @@ __device__ __forceinline__ Q4 dq4(const float* __restrict__ c, size_t ip, size_t
 // the periodic central-difference operator).  kVort2: out = d_x a_y - d_y a_x.
 // kSens2: out = (d_y a, -d_x a) of the scalar a.  Wall rows are zero.
 template <int MODE>
-__global__ void __launch_bounds__(256) curl4_kernel(Params p, const float* __restrict__ a, float* __restrict__ out) {
+__device__ __forceinline__ void curl4_kernel_body(const VB& vb, const Params& p, const float* __restrict__ a,
+                                                  float* __restrict__ out) {
     const int nq = p.nx >> 2;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long q = (long long)vb.x * blockDim.x + threadIdx.x;
     if (q >= p.n >> 2) return;
     const int N = (int)p.n, nx = p.nx, ny = p.ny, nz = p.nz;
     const int x = (int)(q % nq) * 4;
@@ -236,6 +271,18 @@ __global__ void __launch_bounds__(256) curl4_kernel(Params p, const float* __res
     o += N;
     st4(o, dxay.v[0] - dyax.v[0], dxay.v[1] - dyax.v[1], dxay.v[2] - dyax.v[2], dxay.v[3] - dyax.v[3]);
 }
+template <int MODE>
+struct curl4_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        curl4_kernel_body<MODE>(vb, b...);
+    }
+};
+template <int MODE>
+__global__ void __launch_bounds__(256) curl4_kernel(Params p, const float* __restrict__ a, float* __restrict__ out) {
+    curl4_kernel_body<MODE>(vb_hw(), p, a, out);
+}
 
 // ------------------------------------------------------ block reduction --
 // Per block (one y row, a chunk of z planes): <v*, V_k> and <V_i, V_j> (i <= j)
@@ -252,13 +299,13 @@ struct RedPtrs {
 };
 
 template <int NS>
-__global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __restrict__ vps, RedPtrs vk,
-                                                     const float2* __restrict__ w_mp2, float* __restrict__ part,
-                                                     float* __restrict__ plane_part) {
+__device__ __forceinline__ void reduce_kernel_body(const VB& vb, const Params& p, const float* __restrict__ vps,
+                                                   RedPtrs vk, const float2* __restrict__ w_mp2,
+                                                   float* __restrict__ part, float* __restrict__ plane_part) {
     constexpr int NG = NS * (NS + 1) / 2;
     constexpr int NV = NS + NG + 1 + NS;  // <v,V_k>, Gram, row sums (v_x, V_k,x)
-    const int y = blockIdx.x;
-    const int zc = blockIdx.y;
+    const int y = vb.x;
+    const int zc = vb.y;
     const int zper = (p.nz + p.nzc - 1) / p.nzc;
     const int z0 = zc * zper;
     const int z1 = min(p.nz, z0 + zper);
@@ -337,7 +384,7 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
         if (lane == 0) sh[wid][v] = a;
     }
     __syncthreads();
-    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    const int blk = vb.y * vb.gx + vb.x;
     const size_t row = (size_t)blk * p.npart_all;
     for (int v = threadIdx.x; v < NV; v += blockDim.x) {
         const float s = (sh[0][v] + sh[1][v]) + (sh[2][v] + sh[3][v]);
@@ -360,6 +407,20 @@ __global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __re
         part[row + NS + NG + 2 * t] = hi;
         part[row + NS + NG + 2 * t + 1] = lo;
     }
+}
+template <int NS>
+struct reduce_kernel_op {
+    static constexpr int NT = 128, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        reduce_kernel_body<NS>(vb, b...);
+    }
+};
+template <int NS>
+__global__ void __launch_bounds__(128) reduce_kernel(Params p, const float* __restrict__ vps, RedPtrs vk,
+                                                     const float2* __restrict__ w_mp2, float* __restrict__ part,
+                                                     float* __restrict__ plane_part) {
+    reduce_kernel_body<NS>(vb_hw(), p, vps, vk, w_mp2, part, plane_part);
 }
 
 // ------------------------------------------------------------ totals --
@@ -384,9 +445,9 @@ __device__ __forceinline__ DF df_block_sum(DF a, DF* sh) {
     return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(256) totals_kernel(Params p, Layout L, int nplane_blk) {
+__device__ __forceinline__ void totals_kernel_body(const VB& vb, const Params& p, const Layout& L, int nplane_blk) {
     __shared__ DF sh[8];
-    const int b = blockIdx.x;
+    const int b = vb.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (b < p.npart) {
         DF a = {0.f, 0.f};
@@ -447,6 +508,16 @@ __global__ void __launch_bounds__(256) totals_kernel(Params p, Layout L, int npl
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     if (lane == 0) L.hsum[k] = a;
 }
+struct totals_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        totals_kernel_body(vb, b...);
+    }
+};
+__global__ void __launch_bounds__(256) totals_kernel(Params p, Layout L, int nplane_blk) {
+    totals_kernel_body(vb_hw(), p, L, nplane_blk);
+}
 
 // ------------------------------------------- LRS history matvec, normals --
 // Runs on a side branch of the step (it needs only the previous step's
@@ -459,17 +530,17 @@ __global__ void __launch_bounds__(256) totals_kernel(Params p, Layout L, int npl
 // then thread (j, k) accumulates rows j, j + per, ... of column k, so a warp
 // reads consecutive elements of C.  The last block draws the step's normals
 // (the LRS noise or the gamma draws).
-__global__ void __launch_bounds__(256) lrs_pre_kernel(Params p, Layout L, int nb) {
+__device__ __forceinline__ void lrs_pre_kernel_body(const VB& vb, const Params& p, const Layout& L, int nb) {
     const int nq = p.n_q;
     const long long step = L.st->step;
-    if (blockIdx.x == (unsigned)nb) {
+    if (vb.x == (unsigned)nb) {
         const int stream = p.to_mode == LBM_TO_GAMMA ? kStreamGamma : kStreamLrs;
         if (threadIdx.x < (unsigned)nq) L.znorm[threadIdx.x] = philox_normal(p.seed, p.member, step, stream, threadIdx.x);
         return;
     }
     const int h = p.h;
     const int rows = (2 * h + 1) * nq + 1;
-    const int r0 = blockIdx.x * p.lrs_rows_per_blk;
+    const int r0 = vb.x * p.lrs_rows_per_blk;
     const int r1 = min(rows, r0 + p.lrs_rows_per_blk);
     const int posm = (int)(L.st->hist_pos % h);
     __shared__ double xs[kLrsRowsPerBlk];
@@ -501,8 +572,18 @@ __global__ void __launch_bounds__(256) lrs_pre_kernel(Params p, Layout L, int nb
     if (threadIdx.x < (unsigned)nq) {
         double s = 0.0;
         for (int jj = 0; jj < per; ++jj) s += sh[jj * nq + threadIdx.x];
-        L.lrs_part[(size_t)blockIdx.x * nq + threadIdx.x] = s;
+        L.lrs_part[(size_t)vb.x * nq + threadIdx.x] = s;
     }
+}
+struct lrs_pre_kernel_op {
+    static constexpr int NT = 256, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        lrs_pre_kernel_body(vb, b...);
+    }
+};
+__global__ void __launch_bounds__(256) lrs_pre_kernel(Params p, Layout L, int nb) {
+    lrs_pre_kernel_body(vb_hw(), p, L, nb);
 }
 
 // ------------------------------------------------------------- solve --
@@ -578,7 +659,7 @@ __device__ __forceinline__ int half_exp(double gii) {
 
 constexpr int kSolveThreads = 320;  // >= 16 x 17 + 15 active elements, plus a spare warp
 
-__global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L) {
+__device__ __forceinline__ void solve_kernel_body(const VB& vb, const Params& p, const Layout& L) {
     constexpr int MQ = kMaxQoi;
     constexpr int MW = 2 * MQ + 1;
     const int ns = p.n_s, nmp = p.n_mp, nq = p.n_q;
@@ -797,6 +878,16 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L
         L.st->step = step + 1;
     }
 }
+struct solve_kernel_op {
+    static constexpr int NT = kSolveThreads, MINB = 1;
+    template <class... B>
+    static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
+        solve_kernel_body(vb, b...);
+    }
+};
+__global__ void __launch_bounds__(kSolveThreads) solve_kernel(Params p, Layout L) {
+    solve_kernel_body(vb_hw(), p, L);
+}
 
 // ------------------------------------------------- QoIs of a given field --
 // The QoI path on a velocity field supplied by the caller (a projected HF
@@ -829,23 +920,27 @@ cudaError_t launch_to_curl(const Params& p, const Layout& L, cudaStream_t s) {
     float* om = L.x6 + (size_t)p.dim * p.n;
     if (quads_ok(p, L.x6, om)) {
         if (p.dim == 3)
-            curl4_kernel<kCurl3><<<gridn(p.n / 4, 256), 256, 0, s>>>(p, L.x6, om);
+            go<curl4_kernel_op<kCurl3>>(curl4_kernel<kCurl3>, gridn(p.n / 4, 256), 256, 0, s, p, L.x6, om);
         else
-            curl4_kernel<kVort2><<<gridn(p.n / 4, 256), 256, 0, s>>>(p, L.x6, om);
+            go<curl4_kernel_op<kVort2>>(curl4_kernel<kVort2>, gridn(p.n / 4, 256), 256, 0, s, p, L.x6, om);
         return cudaGetLastError();
     }
-    curl_kernel<<<gridn(p.n, 256), 256, 0, s>>>(p, L.x6);
+    go<curl_kernel_op>(curl_kernel, gridn(p.n, 256), 256, 0, s, p, L.x6);
     return cudaGetLastError();
 }
 cudaError_t launch_pass(const Params& p, const float* in, float* out, int ncomp, int axis, const Taps& t, float scale,
                         int accumulate, cudaStream_t s) {
     const cudaError_t e = launch_pass_fast(p, in, out, ncomp, axis, t, scale, accumulate, s);
     if (e != cudaErrorNotSupported) return e;
-    pass_kernel<<<gridn(p.n, 256), 256, 0, s>>>(p, in, out, ncomp, axis, t, scale, accumulate);
+    go<pass_kernel_op>(pass_kernel, gridn(p.n, 256), 256, 0, s, p, in, out, ncomp, axis, t, scale, accumulate);
     return cudaGetLastError();
 }
 cudaError_t launch_band_mask(const Params& p, const float2* in, float2* out, int ncomp, int lo, int hi,
                              cudaStream_t s) {
+    if (g_rec) {  // the transforms around it are library calls: not batched
+        rec_refuse("Fourier band mask");
+        return cudaSuccess;
+    }
     const long long n = (long long)p.ny * (p.nx / 2 + 1) * ncomp;
     band_mask_kernel<<<gridn(n, 256), 256, 0, s>>>(p, in, out, ncomp, lo, hi);
     return cudaGetLastError();
@@ -853,44 +948,48 @@ cudaError_t launch_band_mask(const Params& p, const float2* in, float2* out, int
 cudaError_t launch_sens_curl(const Params& p, const float* w, float* out, cudaStream_t s) {
     if (quads_ok(p, w, out)) {
         if (p.dim == 3)
-            curl4_kernel<kCurl3><<<gridn(p.n / 4, 256), 256, 0, s>>>(p, w, out);
+            go<curl4_kernel_op<kCurl3>>(curl4_kernel<kCurl3>, gridn(p.n / 4, 256), 256, 0, s, p, w, out);
         else
-            curl4_kernel<kSens2><<<gridn(p.n / 4, 256), 256, 0, s>>>(p, w, out);
+            go<curl4_kernel_op<kSens2>>(curl4_kernel<kSens2>, gridn(p.n / 4, 256), 256, 0, s, p, w, out);
         return cudaGetLastError();
     }
-    sens_curl_kernel<<<gridn(p.n, 256), 256, 0, s>>>(p, w, out);
+    go<sens_curl_kernel_op>(sens_curl_kernel, gridn(p.n, 256), 256, 0, s, p, w, out);
     return cudaGetLastError();
+}
+template <int NS>
+static void go_reduce(const Params& p, const Layout& L, const RedPtrs& r, dim3 grid, cudaStream_t s) {
+    go<reduce_kernel_op<NS>>(reduce_kernel<NS>, grid, 128, 0, s, p, L.vps, r, L.w_mp2, L.part, L.plane_part);
 }
 cudaError_t launch_reduce(const Params& p, const Layout& L, const float* const* vk, cudaStream_t s) {
     RedPtrs r;
     for (int k = 0; k < kMaxQoi; ++k) r.v[k] = k < p.n_s ? vk[k] : nullptr;
     dim3 grid(p.ny, p.nzc);
     switch (p.n_s) {
-        case 1: reduce_kernel<1><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
-        case 2: reduce_kernel<2><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
-        case 3: reduce_kernel<3><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
-        case 4: reduce_kernel<4><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
-        case 5: reduce_kernel<5><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
-        case 6: reduce_kernel<6><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
-        case 7: reduce_kernel<7><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
-        case 8: reduce_kernel<8><<<grid, 128, 0, s>>>(p, L.vps, r, L.w_mp2, L.part, L.plane_part); break;
+        case 1: go_reduce<1>(p, L, r, grid, s); break;
+        case 2: go_reduce<2>(p, L, r, grid, s); break;
+        case 3: go_reduce<3>(p, L, r, grid, s); break;
+        case 4: go_reduce<4>(p, L, r, grid, s); break;
+        case 5: go_reduce<5>(p, L, r, grid, s); break;
+        case 6: go_reduce<6>(p, L, r, grid, s); break;
+        case 7: go_reduce<7>(p, L, r, grid, s); break;
+        case 8: go_reduce<8>(p, L, r, grid, s); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 cudaError_t launch_lrs_pre(const Params& p, const Layout& L, cudaStream_t s) {
     const int nb = p.to_mode == LBM_TO_LRS ? p.nblk_lrs : 0;
-    lrs_pre_kernel<<<nb + 1, 256, 0, s>>>(p, L, nb);
+    go<lrs_pre_kernel_op>(lrs_pre_kernel, nb + 1, 256, 0, s, p, L, nb);
     return cudaGetLastError();
 }
 cudaError_t launch_totals(const Params& p, const Layout& L, bool with_lrs, cudaStream_t s) {
     const int nplane_blk = (p.ny * (1 + p.n_s) + 7) / 8;
     const int nb = p.ntot + nplane_blk + (with_lrs && p.to_mode == LBM_TO_LRS ? p.n_q : 0);
-    totals_kernel<<<nb, 256, 0, s>>>(p, L, nplane_blk);
+    go<totals_kernel_op>(totals_kernel, nb, 256, 0, s, p, L, nplane_blk);
     return cudaGetLastError();
 }
 cudaError_t launch_solve(const Params& p, const Layout& L, cudaStream_t s) {
-    solve_kernel<<<1, kSolveThreads, 0, s>>>(p, L);
+    go<solve_kernel_op>(solve_kernel, 1, kSolveThreads, 0, s, p, L);
     return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 
 #include <cufft.h>
 
+#include "batch.cuh"
 #include "lbm_common.cuh"
 
 using namespace lbm;
@@ -431,7 +432,8 @@ struct Launcher {
 // a library call (cuFFT): timed like a kernel, not counted as one of ours
 #define LIBCALL(lc, cls, expr)                                       \
     do {                                                             \
-        if (!(lc).count_only) {                                      \
+        if (g_rec) rec_refuse("library call in the step");          \
+        else if (!(lc).count_only) {                                 \
             const int n_ = (int)(lc).n;                              \
             (lc).before(cls);                                        \
             (lc).n = n_;                                             \
@@ -639,6 +641,7 @@ static int build_graph(lbm_ctx* c) {
     }
     return LBM_OK;
 }
+
 
 static int eager_step(lbm_ctx* c) {
     Launcher lc{c, c->stream, false, 0};
@@ -1165,6 +1168,46 @@ int lbm_set_track_reference(lbm_ctx* c, const double* qref, int64_t len) {
     CK(c, cudaMemcpyAsync(c->L.track, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->stream));
     return sync_check(c);
 }
+
+}  // extern "C"
+
+namespace lbm {
+// Batched execution (lbm_batch.cu): the checks and the tuning lbm_step does
+// before a context's first step, then the launch programs of one step from
+// each population buffer.  A program whose launches cannot all be batched
+// comes back with ok == false (the member then steps on its own).
+int record_step_programs(lbm_ctx* c, Recorder prog[2]) {
+    if (!c) return fail(c, LBM_ERR_ARG, "NULL context");
+    if (c->p.to_mode == LBM_TO_LRS && !c->lrs_set) return fail(c, LBM_ERR_STATE, "call lbm_set_lrs or lbm_set_to_coeffs first");
+    if (c->p.to_mode == LBM_TO_FIXED_GAMMA && !c->fixed_set)
+        return fail(c, LBM_ERR_STATE, "call lbm_set_to_coeffs with gamma_fixed first");
+    if (c->autotune && !c->tuned) {
+        const int rc = autotune(c);
+        if (rc) return rc;
+    }
+    for (int par = 0; par < 2; ++par) {
+        prog[par] = Recorder();
+        if (c->profiling || c->branch) {
+            prog[par].ok = false;
+            prog[par].why = c->profiling ? "profiling" : "branched step";
+            continue;
+        }
+        Launcher lc{c, c->stream, false, 0};
+        lc.timed = false;
+        g_rec = &prog[par];
+        enqueue_step(lc, par);
+        g_rec = nullptr;
+        if (lc.err != cudaSuccess) return fail(c, LBM_ERR_CUDA, "recording a step: %s", cudaGetErrorString(lc.err));
+    }
+    return LBM_OK;
+}
+int step_parity(const lbm_ctx* c) { return c->cur; }
+void steps_taken(lbm_ctx* c, int64_t n) {
+    if (n & 1) c->cur = 1 - c->cur;
+}
+}  // namespace lbm
+
+extern "C" {
 
 int lbm_step(lbm_ctx* c, int64_t nsteps) {
     if (!c) return fail(c, LBM_ERR_ARG, "NULL context");

@@ -1,13 +1,36 @@
 // Ensemble batches on one GPU (include/lbm.h, lbm_batch_*): admission by
-// pool budget, per-member streams and graphs, non-blocking completion polling.
-// Built only on the public C ABI of the single-member library.
+// pool budget, non-blocking completion polling, and two ways to advance the
+// members:
+//
+//   persistent (default)  a member's step is recorded once as a program of
+//                         launches (batch.cuh); members whose programs run
+//                         the same operations form a class, and each launch
+//                         position of a class runs as ONE batched kernel over
+//                         every active member of the class: a persistent grid
+//                         drawing (member, block) items from a global queue,
+//                         over a member table in device memory (recorded
+//                         arguments, prefix sums of the members' grids); a
+//                         round of steps of a class is captured in one CUDA
+//                         graph on the class's stream
+//   per member            each member replays its own two-step CUDA graph on
+//                         its own stream (also the fallback for a member whose
+//                         step has a launch that cannot be batched: a library
+//                         call such as cuFFT)
+//
+// A member's results are bit-identical either way (the batched kernel runs the
+// same body on the same block index and grid as the plain launch).
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <vector>
 
+#include "batch.cuh"
 #include "lbm_common.cuh"
+
+namespace lbm {
+thread_local Recorder* g_rec = nullptr;
+}  // namespace lbm
 
 namespace {
 
@@ -19,6 +42,13 @@ constexpr int kRounds = 4;  // lbm_batch_run calls whose end each member remembe
 
 struct Member {
     bool used = false;
+    int prog = 0;   // 0: step programs not recorded yet, 1: batched, -1: steps on its own
+    int64_t nodes = 0;
+    int cls = -1;   // its class (batched)
+    std::vector<lbm::RecOp> ops[2];      // step programs from population buffer 0 and 1 (arguments uploaded)
+    std::vector<const void*> dargs[2];   // device address of each launch's arguments
+    unsigned char* dblob = nullptr;      // device copy of the argument blocks
+    cudaEvent_t ev_in = nullptr;         // the member's own stream's work, before a batched round
     lbm_ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -42,16 +72,37 @@ int berr(int code, const char* fmt, ...) {
 
 }  // namespace
 
+// a class of batched members: the same operations at every launch position
+struct TableSlot {
+    lbm::BEntry* dev = nullptr;   // member tables of one round (device)
+    lbm::BEntry* host = nullptr;  // staging (pinned)
+    size_t cap = 0;
+    cudaEvent_t used = nullptr;   // after the round's last launch
+};
+struct Class {
+    std::vector<lbm::BatchLaunchFn> sig;
+    int lane = 0;                       // classes of one signature split members over lanes
+    cudaStream_t s = nullptr;
+    unsigned long long* ctr = nullptr;  // [positions][2] work queues (device, self-resetting)
+    TableSlot slot[kRounds];
+    cudaGraphExec_t gexec = nullptr;    // the last round's graph
+};
+
 struct lbm_batch {
     char* pool;
     size_t pool_bytes;
     std::vector<Block> free_list;  // sorted by offset, coalesced
     std::vector<Member> m;
+    std::vector<Class> cls;
     cudaEvent_t epoch;
     int64_t round = 0;  // lbm_batch_run calls so far
+    int persistent = 1; // 0: per-member graphs; n > 0: persistent, n lanes per signature
+    int64_t max_nodes = 16384;  // persistent for members up to this many nodes
+    int n_sm = 0;
 };
 
 static void destroy_member_events(Member& mm) {
+    if (mm.ev_in) cudaEventDestroy(mm.ev_in);
     if (mm.done) cudaEventDestroy(mm.done);
     for (int k = 0; k < kRounds; ++k)
         if (mm.rev[k]) cudaEventDestroy(mm.rev[k]);
@@ -100,6 +151,9 @@ int lbm_batch_create(int32_t n_slots, void* dev_pool, size_t pool_bytes, lbm_bat
     b->pool_bytes = pool_bytes;
     b->free_list.push_back(Block{0, pool_bytes & ~(size_t)255});
     b->m.resize(n_slots);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaEventCreate(&b->epoch);
     if (e == cudaSuccess) e = cudaEventRecord(b->epoch, 0);
     if (e != cudaSuccess) {
@@ -114,7 +168,8 @@ int lbm_batch_release(lbm_batch* b, int32_t slot) {
     if (!b || slot < 0 || slot >= (int32_t)b->m.size() || !b->m[slot].used)
         return berr(LBM_ERR_ARG, "lbm_batch_release: bad slot");
     Member& mm = b->m[slot];
-    if (mm.stream) cudaStreamSynchronize(mm.stream);
+    if (mm.stream) cudaStreamSynchronize(mm.stream);  // its batched rounds too (the stream waited on them)
+    if (mm.dblob) cudaFreeAsync(mm.dblob, mm.stream);
     lbm_destroy(mm.ctx);
     destroy_member_events(mm);
     if (mm.stream) cudaStreamDestroy(mm.stream);
@@ -127,6 +182,18 @@ int lbm_batch_destroy(lbm_batch* b) {
     if (!b) return LBM_OK;
     for (int32_t i = 0; i < (int32_t)b->m.size(); ++i)
         if (b->m[i].used) lbm_batch_release(b, i);
+    for (Class& c : b->cls) {
+        cudaStreamSynchronize(c.s);
+        if (c.gexec) cudaGraphExecDestroy(c.gexec);
+        for (TableSlot& t : c.slot) {
+            if (t.dev) cudaFreeAsync(t.dev, c.s);
+            if (t.host) cudaFreeHost(t.host);
+            if (t.used) cudaEventDestroy(t.used);
+        }
+        if (c.ctr) cudaFreeAsync(c.ctr, c.s);
+        cudaStreamSynchronize(c.s);
+        cudaStreamDestroy(c.s);
+    }
     cudaEventDestroy(b->epoch);
     delete b;
     return LBM_OK;
@@ -150,6 +217,7 @@ int lbm_batch_admit(lbm_batch* b, const lbm_config* cfg, const double* u0, int64
     Member& mm = b->m[s];
     cudaError_t e = cudaStreamCreateWithFlags(&mm.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&mm.done, cudaEventDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&mm.ev_in, cudaEventDisableTiming);
     for (int k = 0; k < kRounds && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&mm.rev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         destroy_member_events(mm);
@@ -174,6 +242,7 @@ int lbm_batch_admit(lbm_batch* b, const lbm_config* cfg, const double* u0, int64
         return rc;
     }
     mm.used = true;
+    mm.nodes = (int64_t)cfg->nx * cfg->ny * cfg->nz;
     mm.off = off;
     mm.size = need;
     mm.horizon = horizon;
@@ -190,15 +259,225 @@ int lbm_batch_member(lbm_batch* b, int32_t slot, lbm_ctx** ctx) {
     return LBM_OK;
 }
 
+// Record a member's step programs and upload their arguments; classify it.
+static int prepare_member(lbm_batch* b, Member& mm) {
+    lbm::Recorder prog[2];
+    int rc = lbm::record_step_programs(mm.ctx, prog);
+    if (rc) return rc;
+    bool ok = prog[0].ok && prog[1].ok && prog[0].ops.size() == prog[1].ops.size() && !prog[0].ops.empty();
+    for (size_t i = 0; ok && i < prog[0].ops.size(); ++i) ok = prog[0].ops[i].launch == prog[1].ops[i].launch;
+    if (!ok) {
+        mm.prog = -1;
+        return LBM_OK;
+    }
+    // argument blocks of both programs in one device blob (16-byte aligned)
+    std::vector<unsigned char> blob;
+    std::vector<size_t> off[2];
+    for (int par = 0; par < 2; ++par)
+        for (const lbm::RecOp& r : prog[par].ops) {
+            off[par].push_back(blob.size());
+            blob.insert(blob.end(), r.args.begin(), r.args.end());
+            blob.resize((blob.size() + 15) & ~(size_t)15);
+        }
+    // stream-ordered: no device-wide synchronisation while other rounds run
+    // (the class stream waits on the member's stream before its first round)
+    cudaError_t e = cudaMallocAsync((void**)&mm.dblob, blob.size(), mm.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mm.dblob, blob.data(), blob.size(), cudaMemcpyHostToDevice, mm.stream);
+    if (e != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: member arguments: %s", cudaGetErrorString(e));
+    for (int par = 0; par < 2; ++par) {
+        mm.dargs[par].clear();
+        for (size_t i = 0; i < prog[par].ops.size(); ++i) {
+            mm.dargs[par].push_back(mm.dblob + off[par][i]);
+            prog[par].ops[i].args.clear();
+            prog[par].ops[i].args.shrink_to_fit();
+        }
+        mm.ops[par] = std::move(prog[par].ops);
+    }
+    // its class: the same operation at every position
+    std::vector<lbm::BatchLaunchFn> sig;
+    for (const lbm::RecOp& r : mm.ops[0]) sig.push_back(r.launch);
+    // the lane of this signature with the fewest active members: lanes run
+    // on their own streams, so one lane's small launches (totals, solve)
+    // overlap another lane's field kernels
+    std::vector<int> count(b->persistent, 0);
+    for (const Member& o : b->m)
+        if (o.used && o.prog == 1 && b->cls[o.cls].sig == sig) ++count[b->cls[o.cls].lane];
+    int lane = 0;
+    for (int l = 1; l < b->persistent; ++l)
+        if (count[l] < count[lane]) lane = l;
+    int ci = -1;
+    for (size_t k = 0; k < b->cls.size(); ++k)
+        if (b->cls[k].sig == sig && b->cls[k].lane == lane) ci = (int)k;
+    if (ci < 0) {
+        Class c;
+        c.sig = sig;
+        c.lane = lane;
+        e = cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMalloc(&c.ctr, sizeof(unsigned long long) * 2 * sig.size());
+        if (e == cudaSuccess) e = cudaMemset(c.ctr, 0, sizeof(unsigned long long) * 2 * sig.size());
+        for (int k = 0; k < kRounds && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&c.slot[k].used, cudaEventDisableTiming);
+        if (e != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: new class: %s", cudaGetErrorString(e));
+        b->cls.push_back(c);
+        ci = (int)b->cls.size() - 1;
+    }
+    mm.cls = ci;
+    mm.prog = 1;
+    return LBM_OK;
+}
+
+// Queue one round of a class: steps 0 .. S-1, member m active while j < n_m;
+// launch position i of step j is one batched kernel over the active members.
+static int run_class(lbm_batch* b, int ci, int64_t steps, int k) {
+    Class& c = b->cls[ci];
+    std::vector<int> mem;
+    std::vector<int64_t> nm;
+    for (int i = 0; i < (int)b->m.size(); ++i) {
+        Member& mm = b->m[i];
+        if (!mm.used || mm.prog != 1 || mm.cls != ci || mm.queued >= mm.horizon) continue;
+        mem.push_back(i);
+        nm.push_back(steps < mm.horizon - mm.queued ? steps : mm.horizon - mm.queued);
+    }
+    if (mem.empty()) return LBM_OK;
+    int64_t S = 0;
+    for (int64_t v : nm) S = v > S ? v : S;
+    const size_t P = c.sig.size();
+    // member tables: for every step and position, the active members' argument
+    // blocks and the prefix sums of their grids
+    size_t need = 0;
+    for (int64_t j = 0; j < S; ++j)
+        for (size_t q = 0; q < mem.size(); ++q) need += nm[q] > j ? P : 0;
+    TableSlot& ts = c.slot[k];
+    cudaError_t e = cudaEventSynchronize(ts.used);  // its previous round has run
+    if (e == cudaSuccess && ts.cap < need) {
+        if (ts.dev) cudaFreeAsync(ts.dev, c.s);
+        if (ts.host) cudaFreeHost(ts.host);
+        ts.dev = nullptr;
+        ts.host = nullptr;
+        ts.cap = need + need / 2 + 64;
+        e = cudaMallocAsync((void**)&ts.dev, sizeof(lbm::BEntry) * ts.cap, c.s);
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&ts.host, sizeof(lbm::BEntry) * ts.cap);
+    }
+    if (e != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: tables: %s", cudaGetErrorString(e));
+    struct L {
+        size_t off;
+        int n;
+        long long total;
+        size_t smem;
+    };
+    std::vector<L> launches;
+    launches.reserve((size_t)S * P);
+    size_t at = 0;
+    for (int64_t j = 0; j < S; ++j)
+        for (size_t i = 0; i < P; ++i) {
+            L l{at, 0, 0, 0};
+            for (size_t q = 0; q < mem.size(); ++q) {
+                if (nm[q] <= j) continue;
+                Member& mm = b->m[mem[q]];
+                const int par = (lbm::step_parity(mm.ctx) + (int)(j & 1)) & 1;
+                const lbm::RecOp& r = mm.ops[par][i];
+                ts.host[at].args = mm.dargs[par][i];
+                ts.host[at].start = l.total;
+                ++at;
+                ++l.n;
+                l.total += r.blocks;
+                if (r.smem > l.smem) l.smem = r.smem;
+            }
+            launches.push_back(l);
+        }
+    // the members' own streams (initial fields, coefficients) come first
+    for (int i : mem) {
+        Member& mm = b->m[i];
+        e = cudaEventRecord(mm.ev_in, mm.stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s, mm.ev_in, 0);
+        if (e != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: %s", cudaGetErrorString(e));
+    }
+    // the round as one graph: table upload, S x P batched kernels, the
+    // members' completion events
+    e = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ts.dev, ts.host, sizeof(lbm::BEntry) * at, cudaMemcpyHostToDevice, c.s);
+    for (int64_t j = 0; j < S && e == cudaSuccess; ++j) {
+        for (size_t i = 0; i < P && e == cudaSuccess; ++i) {
+            const L& l = launches[(size_t)j * P + i];
+            if (l.n == 0 || l.total == 0) continue;
+            const lbm::RecOp& r0 = b->m[mem[0]].ops[0][i];
+            int bpsm = r0.smem == l.smem ? r0.blocks_per_sm : r0.prep(l.smem);
+            if (bpsm < 1) bpsm = 1;
+            const long long cap = (long long)bpsm * b->n_sm;
+            const int grid = (int)(l.total < cap ? l.total : cap);
+            e = c.sig[i](ts.dev + l.off, l.n, l.total, c.ctr + 2 * i, grid, l.smem, c.s);
+        }
+        for (size_t q = 0; q < mem.size() && e == cudaSuccess; ++q) {
+            Member& mm = b->m[mem[q]];
+            if (nm[q] == j + 1 && mm.queued + nm[q] >= mm.horizon && !mm.done_recorded)
+                e = cudaEventRecordWithFlags(mm.done, c.s, cudaEventRecordExternal);
+        }
+    }
+    for (int i : mem)
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->m[i].rev[k], c.s, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ts.used, c.s, cudaEventRecordExternal);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c.s, &g);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) {
+        // reuse the last round's executable graph when the shape allows
+        cudaGraphExecUpdateResultInfo info;
+        if (!c.gexec || cudaGraphExecUpdate(c.gexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            if (c.gexec) cudaGraphExecDestroy(c.gexec);
+            c.gexec = nullptr;
+            e = cudaGraphInstantiate(&c.gexec, g, 0);
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) e = cudaGraphLaunch(c.gexec, c.s);
+    if (e != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: batched round: %s", cudaGetErrorString(e));
+    for (size_t q = 0; q < mem.size(); ++q) {
+        Member& mm = b->m[mem[q]];
+        // later work on the member's own stream (reads, release) follows the round
+        e = cudaStreamWaitEvent(mm.stream, mm.rev[k], 0);
+        if (e != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: %s", cudaGetErrorString(e));
+        mm.rround[k] = b->round;
+        mm.queued += nm[q];
+        lbm::steps_taken(mm.ctx, nm[q]);
+        if (mm.queued >= mm.horizon) mm.done_recorded = true;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_set_persistent(lbm_batch* b, int lanes, int64_t max_nodes) {
+    if (!b || lanes < 0 || lanes > 64 || max_nodes < 0)
+        return berr(LBM_ERR_ARG, "lbm_batch_set_persistent: lanes must be 0..64, max_nodes >= 0");
+    for (const Member& mm : b->m)
+        if (mm.used && mm.prog != 0)
+            return berr(LBM_ERR_STATE, "lbm_batch_set_persistent must precede the first lbm_batch_run of its members");
+    b->persistent = lanes;
+    b->max_nodes = max_nodes;
+    return LBM_OK;
+}
+
 int lbm_batch_run(lbm_batch* b, int64_t steps) {
     if (!b || steps < 0) return berr(LBM_ERR_ARG, "lbm_batch_run: bad argument");
+    const int k = (int)(b->round % kRounds);
     for (Member& mm : b->m) {
-        if (!mm.used || mm.queued >= mm.horizon) continue;
+        if (!mm.used || mm.prog != 0) continue;
+        if (b->persistent && mm.nodes <= b->max_nodes) {
+            const int rc = prepare_member(b, mm);
+            if (rc) return rc;
+        } else {
+            mm.prog = -1;
+        }
+    }
+    for (int ci = 0; ci < (int)b->cls.size(); ++ci) {
+        const int rc = run_class(b, ci, steps, k);
+        if (rc) return rc;
+    }
+    for (Member& mm : b->m) {
+        if (!mm.used || mm.prog != -1 || mm.queued >= mm.horizon) continue;
         const int64_t n = steps < mm.horizon - mm.queued ? steps : mm.horizon - mm.queued;
         const int rc = lbm_step(mm.ctx, n);
         if (rc) return rc;
         mm.queued += n;
-        const int k = (int)(b->round % kRounds);
         const cudaError_t er = cudaEventRecord(mm.rev[k], mm.stream);
         if (er != cudaSuccess) return berr(LBM_ERR_CUDA, "lbm_batch_run: %s", cudaGetErrorString(er));
         mm.rround[k] = b->round;

@@ -27,6 +27,11 @@ __device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// one arrival without transactions (completes the phase of a count-1 barrier)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to shared
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -50,7 +55,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase with the given parity to complete; false if it did not
-// within kWaitTries attempts.
+// within kWaitTries attempts.  Lanes that issue copies must all have issued
+// them (__syncwarp) before any lane of their warp waits: a diverged warp does
+// not interleave its two paths fairly, and waiting lanes can use up their
+// attempts before the issuing lanes run.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (long long i = 0; i < kWaitTries; ++i)
         if (mbar_try_wait(bar, parity)) return true;
@@ -60,7 +68,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // After a wait gave up: flag it, then wait once more (bounded) so that the
 // block does not leave while its copies may still be landing.
 __device__ __forceinline__ void mbar_give_up(uint64_t* bar, uint32_t parity, DevState* st) {
-    if (threadIdx.x == 0) atomicOr(&st->status, kStatusTimeout);
+    atomicOr(&st->status, kStatusTimeout);  // every thread that gave up: none goes unreported
     mbar_wait(bar, parity);
 }
 

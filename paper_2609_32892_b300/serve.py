@@ -52,13 +52,18 @@ def set_coefficients(ctx, req):
 
 
 class EnsembleServer:
-    def __init__(self, pool_bytes, n_slots, device="cuda"):
+    """persistent: lanes of persistent batched kernels per class for members
+    of at most max_nodes nodes (lbm_batch_set_persistent; the library
+    defaults: 1 lane, 16384 nodes); 0: per-member graphs for every member."""
+
+    def __init__(self, pool_bytes, n_slots, device="cuda", persistent=1, max_nodes=16384):
         import torch
 
         self.torch = torch
         self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=device)
         torch.cuda.synchronize(self.pool.device)
         self.batch = B.lbm_batch_create(n_slots, self.pool.data_ptr(), int(pool_bytes))
+        B.lbm_batch_set_persistent(self.batch, int(persistent), max_nodes)
         torch.cuda.synchronize(self.pool.device)
         self.t_epoch = time.perf_counter()  # device time 0 of t_done_ms
 

@@ -35,7 +35,8 @@ def _alone(wl, member):
     return rows, f
 
 
-def test_member_results_identical_alone_and_in_mix():
+@pytest.mark.parametrize("persistent", [True, False])
+def test_member_results_identical_alone_and_in_mix(persistent):
     import torch
 
     from paper_2609_32892_b300 import binding as B
@@ -45,6 +46,7 @@ def test_member_results_identical_alone_and_in_mix():
     pool_bytes = sum(B.lbm_required_bytes(B.config_from_workload(w)) for w in wls) + (1 << 20)
     pool = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
     b = B.lbm_batch_create(4, pool.data_ptr(), pool_bytes)
+    B.lbm_batch_set_persistent(b, 1 if persistent else 0, max_nodes=1 << 40)
     slots = []
     for i, w in enumerate(wls):
         s = B.lbm_batch_admit(b, B.config_from_workload(w, member=i), synthetic.initial_velocity(w), w["steps"], i)
@@ -202,3 +204,85 @@ def test_server_members_carry_their_own_coefficients():
     np.testing.assert_array_equal(out[1]["qoi"][:, 1 + 2 * nq_of(b):1 + 3 * nq_of(b)],
                                   np.tile(b["gamma_fixed"], (b["steps"], 1)))
     torch.cuda.synchronize()
+
+
+def _admit_all(B, b, wls, tags):
+    slots = []
+    for w, t in zip(wls, tags):
+        s = B.lbm_batch_admit(b, B.config_from_workload(w, member=t), synthetic.initial_velocity(w), w["steps"], t)
+        assert s is not None
+        if w["to_mode"] == "lrs":
+            nq = nq_of(w)
+            c, mu, sig = synthetic.synthetic_lrs(nq, w["h"], w["seed"])
+            B.lbm_set_lrs(B.lbm_batch_member(b, s), c, mu, sig, np.zeros(nq))
+        slots.append(s)
+    return slots
+
+
+def test_persistent_classes_with_mixed_sizes_parities_and_horizons():
+    """Persistent batches over two lanes: members of one class with different
+    grids (so different launch grids and dynamic shared memory in one batched
+    kernel), admitted between rounds (so they enter at the other population
+    parity), with horizons that end inside a round, next to members above the
+    node limit and a member whose step calls cuFFT (Fourier-band QoIs): those
+    step on their own graphs.  Every member ends bit for bit where it ends
+    alone."""
+    import torch
+
+    from paper_2609_32892_b300 import binding as B
+
+    first = [synthetic.workload("C2", nx=48, ny=40, h=3, steps=11, seed=51),
+             synthetic.workload("C2", nx=64, ny=32, h=3, steps=7, seed=52),
+             synthetic.workload("C3", nx=20, ny=20, nz=12, h=2, steps=9, seed=53),
+             synthetic.workload("C3", nx=24, ny=18, nz=12, h=2, steps=5, seed=54)]
+    later = [synthetic.workload("C2", nx=40, ny=48, h=3, steps=6, seed=55),
+             synthetic.workload("C3", nx=28, ny=20, nz=14, h=2, steps=8, seed=56),
+             synthetic.workload("C2F", h=3, steps=5, seed=57)]
+    wls = first + later
+    alone = [_alone(w, i) for i, w in enumerate(wls)]
+    pool_bytes = sum(B.lbm_required_bytes(B.config_from_workload(w)) for w in wls) + (1 << 20)
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
+    b = B.lbm_batch_create(8, pool.data_ptr(), pool_bytes)
+    B.lbm_batch_set_persistent(b, 2, max_nodes=5000)  # 24x18x12 and 28x20x14 above it
+    slots = _admit_all(B, b, first, range(len(first)))
+    B.lbm_batch_run(b, 3)  # odd: the later members enter at the other parity
+    slots += _admit_all(B, b, later, range(len(first), len(wls)))
+    done = {}
+    for _ in range(6):
+        B.lbm_batch_run(b, 4)
+        B.lbm_batch_wait(b, 1)
+        for comp in B.lbm_batch_poll(b):
+            done[comp["tag"]] = comp
+    B.lbm_batch_wait(b, 0)
+    for comp in B.lbm_batch_poll(b):
+        done[comp["tag"]] = comp
+    torch.cuda.synchronize()
+    assert sorted(done) == list(range(len(wls)))
+    for i, (w, s) in enumerate(zip(wls, slots)):
+        assert done[i]["status"] == 0 and done[i]["steps"] == w["steps"], (i, done[i])
+        ctx = B.lbm_batch_member(b, s)
+        q = 9 if w["dim"] == 2 else 19
+        f = B.lbm_get_populations(ctx, q, (w["nz"], w["ny"], w["nx"]))
+        np.testing.assert_array_equal(f, alone[i][1], err_msg=f"member {i}")
+        rows, _ = B.lbm_qoi(ctx, 2 + 3 * nq_of(w))
+        np.testing.assert_array_equal(rows, alone[i][0], err_msg=f"member {i}")
+        B.lbm_batch_release(b, s)
+    B.lbm_batch_destroy(b)
+
+
+def test_persistent_mode_is_set_before_the_first_round():
+    import torch
+
+    from paper_2609_32892_b300 import binding as B
+
+    w = synthetic.workload("C2", nx=32, ny=32, h=3, steps=4, seed=61)
+    need = B.lbm_required_bytes(B.config_from_workload(w)) + (1 << 20)
+    pool = torch.empty(need, dtype=torch.uint8, device="cuda")
+    b = B.lbm_batch_create(2, pool.data_ptr(), need)
+    _admit_all(B, b, [w], [0])
+    B.lbm_batch_run(b, 2)
+    with pytest.raises(B.LbmError) as e:
+        B.lbm_batch_set_persistent(b, 0)
+    assert e.value.code == B.LBM_ERR_STATE
+    B.lbm_batch_wait(b, 0)
+    B.lbm_batch_destroy(b)

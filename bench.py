@@ -50,17 +50,19 @@ def _peaks():
 
 
 # DRAM traffic per launch and node of each kernel class, read+write bytes from
-# the ncu launch list of the benchmark command (profiles/), reported only while
+# an ncu capture of the benchmark's kernels, reported only while
 # the kernel source still has the hash it had when captured.
 TRAFFIC = {
-    # 320x200x160 channel, WALE + TO-LRS (profiles/gauss_rr_channel3d_320x200x160.md)
-    "collide": {"bytes_per_node": 230.8, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "4319d70a25bab072"},
-    "predict": {"bytes_per_node": 98.0, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "4319d70a25bab072"},
-    "gauss_x": {"bytes_per_node": 43.2, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
-    "gauss_z": {"bytes_per_node": 43.4, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
-    "gauss_y": {"bytes_per_node": 43.8, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "c35fea59739df391"},
-    "lap1": {"bytes_per_node": 45.1, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "86151afaeaf3f213"},
-    "reduce": {"bytes_per_node": 83.2, "source": "paper_2609_32892_b300/csrc/kernels_to.cu", "sha256_16": "cb81ba72923d33b8"},
+    # 320x200x160 channel, WALE + TO-LRS (the launch-list capture of the
+    # C4_TO_MID workload with dram__bytes_read/write), bytes per node per launch
+    "collide": {"bytes_per_node": 230.8, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "688c83d53418403f"},
+    "predict": {"bytes_per_node": 97.8, "source": "paper_2609_32892_b300/csrc/kernels_lbm.cu", "sha256_16": "688c83d53418403f"},
+    "gauss_x": {"bytes_per_node": 43.2, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "451303361d13a538"},
+    "gauss_z": {"bytes_per_node": 43.5, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "451303361d13a538"},
+    "gauss_y": {"bytes_per_node": 43.8, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "451303361d13a538"},
+    "lap3": {"bytes_per_node": 46.8, "source": "paper_2609_32892_b300/csrc/kernels_lap3.cu", "sha256_16": "8e01786c67a5c61b"},
+    "lap1": {"bytes_per_node": 45.3, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "51489dbb2196958c"},
+    "reduce": {"bytes_per_node": 83.2, "source": "paper_2609_32892_b300/csrc/kernels_to.cu", "sha256_16": "42a062a0dc5b9b89"},
 }
 
 

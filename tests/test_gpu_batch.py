@@ -286,3 +286,36 @@ def test_persistent_mode_is_set_before_the_first_round():
     assert e.value.code == B.LBM_ERR_STATE
     B.lbm_batch_wait(b, 0)
     B.lbm_batch_destroy(b)
+
+
+def test_persistent_blocks_running_many_items_match_plain_launches():
+    """Serving-mix sizes in persistent kernels: 4 x 256^2 Kolmogorov and 6 x
+    96x40x48 channel members give each batched launch several times more
+    work items than its persistent grid has blocks, so blocks run many items
+    in a row (shared memory, mbarrier phases and bulk-copy rings reused from
+    item to item).  Every member ends bit for bit where it ends alone."""
+    import torch
+
+    from paper_2609_32892_b300 import binding as B
+
+    wls = [synthetic.workload("C2", h=5, steps=6, seed=71 + i) for i in range(4)]
+    wls += [synthetic.workload("C3", h=5, steps=6, seed=81 + i) for i in range(6)]
+    alone = [_alone(w, i) for i, w in enumerate(wls)]
+    pool_bytes = sum(B.lbm_required_bytes(B.config_from_workload(w)) for w in wls) + (1 << 22)
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
+    b = B.lbm_batch_create(len(wls), pool.data_ptr(), pool_bytes)
+    B.lbm_batch_set_persistent(b, 1, max_nodes=1 << 40)
+    slots = _admit_all(B, b, wls, range(len(wls)))
+    B.lbm_batch_run(b, 6)
+    B.lbm_batch_wait(b, 0)
+    done = {c["tag"]: c for c in B.lbm_batch_poll(b)}
+    torch.cuda.synchronize()
+    for i, (w, s) in enumerate(zip(wls, slots)):
+        assert done[i]["status"] == 0 and done[i]["steps"] == 6
+        ctx = B.lbm_batch_member(b, s)
+        q = 9 if w["dim"] == 2 else 19
+        f = B.lbm_get_populations(ctx, q, (w["nz"], w["ny"], w["nx"]))
+        np.testing.assert_array_equal(f, alone[i][1], err_msg=f"member {i}")
+        rows, _ = B.lbm_qoi(ctx, 2 + 3 * nq_of(w))
+        np.testing.assert_array_equal(rows, alone[i][0], err_msg=f"member {i}")
+    B.lbm_batch_destroy(b)

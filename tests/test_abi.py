@@ -87,3 +87,12 @@ def test_set_to_coeffs_without_gpu(B):
     with pytest.raises(B.LbmError) as e:
         B.lbm_required_bytes(bad)
     assert e.value.code == B.LBM_ERR_ARG
+
+
+def test_batch_mode_arguments_without_gpu(B):
+    """lbm_batch_set_persistent refuses a missing batch and out-of-range lanes
+    or node limits before touching the device."""
+    for lanes, max_nodes in ((1, 16384), (-1, 16384), (65, 16384), (1, -1)):
+        with pytest.raises(B.LbmError) as e:
+            B.lbm_batch_set_persistent(None, lanes, max_nodes)
+        assert e.value.code == B.LBM_ERR_ARG

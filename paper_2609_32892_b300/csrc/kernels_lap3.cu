@@ -9,7 +9,7 @@
 //
 //   raw ring   input planes with a 7-node halo in y and 8 in x (periodic in
 //              x; zero beyond a wall, periodic in y without walls), staged by
-//              16-byte asynchronous copies NS planes ahead
+//              16-byte asynchronous copies NS - 1 planes ahead
 //   box        per plane, the in-plane 3 x 3 box P_k over the tile plus a
 //              6-node halo: a half-warp holds a row of 16 quads and slides
 //              down 4 rows (column sums of 3 staged rows), the x neighbours
@@ -27,13 +27,6 @@
 
 #include "batch.cuh"
 #include "lbm_common.cuh"
-
-#ifndef L3_TY
-#define L3_TY 16
-#endif
-#ifndef L3_NS
-#define L3_NS 5
-#endif
 
 namespace lbm {
 
@@ -217,8 +210,6 @@ __device__ __forceinline__ void lap3_fused_kernel_body(const VB& vb, const Param
                 // output z_b + d sits in ring slot (k - 9 + d) mod 13; k0 is a
                 // multiple of 13, so every slot below is a constant
                 constexpr int o = 2 * kRing - 9;
-                constexpr int dummy = 0;
-                (void)dummy;
                 const int sm6 = (u + o - 6) % kRing, sm3 = (u + o - 3) % kRing, sc = (u + o) % kRing;
                 const int sp3 = (u + o + 3) % kRing, sp6 = (u + o + 6) % kRing;
                 const Quad done = qadd(acc[sm6], bc);  // output z_b - 6 takes its z + 6 arm
@@ -290,7 +281,9 @@ cudaError_t run_lap3(const Params& p, const float* in, float* out, int ncomp, fl
 
 cudaError_t launch_lap3_fused(const Params& p, const float* in, float* out, int ncomp, float scale, int per_sm,
                               cudaStream_t s) {
-    return run_lap3<L3_TY, L3_NS>(p, in, out, ncomp, scale, per_sm, s);
+    // 16 output rows per tile (32 was slower: one 384-thread block per SM at
+    // 168 registers); five raw plane slots, four in flight
+    return run_lap3<16, 5>(p, in, out, ncomp, scale, per_sm, s);
 }
 
 }  // namespace lbm

@@ -407,43 +407,59 @@ __device__ __forceinline__ void crossq3_kernel_body(const VB& vb, const Params& 
     const bool live = gx0 < p.nx && y < p.ny;
     const bool solid = p.walls && (y == 0 || y == p.ny - 1);
     const int rq = (ry + HY) * NQ + qx + 1;  // the output quad in a staged plane
-    for (int zo = z0; zo < z1; ++zo) {
-        cp_async_wait2();  // planes up to zo + 2 have landed (zo + 3, zo + 4 may be in flight)
-        __syncthreads();
-        issue(zo + RA + 3);
-        const float4* t0 = reinterpret_cast<const float4*>(tile[zo & (NB - 1)]);
-        const float4* m1 = reinterpret_cast<const float4*>(tile[(zo - 1) & (NB - 1)]);
-        const float4* p1 = reinterpret_cast<const float4*>(tile[(zo + 1) & (NB - 1)]);
-        const float4* m2 = reinterpret_cast<const float4*>(tile[(zo - 2) & (NB - 1)]);
-        const float4* p2 = reinterpret_cast<const float4*>(tile[(zo + 2) & (NB - 1)]);
-        const float4 xl = t0[rq - 1], xc = t0[rq], xr = t0[rq + 1];
-        const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-        const float4 a1 = t0[rq - NQ], b1 = t0[rq + NQ], a2 = t0[rq - 2 * NQ], b2 = t0[rq + 2 * NQ];
-        const float ym1[4] = {a1.x, a1.y, a1.z, a1.w}, yp1[4] = {b1.x, b1.y, b1.z, b1.w};
-        const float ym2[4] = {a2.x, a2.y, a2.z, a2.w}, yp2[4] = {b2.x, b2.y, b2.z, b2.w};
-        const float4 c1 = m1[rq], d1 = p1[rq], c2 = m2[rq], d2 = p2[rq];
-        const float zm1[4] = {c1.x, c1.y, c1.z, c1.w}, zp1[4] = {d1.x, d1.y, d1.z, d1.w};
-        const float zm2[4] = {c2.x, c2.y, c2.z, c2.w}, zp2[4] = {d2.x, d2.y, d2.z, d2.w};
-        float res[4];
+    // this thread's column: the quad of planes zo - 2 .. zo + 2 in a register
+    // ring (plane q in slot (q - z0) mod 5; the plane loop is unrolled by 5,
+    // so every slot index is a constant); each plane adds one 16-byte load
+    float4 ring[5];
+    for (int zb = z0; zb < z1; zb += 5) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float ctr = v[4 + j];
-            float axy = 2.f * arm.t[RA] * ctr;
-            axy += arm.t[RA + 1] * ((v[3 + j] + v[5 + j]) + (ym1[j] + yp1[j]));
-            axy += arm.t[RA + 2] * ((v[2 + j] + v[6 + j]) + (ym2[j] + yp2[j]));
-            float w = axy + arm.t[RA] * ctr;
-            w += arm.t[RA + 1] * (zm1[j] + zp1[j]);
-            w += arm.t[RA + 2] * (zm2[j] + zp2[j]);
-            res[j] = solid ? 0.f : scale * w;
-        }
-        if (live) {
-            float4* op = reinterpret_cast<float4*>(o + ((size_t)zo * p.ny + y) * p.nx + gx0);
-            float4 w = make_float4(res[0], res[1], res[2], res[3]);
-            if (accumulate) {
-                const float4 old = *op;
-                w.x += old.x; w.y += old.y; w.z += old.z; w.w += old.w;
+        for (int u = 0; u < 5; ++u) {
+            const int zo = zb + u;
+            if (zo >= z1) break;  // uniform over the block
+            cp_async_wait2();  // planes up to zo + 2 have landed (zo + 3, zo + 4 may be in flight)
+            __syncthreads();
+            issue(zo + RA + 3);
+            const float* t0 = tile[zo & (NB - 1)];
+            if (zb == z0 && u == 0) {
+                ring[3] = reinterpret_cast<const float4*>(tile[(zo - 2) & (NB - 1)])[rq];
+                ring[4] = reinterpret_cast<const float4*>(tile[(zo - 1) & (NB - 1)])[rq];
+                ring[0] = reinterpret_cast<const float4*>(t0)[rq];
+                ring[1] = reinterpret_cast<const float4*>(tile[(zo + 1) & (NB - 1)])[rq];
             }
-            *op = w;
+            ring[(u + 2) % 5] = reinterpret_cast<const float4*>(tile[(zo + 2) & (NB - 1)])[rq];
+            const float4 xc = ring[u % 5];
+            const float2 xl = reinterpret_cast<const float2*>(t0)[2 * rq - 1];  // x - 2, x - 1
+            const float2 xr = reinterpret_cast<const float2*>(t0)[2 * rq + 2];  // x + 4, x + 5
+            const float v[8] = {xl.x, xl.y, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y};  // x - 2 .. x + 5
+            const float4* t4 = reinterpret_cast<const float4*>(t0);
+            const float4 a1 = t4[rq - NQ], b1 = t4[rq + NQ], a2 = t4[rq - 2 * NQ], b2 = t4[rq + 2 * NQ];
+            const float ym1[4] = {a1.x, a1.y, a1.z, a1.w}, yp1[4] = {b1.x, b1.y, b1.z, b1.w};
+            const float ym2[4] = {a2.x, a2.y, a2.z, a2.w}, yp2[4] = {b2.x, b2.y, b2.z, b2.w};
+            const float4 c1 = ring[(u + 4) % 5], d1 = ring[(u + 1) % 5], c2 = ring[(u + 3) % 5],
+                         d2 = ring[(u + 2) % 5];
+            const float zm1[4] = {c1.x, c1.y, c1.z, c1.w}, zp1[4] = {d1.x, d1.y, d1.z, d1.w};
+            const float zm2[4] = {c2.x, c2.y, c2.z, c2.w}, zp2[4] = {d2.x, d2.y, d2.z, d2.w};
+            float res[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float ctr = v[2 + j];
+                float axy = 2.f * arm.t[RA] * ctr;
+                axy += arm.t[RA + 1] * ((v[1 + j] + v[3 + j]) + (ym1[j] + yp1[j]));
+                axy += arm.t[RA + 2] * ((v[0 + j] + v[4 + j]) + (ym2[j] + yp2[j]));
+                float w = axy + arm.t[RA] * ctr;
+                w += arm.t[RA + 1] * (zm1[j] + zp1[j]);
+                w += arm.t[RA + 2] * (zm2[j] + zp2[j]);
+                res[j] = solid ? 0.f : scale * w;
+            }
+            if (live) {
+                float4* op = reinterpret_cast<float4*>(o + ((size_t)zo * p.ny + y) * p.nx + gx0);
+                float4 w = make_float4(res[0], res[1], res[2], res[3]);
+                if (accumulate) {
+                    const float4 old = *op;
+                    w.x += old.x; w.y += old.y; w.z += old.z; w.w += old.w;
+                }
+                *op = w;
+            }
         }
     }
     cp_async_wait0();

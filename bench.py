@@ -61,7 +61,7 @@ TRAFFIC = {
     "gauss_z": {"bytes_per_node": 43.5, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "451303361d13a538"},
     "gauss_y": {"bytes_per_node": 43.8, "source": "paper_2609_32892_b300/csrc/kernels_gauss.cu", "sha256_16": "451303361d13a538"},
     "lap3": {"bytes_per_node": 46.8, "source": "paper_2609_32892_b300/csrc/kernels_lap3.cu", "sha256_16": "ec461ce139f74cbf"},
-    "lap1": {"bytes_per_node": 45.3, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "51489dbb2196958c"},
+    "lap1": {"bytes_per_node": 45.2, "source": "paper_2609_32892_b300/csrc/kernels_filter3d.cu", "sha256_16": "299188d226c581c3"},
     "reduce": {"bytes_per_node": 83.2, "source": "paper_2609_32892_b300/csrc/kernels_to.cu", "sha256_16": "42a062a0dc5b9b89"},
 }
 

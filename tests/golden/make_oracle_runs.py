@@ -13,9 +13,13 @@ physics and its 12 QoIs) on a smaller grid:
                     the history product spans two 256-row blocks
   c3_36x22x13_h20   1000 steps on 36 x 22 x 13, h = 20
   c3_36x22x13_h20_u0f32   the same from the initial field rounded to FP32
+  c3_96x40x48_h500  6 steps of the 96x40x48 workload itself (h = 500: 12 013
+                    rows of C), full-size filter tiles in every direction
 
 Stored per case (float64): the QoI block rows, the final density and velocity
-(`Simulation.macros`), the running mean-profile sum, the reference scales.
+(`Simulation.macros`), the running mean-profile sum, the reference scales.  A
+case with `sample` stores the final state only on nodes x[::sx], z[::sz] (all
+rows), in float32 (far below the FP32-run tolerances), to keep the file small.
 
 Usage:  python tests/golden/make_oracle_runs.py [case ...]   (all cases by default)
 """
@@ -36,6 +40,7 @@ CASES = {
     # the same run from the initial field rounded to FP32: the oracle's own
     # sensitivity to a perturbation of the size of FP32 rounding
     "c3_36x22x13_h20_u0f32": dict(name="C3", kw=dict(nx=36, ny=22, nz=13, h=20), steps=1000, warm=3, u0_f32=True),
+    "c3_96x40x48_h500": dict(name="C3", kw=dict(), steps=6, warm=3, sample=(3, 2)),
 }
 
 
@@ -70,9 +75,14 @@ def _run(case):
     sim = Simulation(wl, u0, lrs=(cmat, mu, sig, sigma_ref))
     rows = sim.run(c["steps"])
     rho, u = sim.macros()
+    if c.get("sample"):
+        sx, sz = c["sample"]
+        rho = rho[::sz, :, ::sx].astype(np.float32)
+        u = u[:, ::sz, :, ::sx].astype(np.float32)
     np.savez_compressed(os.path.join(OUT, case + ".npz"), rows=rows, rho=rho, u=u,
                         profile_sum=sim.profile_sum, sigma_ref=sigma_ref,
-                        meta=json.dumps(dict(case=case, steps=c["steps"], workload=c["name"], kw=c["kw"])))
+                        meta=json.dumps(dict(case=case, steps=c["steps"], workload=c["name"], kw=c["kw"],
+                                             sample=c.get("sample"))))
     return case, time.time() - t0, int(np.max(rows[:, -1]))
 
 

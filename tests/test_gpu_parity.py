@@ -29,8 +29,8 @@ from oracle import philox
 pytestmark = pytest.mark.gpu
 
 
-def _compare_state(wl, rho_g, u_g, rho_o, u_o, tol=1e-5, rho_abs=1e-6):
-    m = fluid_mask(wl)
+def _compare_state(wl, rho_g, u_g, rho_o, u_o, tol=1e-5, rho_abs=1e-6, mask=None):
+    m = fluid_mask(wl) if mask is None else mask
     e_rho = rel_l2(rho_g, rho_o, m)
     e_dev = rel_l2(rho_g - 1.0, rho_o - 1.0, m)
     d_abs = float(np.max(np.abs(rho_g - rho_o) * m))

@@ -39,8 +39,11 @@ sys.path.insert(0, os.path.join(HERE, "golden"))
 import make_oracle_runs  # noqa: E402
 
 
-@pytest.mark.parametrize("case", ["c3_68x38x17_h20"])
+@pytest.mark.parametrize("case", ["c3_68x38x17_h20", "c3_96x40x48_h500"])
 def test_stored_channel_wale_lrs_run(case):
+    """GPU against stored FP64 oracle runs of the channel LES (WALE + TO-LRS,
+    12 QoIs): 100 steps on 68x38x17 (h = 20), and 6 steps of the 96x40x48
+    workload itself (h = 500, full-size filter tiles in every direction)."""
     from paper_2609_32892_b300 import binding as B
 
     path = os.path.join(HERE, "golden", "oracle_runs", case + ".npz")
@@ -56,7 +59,11 @@ def test_stored_channel_wale_lrs_run(case):
     assert np.all(ro[:, -1] == 0)  # the stored run never went singular or unstable
     # rho ~ 1 +- 3e-3 here: FP32 rounding of rho (half-ulp 6e-8 per step) walks
     # ~6e-7 rms over 100 steps, ~2e-6 at the worst of 4e4 nodes
-    _compare_state(wl, rho_g, u_g, d["rho"], d["u"], rho_abs=5e-6)
+    mask = fluid_mask(wl)
+    if meta.get("sample"):  # the stored state is the subsample x[::sx], z[::sz]
+        sx, sz = meta["sample"]
+        rho_g, u_g, mask = rho_g[::sz, :, ::sx], u_g[:, ::sz, :, ::sx], mask[::sz, :, ::sx]
+    _compare_state(wl, rho_g, u_g, d["rho"].astype(np.float64), d["u"].astype(np.float64), rho_abs=5e-6, mask=mask)
     _compare_rows(wl, rg, ro)
     # mean streamwise profile: FP64 running sum of plane means (Sec. 7.3); the
     # plane means inherit the FP32 state's error (rel-L2(u) <= 1e-5 above), so

@@ -15,6 +15,8 @@ physics and its 12 QoIs) on a smaller grid:
   c3_36x22x13_h20_u0f32   the same from the initial field rounded to FP32
   c3_96x40x48_h500  6 steps of the 96x40x48 workload itself (h = 500: 12 013
                     rows of C), full-size filter tiles in every direction
+  c2_256_h400       100 steps of the 256^2 Kolmogorov workload itself
+                    (Smagorinsky + TO-LRS, 4 QoIs, h = 400: 3205 rows of C)
 
 Stored per case (float64): the QoI block rows, the final density and velocity
 (`Simulation.macros`), the running mean-profile sum, the reference scales.  A
@@ -41,6 +43,7 @@ CASES = {
     # sensitivity to a perturbation of the size of FP32 rounding
     "c3_36x22x13_h20_u0f32": dict(name="C3", kw=dict(nx=36, ny=22, nz=13, h=20), steps=1000, warm=3, u0_f32=True),
     "c3_96x40x48_h500": dict(name="C3", kw=dict(), steps=6, warm=3, sample=(3, 2)),
+    "c2_256_h400": dict(name="C2", kw=dict(), steps=100, warm=3, sample=(2, 1)),
 }
 
 

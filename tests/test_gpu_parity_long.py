@@ -181,3 +181,23 @@ def test_kolmogorov_lrs_h100_150_steps():
     _compare_state(wl, rho_g, u_g, rho_o, u_o)
     _compare_rows(wl, rg, ro)
     assert rel_l2(u_g, u_o, fluid_mask(wl)) <= 1e-5
+
+
+def test_stored_kolmogorov_lrs_run():
+    """GPU against the stored FP64 oracle run of the 256^2 Kolmogorov workload
+    itself (Smagorinsky + TO-LRS, 4 QoIs, h = 400: 3205 rows of C, thirteen
+    blocks of the history product) over 100 steps."""
+    case = "c2_256_h400"
+    d = np.load(os.path.join(HERE, "golden", "oracle_runs", case + ".npz"))
+    meta = json.loads(str(d["meta"]))
+    wl = make_oracle_runs.case_workload(case)
+    lrs = lrs_inputs(wl, d["sigma_ref"])
+    g, rg, rho_g, u_g = run_gpu(wl, meta["steps"], lrs=lrs)
+    g.close()
+    ro = d["rows"]
+    assert np.all(ro[:, -1] == 0)
+    sx, sz = meta["sample"]
+    mask = fluid_mask(wl)[::sz, :, ::sx]
+    _compare_state(wl, rho_g[::sz, :, ::sx], u_g[:, ::sz, :, ::sx], d["rho"].astype(np.float64),
+                   d["u"].astype(np.float64), mask=mask)
+    _compare_rows(wl, rg, ro)

@@ -296,14 +296,15 @@ int lbm_eval_qoi(lbm_ctx* ctx, const float* u, double* q);
 
 /* Autotuner (default on): before the first lbm_step the library times the
  * candidate launch shapes of its kernels on this context's buffers (node-pair
- * vs single-node collide, the z-segment count of the fused 3-D filters, the
+ * vs single-node collide and predictor pass, the z-segment count of the fused 3-D filters, the
  * line segments of 2-D filter passes) and keeps the fastest, cached per grid
  * shape for the process.  Per node, every candidate evaluates the same
  * arithmetic.  lbm_set_autotune must precede the first lbm_step; 0 keeps the
  * built-in shapes.  lbm_get_tuning returns [tuned, collide_pair,
  * corrector_in_collide (1 when the step's SGS corrector runs inside the
  * collide: every TO mode but OFF and OBSERVE), march_threads, blocks_per_sm
- * of filter slot 0..7 (0 = default), throughput goal] (up to count values). */
+ * of filter slot 0..7 (0 = default), throughput goal, predict_pair] (up to
+ * count values). */
 int lbm_set_autotune(lbm_ctx* ctx, int enable);
 int lbm_get_tuning(lbm_ctx* ctx, int32_t* values, int count);
 

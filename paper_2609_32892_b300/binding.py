@@ -420,7 +420,8 @@ def lbm_eval_qoi(ctx, u_ptr, q_ptr):
 
 
 def lbm_get_tuning(ctx):
-    v = (C.c_int32 * 13)()
-    _check(_lib.lbm_get_tuning(ctx, v, 13), ctx)
+    v = (C.c_int32 * 14)()
+    _check(_lib.lbm_get_tuning(ctx, v, 14), ctx)
     return {"tuned": int(v[0]), "collide_pair": int(v[1]), "corrector_in_collide": int(v[2]), "march_threads": int(v[3]),
-            "filter_blocks_per_sm": [int(v[4 + f]) for f in range(8)], "throughput_goal": int(v[12])}
+            "filter_blocks_per_sm": [int(v[4 + f]) for f in range(8)], "throughput_goal": int(v[12]),
+            "predict_pair": int(v[13])}

@@ -746,7 +746,7 @@ cudaError_t launch_init_feq(const Params& p, const Layout& L, const float* drho,
 template <int DIM, typename T, bool WV, bool WN>
 static void do_predict_d(const Params& p, const Layout& L, int src, cudaStream_t s) {
     const T* a = (const T*)L.f[src];
-    if (p.nx % 2 == 0)
+    if (p.nx % 2 == 0 && p.tune.predict_pair)  // node pairs (autotuned; single nodes read fewer bytes per load)
         go<predict2_kernel_op<DIM, T, WV, WN>>(predict2_kernel<DIM, T, WV, WN>, grid_of(p.n / 2, 128), 128, 0, s, p,
                                                a, L.vps, L.vn, L.kolmo);
     else

@@ -228,6 +228,7 @@ static void make_params(const lbm_config* c, Params* p, std::vector<Filter>* fil
     for (int f = 0; f < 8; ++f) p->tune.filter_per_sm[f] = 0;
     p->tune.march_lines = 148 * 2048;
     p->tune.collide_pair = c->substrate == LBM_SUBSTRATE_WALE ? 0 : 1;
+    p->tune.predict_pair = c->substrate == LBM_SUBSTRATE_WALE ? 0 : 1;
     p->tune.one_seg = 0;
     if (p->h > 0) {
         const long long rows = (long long)(2 * p->h + 1) * p->n_q + 1;
@@ -810,6 +811,17 @@ static int autotune(lbm_ctx* c) {
             if (t < best) { best = t; pick = v; }
         }
         p.tune.collide_pair = pick;
+    }
+    // predictor pass: node pairs or single nodes
+    if (p.nx % 2 == 0 && (p.to_mode != LBM_TO_OFF || p.substrate == LBM_SUBSTRATE_WALE)) {
+        float best = 1e30f;
+        int pick = p.tune.predict_pair;
+        for (int v = 0; v <= 1; ++v) {
+            p.tune.predict_pair = v;
+            const float t = time_ms(c, [&] { chk(launch_predict(p, c->L, src, c->stream)); }, 5);
+            if (t < best) { best = t; pick = v; }
+        }
+        p.tune.predict_pair = pick;
     }
     if (p.to_mode != LBM_TO_OFF) {
         const int nc = p.ncomp;
@@ -1465,10 +1477,11 @@ int lbm_set_autotune(lbm_ctx* c, int enable) {
 
 int lbm_get_tuning(lbm_ctx* c, int32_t* values, int count) {
     if (!c || !values) return fail(c, LBM_ERR_ARG, "NULL argument");
-    int32_t v[13] = {c->tuned, c->p.tune.collide_pair, corrector_runs(c->p) ? 1 : 0, c->p.tune.march_lines};
+    int32_t v[14] = {c->tuned, c->p.tune.collide_pair, corrector_runs(c->p) ? 1 : 0, c->p.tune.march_lines};
     for (int f = 0; f < 8; ++f) v[4 + f] = c->p.tune.filter_per_sm[f];
     v[12] = c->p.tune.one_seg;
-    for (int k = 0; k < count && k < 13; ++k) values[k] = v[k];
+    v[13] = c->p.tune.predict_pair;
+    for (int k = 0; k < count && k < 14; ++k) values[k] = v[k];
     return LBM_OK;
 }
 

@@ -85,6 +85,7 @@ struct Tune {
     int filter_per_sm[8];  // fused 3-D filter of each distinct filter slot: target blocks per SM (0: default)
     int march_lines;    // 1-D passes along y/z: target threads in flight (line segments)
     int collide_pair;   // node-pair collide when nx is even
+    int predict_pair;   // node-pair predictor pass when nx is even
     int one_seg;        // fused 3-D filters: one z segment per block column (least total work)
 };
 

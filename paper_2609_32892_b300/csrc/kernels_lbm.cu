@@ -452,6 +452,18 @@ __device__ __forceinline__ void sgs_correct(float* g, float r, float ux, float u
 // One thread per node: pull, collide_node and, with CORR, the SGS corrector
 // of the step (Eq. LES-2) before the store: the predictor populations never
 // leave registers.
+//
+// 3-D FP32 launches collide4_kernel: four 256-thread blocks per SM (64
+// registers; the WALE corrector form takes 80 otherwise, three blocks).  The
+// kernel waits on its population, sensitivity and velocity loads, and the
+// fourth block hides more of that latency than the few spilled bytes cost
+// (1.17 -> 1.15 ms at 480 x 200 x 240).  16-bit storage and 2-D keep
+// collide_kernel and the compiler's register choice (the 16-bit forms are
+// arithmetic bound and would spill more under the cap).
+template <int DIM, typename T>
+constexpr int collide_minb() {
+    return DIM == 3 && sizeof(T) == 4 ? 4 : 1;
+}
 template <int DIM, typename T, int SUB, bool CORR>
 __device__ __forceinline__ void collide_kernel_body(const VB& vb, const Params& p, const T* __restrict__ src,
                                                     T* __restrict__ dst, const float* __restrict__ vn,
@@ -477,7 +489,7 @@ __device__ __forceinline__ void collide_kernel_body(const VB& vb, const Params& 
 }
 template <int DIM, typename T, int SUB, bool CORR>
 struct collide_kernel_op {
-    static constexpr int NT = 256, MINB = 1;
+    static constexpr int NT = 256, MINB = collide_minb<DIM, T>();
     template <class... B>
     static __device__ __forceinline__ void run(const VB& vb, const B&... b) {
         collide_kernel_body<DIM, T, SUB, CORR>(vb, b...);
@@ -488,6 +500,13 @@ __global__ void __launch_bounds__(256) collide_kernel(Params p, const T* __restr
                                                       const float* __restrict__ vn, const float* __restrict__ kolmo,
                                                       DevState* st, VPtrs vk, const float* __restrict__ betaf,
                                                       const float* __restrict__ mprow) {
+    collide_kernel_body<DIM, T, SUB, CORR>(vb_hw(), p, src, dst, vn, kolmo, st, vk, betaf, mprow);
+}
+template <int DIM, typename T, int SUB, bool CORR>
+__global__ void __launch_bounds__(256, 4) collide4_kernel(Params p, const T* __restrict__ src, T* __restrict__ dst,
+                                                          const float* __restrict__ vn, const float* __restrict__ kolmo,
+                                                          DevState* st, VPtrs vk, const float* __restrict__ betaf,
+                                                          const float* __restrict__ mprow) {
     collide_kernel_body<DIM, T, SUB, CORR>(vb_hw(), p, src, dst, vn, kolmo, st, vk, betaf, mprow);
 }
 
@@ -788,6 +807,9 @@ static void do_collide_k(const Params& p, const Layout& L, int src, cudaStream_t
     if (p.nx % 2 == 0 && p.tune.collide_pair)  // node pairs: nx even keeps every pair inside one row, 2-aligned
         go<collide2_kernel_op<DIM, T, SUB, CORR>>(collide2_kernel<DIM, T, SUB, CORR>, grid_of(p.n / 2, 128), 128, 0, s,
                                                   p, a, b, L.vn, L.kolmo, L.st, vk, L.betaf, L.mprow);
+    else if constexpr (collide_minb<DIM, T>() == 4)
+        go<collide_kernel_op<DIM, T, SUB, CORR>>(collide4_kernel<DIM, T, SUB, CORR>, grid_of(p.n, 256), 256, 0, s, p,
+                                                 a, b, L.vn, L.kolmo, L.st, vk, L.betaf, L.mprow);
     else
         go<collide_kernel_op<DIM, T, SUB, CORR>>(collide_kernel<DIM, T, SUB, CORR>, grid_of(p.n, 256), 256, 0, s, p,
                                                  a, b, L.vn, L.kolmo, L.st, vk, L.betaf, L.mprow);

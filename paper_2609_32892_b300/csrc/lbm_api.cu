@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <memory>
 #include <thread>
 #include <vector>
@@ -1077,16 +1078,42 @@ int lbm_init_macros(lbm_ctx* c, const double* rho, const double* u) {
     if (!c || !u) return fail(c, LBM_ERR_ARG, "NULL argument");
     const size_t N = (size_t)c->p.n;
     std::unique_ptr<float[]> tmp;
-    float* hp = host_stage(c, tmp);  // every element is written below
+    float* hp = host_stage(c, tmp);
+    // without a density field its slot is zeroed on the device (a quarter of
+    // the upload saved)
+    if (!rho) CK(c, cudaMemsetAsync(c->aux, 0, sizeof(float) * N, c->stream));
+    // every conversion thread queues the copy of each 1 MB piece it has
+    // written, so the DMA of one piece overlaps the conversion of the next
+    // (worker threads select the caller's device first)
+    int dev = 0;
+    CK(c, cudaGetDevice(&dev));
+    std::atomic<int> err{0};
     parallel_for(N, [&](size_t a, size_t b) {
-        for (size_t i = a; i < b; ++i) hp[i] = rho ? (float)(rho[i] - 1.0) : 0.f;
-        for (size_t i = a; i < b; ++i) {
-            hp[N + i] = (float)u[i];
-            hp[2 * N + i] = (float)u[N + i];
-            hp[3 * N + i] = (float)u[2 * N + i];
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            err.store((int)cudaErrorInvalidDevice);
+            return;
+        }
+        constexpr size_t kPiece = (size_t)1 << 18;
+        for (size_t q0 = a; q0 < b; q0 += kPiece) {
+            const size_t q1 = q0 + kPiece < b ? q0 + kPiece : b;
+            if (rho)
+                for (size_t i = q0; i < q1; ++i) hp[i] = (float)(rho[i] - 1.0);
+            for (size_t i = q0; i < q1; ++i) {
+                hp[N + i] = (float)u[i];
+                hp[2 * N + i] = (float)u[N + i];
+                hp[3 * N + i] = (float)u[2 * N + i];
+            }
+            for (int sl = rho ? 0 : 1; sl < 4; ++sl) {
+                const cudaError_t e = cudaMemcpyAsync(c->aux + sl * N + q0, hp + sl * N + q0, sizeof(float) * (q1 - q0),
+                                                      cudaMemcpyHostToDevice, c->stream);
+                if (e != cudaSuccess) {
+                    int none = 0;
+                    err.compare_exchange_strong(none, (int)e);
+                }
+            }
         }
     });
-    CK(c, cudaMemcpyAsync(c->aux, hp, sizeof(float) * 4 * N, cudaMemcpyHostToDevice, c->stream));
+    if (err.load()) CK(c, (cudaError_t)err.load());
     c->cur = 0;
     CK(c, launch_init_feq(c->p, c->L, c->aux, c->aux + N, 0, c->stream));
     int rc = reset_counters(c);

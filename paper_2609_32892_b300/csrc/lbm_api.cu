@@ -10,6 +10,9 @@
 #include <atomic>
 #include <memory>
 #include <thread>
+#if defined(__SSE2__)
+#include <emmintrin.h>
+#endif
 #include <vector>
 
 #include <cufft.h>
@@ -900,6 +903,27 @@ static void parallel_for(size_t n, F body) {
     for (std::thread& th : pool) th.join();
 }
 
+// dst[i] = (float)(src[i] - off) for i in [0, n): the same conversion as the
+// scalar loop, with 16-byte non-temporal stores where dst is aligned (the
+// staging buffer is written once and read by the DMA engine, so the stores
+// skip the cache and its read-for-ownership of every line).
+static void f64_to_f32(float* dst, const double* src, size_t n, double off) {
+    size_t i = 0;
+#if defined(__SSE2__)
+    while (i < n && ((uintptr_t)(dst + i) & 15)) {
+        dst[i] = (float)(src[i] - off);
+        ++i;
+    }
+    const __m128d o = _mm_set1_pd(off);
+    for (; i + 4 <= n; i += 4) {
+        const __m128 lo = _mm_cvtpd_ps(_mm_sub_pd(_mm_loadu_pd(src + i), o));
+        const __m128 hi = _mm_cvtpd_ps(_mm_sub_pd(_mm_loadu_pd(src + i + 2), o));
+        _mm_stream_ps(dst + i, _mm_movelh_ps(lo, hi));
+    }
+#endif
+    for (; i < n; ++i) dst[i] = (float)(src[i] - off);
+}
+
 // The context's pinned host staging for whole-field transfers ([4][N]
 // floats), allocated on first use for fields of 2^20 nodes or more: a
 // pageable copy of a 23 M-node field runs at a fraction of the DMA rate.
@@ -1096,13 +1120,11 @@ int lbm_init_macros(lbm_ctx* c, const double* rho, const double* u) {
         constexpr size_t kPiece = (size_t)1 << 18;
         for (size_t q0 = a; q0 < b; q0 += kPiece) {
             const size_t q1 = q0 + kPiece < b ? q0 + kPiece : b;
-            if (rho)
-                for (size_t i = q0; i < q1; ++i) hp[i] = (float)(rho[i] - 1.0);
-            for (size_t i = q0; i < q1; ++i) {
-                hp[N + i] = (float)u[i];
-                hp[2 * N + i] = (float)u[N + i];
-                hp[3 * N + i] = (float)u[2 * N + i];
-            }
+            if (rho) f64_to_f32(hp + q0, rho + q0, q1 - q0, 1.0);
+            for (int k = 0; k < 3; ++k) f64_to_f32(hp + (k + 1) * N + q0, u + k * N + q0, q1 - q0, 0.0);
+#if defined(__SSE2__)
+            _mm_sfence();  // the streamed stores are visible before the copy is queued
+#endif
             for (int sl = rho ? 0 : 1; sl < 4; ++sl) {
                 const cudaError_t e = cudaMemcpyAsync(c->aux + sl * N + q0, hp + sl * N + q0, sizeof(float) * (q1 - q0),
                                                       cudaMemcpyHostToDevice, c->stream);

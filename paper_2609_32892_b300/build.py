@@ -35,15 +35,20 @@ def _stale():
 def build(force=False, verbose=False):
     if not force and not _stale():
         return LIB
-    objs = []
-    for src in SOURCES:
-        obj = os.path.join(CSRC, src.replace(".cu", ".o"))
+    from concurrent.futures import ThreadPoolExecutor
+
+    objs = [os.path.join(CSRC, src.replace(".cu", ".o")) for src in SOURCES]
+    cmds = []
+    for src, obj in zip(SOURCES, objs):
         cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
                os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
-        subprocess.run(cmd, check=True)
-        objs.append(obj)
+        cmds.append(cmd)
+    # the translation units compile independently: one nvcc per source at once
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as pool:
+        for r in pool.map(lambda c: subprocess.run(c, check=True), cmds):
+            pass
     tmp = LIB + ".tmp"
     subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft"], check=True)
     os.replace(tmp, LIB)
